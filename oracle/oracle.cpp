@@ -1,0 +1,566 @@
+// Plain CPU oracle for the semiring Datalog fixpoint -- TEST INFRASTRUCTURE ONLY.
+//
+// Only the tests, the smoke check and the benchmark's CPU-baseline leg use this
+// file.  It shares no code with the CUDA engine: it has its own parser, its own
+// relations (std::map of tuples), and its own semiring arithmetic in FP64.
+//
+// What it computes (Lobster, Sec. 3.1 "Provenance Semirings", Fig. 3 and the
+// semiring table; Algorithm 1 for the iteration-until-no-growth loop):
+//
+//   F_0     = the loaded facts, duplicate rows merged with (+)  [(+) = oplus]
+//   F_{k+1} = F_k updated with, for every head key h,
+//               T(h) = (+) over all groundings g of a rule with head h,
+//                      evaluated over F_k, of (x) of the tags of g's body facts
+//   stop when an iteration changes nothing.
+//
+// This is naive (not semi-naive) evaluation: every grounding over the whole
+// database is enumerated in every iteration, which is the textbook definition
+// of the least fixpoint.  How T(h) enters F_{k+1} depends on the semiring:
+//
+//   * unit, max-min-prob, diff-max-min (idempotent (+)):  F_{k+1}(h) = F_k(h) (+) T(h)
+//     for every h (a missing key counts as 0).  This is the least fixpoint.
+//   * add-mult-prob, diff-add-mult (non-idempotent (+)):  only keys absent from
+//     F_k are added, with tag T(h); tags of existing keys never change.  This is
+//     what semi-naive evaluation with size-based termination (Algorithm 1)
+//     computes, and it terminates on cyclic graphs.
+//
+// Semirings (semiring table of Sec. 3.1 plus the probabilistic ones of Sec. 3.4):
+//   0 unit           T = {true}, every tag is 1
+//   1 max-min-prob   (+) = max, (x) = min on [0,1]
+//   2 add-mult-prob  (+) = min(1, a + b), (x) = a * b on [0,1]
+//   3 diff-max-min   tags (v, id); (+) keeps the larger (v, then smaller id),
+//                    (x) keeps the smaller; d v / d p_id = 1
+//   4 diff-add-mult  add-mult-prob carried with a forward-mode sparse gradient
+//                    (dual number): d(a+b) = da + db, zero when a + b > 1;
+//                    d(a*b) = a db + b da
+//
+// Batched inputs (Sec. 4.3): facts carry a sample id and samples never join; the
+// oracle states that directly by running the fixpoint once per sample.
+#include <algorithm>
+#include <array>
+#include <cctype>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <set>
+#include <string>
+#include <vector>
+
+namespace {
+
+constexpr int kMaxArity = 8;
+constexpr uint32_t kNoId = 0xFFFFFFFFu;
+using Tuple = std::array<uint32_t, kMaxArity>;
+using Dual = std::map<uint32_t, double>;  // input-fact id -> partial derivative
+
+enum Semiring { UNIT = 0, MAX_MIN = 1, ADD_MULT = 2, DIFF_MAX_MIN = 3, DIFF_ADD_MULT = 4 };
+
+struct Tag {
+  double v = 1.0;
+  uint32_t id = kNoId;  // diff-max-min: the input fact that bounds v
+  Dual d;               // diff-add-mult: d v / d p
+};
+
+std::string g_err;
+
+// ---------------------------------------------------------------------------
+// program text
+// ---------------------------------------------------------------------------
+struct Term {
+  bool is_var = false;
+  uint32_t value = 0;  // variable index or constant
+};
+struct Atom {
+  std::string rel;
+  std::vector<Term> args;
+};
+struct Filter {
+  Term a, b;
+  bool equal = false;
+};
+struct Rule {
+  Atom head;
+  std::vector<Atom> body;
+  std::vector<Filter> filters;
+  int nvars = 0;
+};
+
+struct Parser {
+  const char* s;
+  size_t i = 0;
+  std::map<std::string, int> vars;
+  explicit Parser(const char* text) : s(text) {}
+
+  void skip() {
+    for (;;) {
+      while (s[i] && std::isspace((unsigned char)s[i])) i++;
+      if (s[i] == '/' && s[i + 1] == '/') {
+        while (s[i] && s[i] != '\n') i++;
+      } else if (s[i] == '#') {
+        while (s[i] && s[i] != '\n') i++;
+      } else {
+        return;
+      }
+    }
+  }
+  bool eat(const char* tok) {
+    skip();
+    size_t n = std::strlen(tok);
+    if (std::strncmp(s + i, tok, n) == 0) {
+      i += n;
+      return true;
+    }
+    return false;
+  }
+  bool ident(std::string& out) {
+    skip();
+    if (!(std::isalpha((unsigned char)s[i]) || s[i] == '_')) return false;
+    size_t j = i;
+    while (std::isalnum((unsigned char)s[j]) || s[j] == '_') j++;
+    out.assign(s + i, j - i);
+    i = j;
+    return true;
+  }
+  bool term(Term& t) {
+    skip();
+    if (std::isdigit((unsigned char)s[i])) {
+      uint64_t v = 0;
+      while (std::isdigit((unsigned char)s[i])) {
+        v = v * 10 + (s[i] - '0');
+        if (v > 0xFFFFFFFEull) return false;
+        i++;
+      }
+      t.is_var = false;
+      t.value = (uint32_t)v;
+      return true;
+    }
+    std::string name;
+    if (!ident(name)) return false;
+    auto it = vars.find(name);
+    int idx = it == vars.end() ? (int)vars.size() : it->second;
+    if (it == vars.end()) vars[name] = idx;
+    t.is_var = true;
+    t.value = (uint32_t)idx;
+    return true;
+  }
+  bool atom_after_name(const std::string& name, Atom& a) {
+    a.rel = name;
+    if (!eat("(")) return false;
+    do {
+      Term t;
+      if (!term(t)) return false;
+      a.args.push_back(t);
+    } while (eat(","));
+    return eat(")") && a.args.size() <= (size_t)kMaxArity;
+  }
+  bool rule(Rule& r) {
+    vars.clear();
+    std::string name;
+    if (!ident(name) || !atom_after_name(name, r.head)) return false;
+    if (!eat(":-")) return false;
+    do {
+      skip();
+      size_t save = i;
+      std::string nm;
+      if (ident(nm) && (skip(), s[i] == '(')) {
+        Atom a;
+        if (!atom_after_name(nm, a)) return false;
+        r.body.push_back(a);
+      } else {
+        i = save;
+        Filter f;
+        if (!term(f.a)) return false;
+        if (eat("!=")) f.equal = false;
+        else if (eat("==")) f.equal = true;
+        else return false;
+        if (!term(f.b)) return false;
+        r.filters.push_back(f);
+      }
+    } while (eat(","));
+    if (!eat(".")) return false;
+    r.nvars = (int)vars.size();
+    return !r.body.empty();
+  }
+  bool program(std::vector<Rule>& rules) {
+    for (;;) {
+      skip();
+      if (!s[i]) return true;
+      Rule r;
+      if (!rule(r)) return false;
+      rules.push_back(r);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// semiring arithmetic on tags (FP64)
+// ---------------------------------------------------------------------------
+// a "greater than" b in the diff-max-min order: larger value, then smaller id.
+bool dmm_greater(const Tag& a, const Tag& b) {
+  if (a.v != b.v) return a.v > b.v;
+  return a.id < b.id;
+}
+
+Tag otimes(int sr, const Tag& a, const Tag& b) {
+  Tag r;
+  switch (sr) {
+    case UNIT: r.v = 1.0; break;
+    case MAX_MIN: r.v = std::min(a.v, b.v); break;
+    case ADD_MULT: r.v = a.v * b.v; break;
+    case DIFF_MAX_MIN: r = dmm_greater(a, b) ? b : a; break;
+    case DIFF_ADD_MULT:
+      r.v = a.v * b.v;
+      for (auto& kv : a.d) r.d[kv.first] += b.v * kv.second;
+      for (auto& kv : b.d) r.d[kv.first] += a.v * kv.second;
+      break;
+  }
+  return r;
+}
+
+// Accumulator for the (+) over the groundings of one head key.  For the
+// add-mult semirings the clamp is applied once to the plain sum; this equals
+// folding min(1, a + b) pairwise because all tags are non-negative.
+struct Acc {
+  bool any = false;
+  Tag t;
+  double sum = 0.0;
+  Dual dsum;
+};
+
+void acc_add(int sr, Acc& acc, const Tag& g) {
+  if (sr == ADD_MULT || sr == DIFF_ADD_MULT) {
+    acc.sum += g.v;
+    if (sr == DIFF_ADD_MULT)
+      for (auto& kv : g.d) acc.dsum[kv.first] += kv.second;
+    acc.any = true;
+    return;
+  }
+  if (!acc.any) {
+    acc.t = g;
+    acc.any = true;
+    return;
+  }
+  switch (sr) {
+    case UNIT: break;
+    case MAX_MIN: acc.t.v = std::max(acc.t.v, g.v); break;
+    case DIFF_MAX_MIN:
+      if (dmm_greater(g, acc.t)) acc.t = g;
+      break;
+  }
+}
+
+Tag acc_value(int sr, const Acc& acc) {
+  if (sr == ADD_MULT || sr == DIFF_ADD_MULT) {
+    Tag r;
+    r.v = std::min(1.0, acc.sum);
+    if (sr == DIFF_ADD_MULT && !(acc.sum > 1.0)) r.d = acc.dsum;  // clamped: derivative 0
+    return r;
+  }
+  return acc.t;
+}
+
+bool tag_equal(int sr, const Tag& a, const Tag& b) {
+  if (sr == DIFF_MAX_MIN) return a.v == b.v && a.id == b.id;
+  return a.v == b.v;
+}
+
+// ---------------------------------------------------------------------------
+// naive fixpoint for one database (one sample)
+// ---------------------------------------------------------------------------
+using Relation = std::map<Tuple, Tag>;
+using Database = std::map<std::string, Relation>;
+
+struct Engine {
+  int sr;
+  const std::vector<Rule>& rules;
+  Database db;
+  int iterations = 0;
+
+  Engine(int s, const std::vector<Rule>& r) : sr(s), rules(r) {}
+
+  // Enumerate every grounding of rule `r` over `db` (body atoms in written
+  // order, each matched against all facts of its relation consistent with the
+  // variables bound so far).  Calls emit(head tuple, body fact tags).
+  void groundings(const Rule& r, const std::function<void(const Tuple&, const std::vector<const Tag*>&)>& emit) {
+    std::vector<uint32_t> val(r.nvars, 0);
+    std::vector<char> bound(r.nvars, 0);
+    std::vector<const Tag*> tags(r.body.size(), nullptr);
+    // per atom: index from the values of columns bound on entry -> matching facts
+    std::vector<std::vector<int>> bound_cols(r.body.size());
+    {
+      std::vector<char> b(r.nvars, 0);
+      for (size_t j = 0; j < r.body.size(); j++) {
+        const Atom& a = r.body[j];
+        for (size_t c = 0; c < a.args.size(); c++)
+          if (!a.args[c].is_var || b[a.args[c].value]) bound_cols[j].push_back((int)c);
+        for (auto& t : a.args)
+          if (t.is_var) b[t.value] = 1;
+      }
+    }
+    using Key = std::vector<uint32_t>;
+    std::vector<std::map<Key, std::vector<const std::pair<const Tuple, Tag>*>>> index(r.body.size());
+    for (size_t j = 0; j < r.body.size(); j++) {
+      auto it = db.find(r.body[j].rel);
+      if (it == db.end()) return;
+      for (auto& f : it->second) {
+        Key k;
+        for (int c : bound_cols[j]) k.push_back(f.first[c]);
+        index[j][k].push_back(&f);
+      }
+    }
+    std::function<void(size_t)> rec = [&](size_t j) {
+      if (j == r.body.size()) {
+        for (const Filter& f : r.filters) {
+          uint32_t x = f.a.is_var ? val[f.a.value] : f.a.value;
+          uint32_t y = f.b.is_var ? val[f.b.value] : f.b.value;
+          if ((x == y) != f.equal) return;
+        }
+        Tuple h{};
+        for (size_t c = 0; c < r.head.args.size(); c++)
+          h[c] = r.head.args[c].is_var ? val[r.head.args[c].value] : r.head.args[c].value;
+        emit(h, tags);
+        return;
+      }
+      const Atom& a = r.body[j];
+      Key k;
+      for (int c : bound_cols[j]) k.push_back(a.args[c].is_var ? val[a.args[c].value] : a.args[c].value);
+      auto it = index[j].find(k);
+      if (it == index[j].end()) return;
+      for (auto* f : it->second) {
+        std::vector<int> newly;
+        bool ok = true;
+        for (size_t c = 0; c < a.args.size() && ok; c++) {
+          const Term& t = a.args[c];
+          if (!t.is_var) continue;  // constants were part of the index key
+          if (bound[t.value]) {
+            if (val[t.value] != f->first[c]) ok = false;
+          } else {
+            bound[t.value] = 1;
+            val[t.value] = f->first[c];
+            newly.push_back((int)t.value);
+          }
+        }
+        if (ok) {
+          tags[j] = &f->second;
+          rec(j + 1);
+        }
+        for (int v : newly) bound[v] = 0;
+      }
+    };
+    rec(0);
+  }
+
+  // returns 0 on fixpoint, -2 when max_iters iterations did not reach it
+  int run(uint32_t max_iters) {
+    const bool key_policy = (sr == ADD_MULT || sr == DIFF_ADD_MULT);
+    for (uint32_t it = 0; it < max_iters; it++) {
+      std::map<std::string, std::map<Tuple, Acc>> derived;
+      for (const Rule& r : rules) {
+        auto& out = derived[r.head.rel];
+        const Relation* existing = nullptr;
+        auto e = db.find(r.head.rel);
+        if (e != db.end()) existing = &e->second;
+        groundings(r, [&](const Tuple& h, const std::vector<const Tag*>& body) {
+          Acc& acc = out[h];
+          if (key_policy && existing && existing->count(h)) {
+            acc.any = true;  // key already known: its tag is not recomputed
+            return;
+          }
+          Tag g = *body[0];
+          for (size_t j = 1; j < body.size(); j++) g = otimes(sr, g, *body[j]);
+          acc_add(sr, acc, g);
+        });
+      }
+      bool changed = false;
+      for (auto& rel : derived) {
+        Relation& R = db[rel.first];
+        for (auto& kv : rel.second) {
+          auto f = R.find(kv.first);
+          if (f == R.end()) {
+            R[kv.first] = acc_value(sr, kv.second);
+            changed = true;
+          } else if (!key_policy) {
+            Acc merged;
+            acc_add(sr, merged, f->second);
+            acc_add(sr, merged, acc_value(sr, kv.second));
+            Tag nv = acc_value(sr, merged);
+            if (!tag_equal(sr, nv, f->second)) {
+              f->second = nv;
+              changed = true;
+            }
+          }
+        }
+      }
+      iterations = (int)it + 1;
+      if (!changed) return 0;
+    }
+    return -2;
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C interface used by the Python test helpers
+// ---------------------------------------------------------------------------
+struct orc_input {
+  std::string name;
+  uint32_t arity;
+  uint64_t base_id;  // input-fact id of row 0
+  uint64_t n;
+};
+
+struct orc_result {
+  int semiring;
+  int iterations = 0;
+  std::vector<orc_input> inputs;
+  // relation -> sample -> sorted facts
+  std::map<std::string, uint32_t> arity;
+  std::map<std::string, std::map<uint32_t, Relation>> out;
+};
+
+extern "C" {
+
+const char* orc_error(void) { return g_err.c_str(); }
+
+int orc_run(const char* program, int semiring, int n_inputs, const char* const* names, const uint32_t* arities,
+            const uint64_t* nrows, const uint32_t* const* cols, const double* const* tags,
+            const uint32_t* const* samples, uint32_t max_iters, orc_result** result) {
+  g_err.clear();
+  if (!program || !result || semiring < 0 || semiring > 4 || n_inputs < 0) {
+    g_err = "bad argument";
+    return -3;
+  }
+  std::vector<Rule> rules;
+  Parser p(program);
+  if (!p.program(rules)) {
+    g_err = "parse error near offset " + std::to_string(p.i);
+    return -1;
+  }
+  auto* res = new orc_result();
+  res->semiring = semiring;
+  for (auto& r : rules) {
+    res->arity[r.head.rel] = (uint32_t)r.head.args.size();
+    for (auto& a : r.body) res->arity[a.rel] = (uint32_t)a.args.size();
+  }
+  // split loaded facts by sample; duplicates merged with (+)
+  std::map<uint32_t, std::map<std::string, std::map<Tuple, Acc>>> loaded;
+  uint64_t base = 0;
+  for (int k = 0; k < n_inputs; k++) {
+    if (arities[k] < 1 || arities[k] > (uint32_t)kMaxArity) {
+      delete res;
+      g_err = "bad arity";
+      return -3;
+    }
+    res->inputs.push_back({names[k], arities[k], base, nrows[k]});
+    res->arity[names[k]] = arities[k];
+    for (uint64_t r = 0; r < nrows[k]; r++) {
+      Tuple t{};
+      for (uint32_t c = 0; c < arities[k]; c++) t[c] = cols[k][c * nrows[k] + r];
+      uint32_t s = samples && samples[k] ? samples[k][r] : 0;
+      Tag g;
+      g.v = tags && tags[k] ? tags[k][r] : 1.0;
+      if (semiring == UNIT) g.v = 1.0;
+      const bool differentiable = tags && tags[k];
+      if (semiring == DIFF_MAX_MIN && differentiable) g.id = (uint32_t)(base + r);
+      if (semiring == DIFF_ADD_MULT && differentiable) g.d[(uint32_t)(base + r)] = 1.0;
+      acc_add(semiring, loaded[s][names[k]][t], g);
+    }
+    base += nrows[k];
+  }
+  if (loaded.empty()) loaded[0];
+  int max_it = 0;
+  for (auto& smp : loaded) {
+    Engine e(semiring, rules);
+    for (auto& rel : smp.second)
+      for (auto& kv : rel.second) e.db[rel.first][kv.first] = acc_value(semiring, kv.second);
+    int rc = e.run(max_iters);
+    if (rc != 0) {
+      delete res;
+      g_err = "max_iters reached";
+      return rc;
+    }
+    max_it = std::max(max_it, e.iterations);
+    for (auto& rel : e.db) res->out[rel.first][smp.first] = std::move(rel.second);
+  }
+  res->iterations = max_it;
+  *result = res;
+  return 0;
+}
+
+int orc_iterations(const orc_result* r) { return r ? r->iterations : -1; }
+
+int64_t orc_size(const orc_result* r, const char* rel) {
+  auto it = r->out.find(rel);
+  if (it == r->out.end()) return r->arity.count(rel) ? 0 : -1;
+  int64_t n = 0;
+  for (auto& s : it->second) n += (int64_t)s.second.size();
+  return n;
+}
+
+int orc_arity(const orc_result* r, const char* rel) {
+  auto it = r->arity.find(rel);
+  return it == r->arity.end() ? -1 : (int)it->second;
+}
+
+// cols: arity x n column-major; tags, samples nullable.  Sorted by (sample, cols).
+int orc_read(const orc_result* r, const char* rel, uint32_t* cols, double* tags, uint32_t* samples) {
+  auto it = r->out.find(rel);
+  if (it == r->out.end()) return 0;
+  uint32_t ar = r->arity.at(rel);
+  int64_t n = orc_size(r, rel);
+  int64_t i = 0;
+  for (auto& s : it->second)
+    for (auto& kv : s.second) {
+      for (uint32_t c = 0; c < ar; c++) cols[c * n + i] = kv.first[c];
+      if (tags) tags[i] = kv.second.v;
+      if (samples) samples[i] = s.first;
+      i++;
+    }
+  return 0;
+}
+
+// For diff-max-min: the input-fact id (global row index over all inputs in
+// load order) that bounds each output tag, or 0xFFFFFFFF.
+int orc_read_ids(const orc_result* r, const char* rel, uint32_t* ids) {
+  auto it = r->out.find(rel);
+  if (it == r->out.end()) return 0;
+  int64_t i = 0;
+  for (auto& s : it->second)
+    for (auto& kv : s.second) ids[i++] = kv.second.id;
+  return 0;
+}
+
+// Vector-Jacobian product: grad_in[k][row] += sum_o grad_out[o] * d tag_o / d p_(k,row)
+// with o running over `rel` in read order.  Only for the diff semirings.
+int orc_vjp(const orc_result* r, const char* rel, const double* grad_out, double* const* grad_in) {
+  if (r->semiring != DIFF_MAX_MIN && r->semiring != DIFF_ADD_MULT) return -4;
+  auto it = r->out.find(rel);
+  if (it == r->out.end()) return 0;
+  auto deposit = [&](uint32_t id, double g) {
+    for (size_t k = 0; k < r->inputs.size(); k++) {
+      const orc_input& in = r->inputs[k];
+      if (id >= in.base_id && id < in.base_id + in.n) {
+        if (grad_in[k]) grad_in[k][id - in.base_id] += g;
+        return;
+      }
+    }
+  };
+  int64_t i = 0;
+  for (auto& s : it->second)
+    for (auto& kv : s.second) {
+      double g = grad_out[i++];
+      if (r->semiring == DIFF_MAX_MIN) {
+        if (kv.second.id != kNoId) deposit(kv.second.id, g);
+      } else {
+        for (auto& d : kv.second.d) deposit(d.first, g * d.second);
+      }
+    }
+  return 0;
+}
+
+void orc_free(orc_result* r) { delete r; }
+
+}  // extern "C"

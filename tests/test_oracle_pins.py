@@ -1,0 +1,317 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics:
+closed forms, textbook algorithms, brute-force possible worlds, finite
+differences and invariants.  No expected value here comes from the engine."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_21937_gb300 import workloads as W
+from tests import pins
+
+
+def rel_set(rel):
+    return set(map(tuple, rel.cols.T.tolist()))
+
+
+# ----------------------------------------------------------------------------
+# unit semiring: least fixpoint of the discrete program (Alg. 1; Sec. 3.1)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 5, 40])
+def test_tc_chain_closed_form(n):
+    a, b = W.ktree_chain(max(n, 2))
+    a, b = a[: n - 1], b[: n - 1]
+    if n == 1:
+        a = b = np.zeros(0, np.uint32)
+    r = oracle.run(W.TC_PROGRAM, {"edge": ((a, b),)})
+    path = rel_set(r.relation("path"))
+    assert len(path) == n * (n - 1) // 2
+    assert path == {(i, j) for i in range(n) for j in range(i + 1, n)}
+
+
+@pytest.mark.parametrize("n", [1, 3, 17])
+def test_tc_cycle_and_complete_closed_form(n):
+    a = np.arange(n, dtype=np.uint32)
+    b = (a + 1) % n
+    r = oracle.run(W.TC_PROGRAM, {"edge": ((a, b),)})
+    assert len(rel_set(r.relation("path"))) == n * n
+    x, y = np.meshgrid(np.arange(n), np.arange(n))
+    keep = x != y
+    r = oracle.run(W.TC_PROGRAM, {"edge": ((x[keep].astype(np.uint32), y[keep].astype(np.uint32)),)})
+    # complete digraph without loops: every ordered pair, loops via 2-cycles (n >= 2)
+    assert len(rel_set(r.relation("path"))) == (n * n if n >= 2 else 0)
+
+
+def test_tc_matches_bfs_on_random_graphs():
+    for n, m, seed in [(30, 60, 11), (200, 500, 12), (50, 400, 13)]:
+        a, b = W.erdos_renyi(n, m, seed_index=seed)
+        r = oracle.run(W.TC_PROGRAM, {"edge": ((a, b),)})
+        assert rel_set(r.relation("path")) == pins.bfs_closure(a, b)
+
+
+def test_sg_tree_depth_closed_form():
+    parent, child, depth = W.random_tree(600, seed_index=21)
+    r = oracle.run(W.SG_PROGRAM, {"parent": ((parent, child),)})
+    sg = r.relation("sg")
+    assert sg.cols.shape[1] == pins.same_generation_closed_form(depth)
+    x, y = sg.cols
+    assert np.all(depth[x] == depth[y]) and np.all(x != y) and np.all(depth[x] >= 1)
+
+
+@pytest.mark.parametrize("k,levels", [(2, 4), (3, 3)])
+def test_sg_perfect_tree(k, levels):
+    parent, child = W.perfect_tree(k, levels)
+    r = oracle.run(W.SG_PROGRAM, {"parent": ((parent, child),)})
+    expect = sum(k ** d * (k ** d - 1) for d in range(1, levels + 1))
+    assert r.relation("sg").cols.shape[1] == expect
+
+
+def test_andersen_matches_worklist_solver():
+    A = W.andersen_program(3000, 8000, seed_index=31)
+    inputs = {k: ((v[0], v[1]),) for k, v in A.items()}
+    r = oracle.run(W.ANDERSEN_PROGRAM, inputs)
+    expect = pins.andersen_worklist(A["addr"], A["assign"], A["load"], A["store"])
+    got = rel_set(r.relation("pt"))
+    assert len(expect) > 1000
+    assert got == expect
+
+
+def test_filters_constants_and_repeated_variables():
+    edge = (np.array([0, 1, 1, 2, 3], np.uint32), np.array([1, 1, 2, 2, 0], np.uint32))
+    prog = ("loop(x) :- edge(x,x).\n"
+            "fromzero(y) :- edge(0,y).\n"
+            "twohop(x,z) :- edge(x,y), edge(y,z), x != z.\n"
+            "same(x) :- edge(x,y), x == 1.\n")
+    r = oracle.run(prog, {"edge": (edge,)})
+    assert rel_set(r.relation("loop")) == {(1,), (2,)}
+    assert rel_set(r.relation("fromzero")) == {(1,)}
+    E = set(zip(edge[0].tolist(), edge[1].tolist()))
+    two = {(x, z) for (x, y) in E for (y2, z) in E if y == y2 and x != z}
+    assert rel_set(r.relation("twohop")) == two
+    assert rel_set(r.relation("same")) == {(1,)}
+
+
+def test_duplicate_input_rows_are_merged():
+    a = np.array([0, 0, 1], np.uint32)
+    b = np.array([1, 1, 2], np.uint32)
+    r = oracle.run(W.TC_PROGRAM, {"edge": ((a, b), np.array([0.2, 0.7, 0.5]))}, "max_min")
+    p = r.relation("path")
+    d = {tuple(c): t for c, t in zip(p.cols.T.tolist(), p.tags)}
+    assert d[(0, 1)] == 0.7 and d[(0, 2)] == 0.5
+    r = oracle.run(W.TC_PROGRAM, {"edge": ((a, b), np.array([0.2, 0.7, 0.5]))}, "add_mult")
+    p = r.relation("path")
+    d = {tuple(c): t for c, t in zip(p.cols.T.tolist(), p.tags)}
+    assert d[(0, 1)] == pytest.approx(0.9) and d[(0, 2)] == pytest.approx(0.45)
+    r = oracle.run(W.TC_PROGRAM, {"edge": ((a, b), np.array([0.6, 0.7, 0.5]))}, "add_mult")
+    p = r.relation("path")
+    d = {tuple(c): t for c, t in zip(p.cols.T.tolist(), p.tags)}
+    assert d[(0, 1)] == 1.0  # clamped sum
+
+
+# ----------------------------------------------------------------------------
+# max-min-prob (semiring table of Sec. 3.1): possible worlds and widest paths
+# ----------------------------------------------------------------------------
+
+def small_graphs():
+    out = []
+    for m, seed in [(6, 41), (9, 42), (12, 43)]:
+        s = W.stream(900 + seed)
+        n = 5
+        src = s.below(m, n)
+        dst = s.below(m, n)
+        p = s.prob(m).astype(np.float64)
+        out.append((src, dst, p))
+    # a graph with equal probabilities to exercise the id tie-break
+    out.append((np.array([0, 0, 1, 2], np.uint32), np.array([1, 2, 3, 3], np.uint32), np.array([0.5] * 4)))
+    return out
+
+
+@pytest.mark.parametrize("g", range(4))
+def test_maxmin_possible_worlds(g):
+    src, dst, p = small_graphs()[g]
+    inputs = {"edge": ((src, dst), p), "start": ((np.array([0], np.uint32),),)}
+    truth = pins.possible_worlds_maxmin_reach(src, dst, p, 0)
+    for sr in ("max_min", "diff_max_min"):
+        r = oracle.run(W.REACH_PROGRAM, inputs, sr)
+        rel = r.relation("reach")
+        got = {int(c): t for c, t in zip(rel.cols[0], rel.tags)}
+        assert set(got) == set(truth)
+        for y, (v, _) in truth.items():
+            assert got[y] == v
+        if sr == "diff_max_min":
+            ids = r.ids("reach")
+            for c, i in zip(rel.cols[0], ids):
+                want = truth[int(c)][1]
+                # ids index the loaded rows in load order: edge rows first
+                assert (i if i != 0xFFFFFFFF else 2 ** 40) == want
+
+
+def test_maxmin_matches_widest_path_on_grid():
+    g = W.grid_reach_instance(12, sub=5)
+    src, dst, p = g["edge"]
+    r = oracle.run(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, "max_min")
+    rel = r.relation("reach")
+    best = pins.widest_path(src, dst, p, 0)
+    got = {int(c): t for c, t in zip(rel.cols[0], rel.tags)}
+    assert set(got) == set(best)
+    for y in best:
+        assert got[y] == pytest.approx(best[y], abs=0)
+    vals = set(np.asarray(p, np.float64).tolist()) | {1.0}
+    assert set(got.values()) <= vals
+
+
+def test_maxmin_chain_is_min_of_edges():
+    n = 9
+    a, b = W.ktree_chain(n)
+    p = W.stream(77).prob(n - 1).astype(np.float64)
+    r = oracle.run(W.TC_PROGRAM, {"edge": ((a, b), p)}, "max_min")
+    rel = r.relation("path")
+    for (x, y), t in zip(rel.cols.T.tolist(), rel.tags):
+        assert t == p[x:y].min()
+
+
+# ----------------------------------------------------------------------------
+# add-mult-prob: layered DP, lattice-path closed form, exact probability on trees
+# ----------------------------------------------------------------------------
+
+def test_addmult_reach_equals_layered_dp():
+    for side, sub in [(7, 1), (16, 2)]:
+        g = W.grid_reach_instance(side, sub=sub)
+        src, dst, p = g["edge"]
+        r = oracle.run(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, "add_mult")
+        rel = r.relation("reach")
+        t, dist = pins.layered_reach_dp(src, dst, p, 0)
+        got = {int(c): v for c, v in zip(rel.cols[0], rel.tags)}
+        assert set(got) == set(t)
+        for y in t:
+            assert got[y] == pytest.approx(t[y], rel=1e-12)
+        assert r.iterations == max(dist.values()) + 2  # one per layer, the source's rule, one empty
+
+
+def test_addmult_grid_lattice_paths_closed_form():
+    side = 6
+    u, v = W.grid_edges(side)
+    src, dst, tags = W.directed_from_undirected(u, v, np.full(len(u), 0.5, np.float32))
+    r = oracle.run(W.REACH_PROGRAM, {"edge": ((src, dst), tags.astype(np.float64)),
+                                     "start": ((np.array([0], np.uint32),),)}, "add_mult")
+    rel = r.relation("reach")
+    for c, t in zip(rel.cols[0], rel.tags):
+        dx, dy = int(c) % side, int(c) // side
+        assert t == pytest.approx(math.comb(dx + dy, dx) * 0.5 ** (dx + dy), rel=1e-14)
+
+
+def test_addmult_tree_equals_possible_worlds_probability():
+    # directed tree: one derivation per fact, so the tag is the exact probability
+    parent, child = W.perfect_tree(2, 3)
+    p = W.stream(78).prob(len(parent)).astype(np.float64)
+    r = oracle.run(W.REACH_PROGRAM, {"edge": ((parent, child), p), "start": ((np.array([0], np.uint32),),)},
+                   "add_mult")
+    exact = pins.possible_worlds_probability(parent, child, p, 0)
+    rel = r.relation("reach")
+    got = {int(c): t for c, t in zip(rel.cols[0], rel.tags)}
+    assert set(got) == set(exact)
+    for y in exact:
+        assert got[y] == pytest.approx(exact[y], rel=1e-12)
+
+
+def test_addmult_counts_each_grounding_once_in_nonlinear_rule():
+    # chain 0-1-2-3, every label 0, comp(0,0,0), p = 0.3: kin(0,0,2) first appears
+    # at iteration 2 with one grounding (0.09); kin(0,0,3) first appears at
+    # iteration 3 with two groundings, kin(0,0,1)+kin(0,1,3) and kin(0,0,2)+kin(0,2,3),
+    # each 0.3 * 0.09, so its tag is their sum 0.054 (no clamp)
+    fact = (np.zeros(3, np.uint32), np.array([0, 1, 2], np.uint32), np.array([1, 2, 3], np.uint32))
+    comp = (np.zeros(1, np.uint32), np.zeros(1, np.uint32), np.zeros(1, np.uint32))
+    r = oracle.run(W.KIN_PROGRAM, {"fact": (fact, np.full(3, 0.3)), "comp": (comp,)}, "add_mult")
+    rel = r.relation("kin")
+    d = {tuple(c): t for c, t in zip(rel.cols.T.tolist(), rel.tags)}
+    assert d[(0, 0, 2)] == pytest.approx(0.09)
+    # kin(0,0,3) appears at iteration 3 only via (0,2)+(2,3) and (0,1)+(1,3): 2 * 0.027
+    assert d[(0, 0, 3)] == pytest.approx(2 * 0.027)
+
+
+# ----------------------------------------------------------------------------
+# invariants across semirings
+# ----------------------------------------------------------------------------
+
+def test_key_sets_agree_across_semirings_and_tag_ranges():
+    g = W.grid_reach_instance(9, sub=3)
+    src, dst, p = g["edge"]
+    inputs = {"edge": ((src, dst), p), "start": (g["start"],)}
+    keys = None
+    for sr in ("unit", "max_min", "add_mult", "diff_max_min", "diff_add_mult"):
+        rel = oracle.run(W.REACH_PROGRAM, inputs, sr).relation("reach")
+        k = rel_set(rel)
+        keys = k if keys is None else keys
+        assert k == keys
+        assert np.all(rel.tags >= 0) and np.all(rel.tags <= 1)
+    assert len(keys) == 81
+
+
+def test_batched_equals_per_sample():
+    B = W.batched_instance(4)
+    e = B["edge"]
+    inputs = {"edge": ((e[0], e[1]), e[2], e[3]), "start": ((B["start"][0],), None, B["start"][2])}
+    both = oracle.run(W.REACH_PROGRAM, inputs, "add_mult").relation("reach")
+    for i in range(4):
+        sel = e[3] == i
+        one = oracle.run(W.REACH_PROGRAM, {"edge": ((e[0][sel], e[1][sel]), e[2][sel]),
+                                           "start": ((np.array([0], np.uint32),),)}, "add_mult").relation("reach")
+        m = both.samples == i
+        assert np.array_equal(both.cols[:, m], one.cols)
+        assert np.array_equal(both.tags[m], one.tags)
+
+
+# ----------------------------------------------------------------------------
+# gradients: forward-mode duals vs FP64 central finite differences
+# ----------------------------------------------------------------------------
+
+def _fd_check(program, inputs, rel_name, sr, gout, which, h=1e-6, tol=1e-4, skip=None):
+    res = oracle.run(program, inputs, sr)
+    grads = res.vjp({rel_name: gout})["edge"]
+    base_rel = res.relation(rel_name)
+    for e in which:
+        if skip is not None and skip(e):
+            continue
+        vals = []
+        for sign in (+1, -1):
+            cols, p = inputs["edge"][0], np.array(inputs["edge"][1], np.float64)
+            p[e] += sign * h
+            inp = dict(inputs)
+            inp["edge"] = (cols, p)
+            rel = oracle.run(program, inp, sr.replace("diff_", "")).relation(rel_name)
+            assert np.array_equal(rel.cols, base_rel.cols)
+            vals.append(float(np.dot(rel.tags, gout)))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert grads[e] == pytest.approx(fd, abs=tol, rel=tol), (e, grads[e], fd)
+
+
+def test_addmult_gradient_matches_finite_differences():
+    side = 8
+    g = W.grid_reach_instance(side, sub=9)
+    src, dst, p = g["edge"]
+    p = p.astype(np.float64) * 0.5  # keep sums away from the clamp
+    inputs = {"edge": ((src, dst), p), "start": (g["start"],)}
+    n_out = oracle.run(W.REACH_PROGRAM, inputs, "add_mult").relation("reach").cols.shape[1]
+    gout = W.stream(55).normal(n_out)
+    _fd_check(W.REACH_PROGRAM, inputs, "reach", "diff_add_mult", gout, range(len(src)))
+
+
+def test_maxmin_gradient_matches_finite_differences():
+    # one independent probability per directed fact, so each fact is its own input
+    side = 6
+    u, v = W.grid_edges(side)
+    src, dst, _ = W.directed_from_undirected(u, v, np.zeros(len(u), np.float32))
+    p = W.stream(57).prob(len(src)).astype(np.float64)
+    inputs = {"edge": ((src, dst), p), "start": ((np.array([0], np.uint32),),)}
+    n_out = oracle.run(W.REACH_PROGRAM, inputs, "max_min").relation("reach").cols.shape[1]
+    gout = W.stream(56).normal(n_out)
+
+    def near_tie(e):
+        d = np.abs(p - p[e])
+        d[e] = np.inf
+        return d.min() < 2e-6
+
+    _fd_check(W.REACH_PROGRAM, inputs, "reach", "diff_max_min", gout, range(len(src)), skip=near_tie)
