@@ -1,0 +1,162 @@
+/*
+ * lobster.h -- C ABI of the GB300 semiring-Datalog fixpoint engine.
+ *
+ * The engine evaluates positive Datalog rules over columnar u32 relations whose
+ * tuples carry provenance-semiring tags, by semi-naive fixpoint iteration on
+ * one GPU (Lobster, Sec. 3 and Algorithm 1).  Every step of the iteration runs
+ * in hand-written CUDA kernels; the host only plans and sequences them.
+ *
+ * Conventions for every function below:
+ *   - The return value is a status: LOB_OK (0) or a negative LOB_E_* code.
+ *     No function aborts or exits; lob_last_error() gives a one-line message.
+ *   - `mem` says where caller buffers live: LOB_MEM_HOST (pageable or pinned
+ *     host memory) or LOB_MEM_DEVICE (device memory of the engine's device).
+ *   - The engine copies what it is given and owns all its device state; the
+ *     caller keeps ownership of every buffer it passes.
+ *   - Work is ordered on the CUDA stream given to lob_create; calls that
+ *     return data to the caller synchronise that stream before returning.
+ *   - An engine is not thread-safe; use one engine per host thread.
+ */
+#ifndef LOBSTER_H
+#define LOBSTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lob_engine lob_engine;
+
+/* status codes */
+#define LOB_OK 0
+#define LOB_E_ARG (-1)          /* invalid argument (null pointer, bad arity, duplicate name, ...) */
+#define LOB_E_PARSE (-2)        /* rule text does not parse */
+#define LOB_E_UNKNOWN_REL (-3)  /* relation id or name not declared */
+#define LOB_E_UNSAFE_RULE (-4)  /* head or filter variable not bound by a body atom */
+#define LOB_E_OOM (-5)          /* device allocation failed; engine state is unchanged */
+#define LOB_E_MAXITER (-6)      /* max_iters reached before the fixpoint; state is kept and readable */
+#define LOB_E_TIMEOUT (-7)      /* a bounded device wait gave up; results of the run are invalid */
+#define LOB_E_CUDA (-8)         /* a CUDA runtime call failed */
+#define LOB_E_CAPACITY (-9)     /* output buffer too small; *n_out holds the required row count */
+#define LOB_E_STATE (-10)       /* call not valid in the engine's current state */
+#define LOB_E_KEY_WIDTH (-11)   /* a relation's packed key (sample id + columns) needs more than 64 bits */
+
+/* provenance semirings (Sec. 3.1 semiring table; Sec. 3.4 lists the probabilistic ones) */
+#define LOB_UNIT 0           /* discrete: every tag is 1 (no tags stored) */
+#define LOB_MAX_MIN 1        /* max-min-prob: (+) = max, (x) = min on [0,1] */
+#define LOB_ADD_MULT 2       /* add-mult-prob: (+) = min(1, a+b), (x) = a*b on [0,1] */
+#define LOB_DIFF_MAX_MIN 3   /* differentiable max-min: gradient 1 to the bounding input fact */
+#define LOB_DIFF_ADD_MULT 4  /* differentiable add-mult: exact reverse-mode gradient */
+
+#define LOB_MEM_HOST 0
+#define LOB_MEM_DEVICE 1
+
+/* Optional device allocator.  alloc returns NULL on failure (the engine then
+ * reports LOB_E_OOM).  Both are called with the engine's stream. */
+typedef struct lob_alloc {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*release)(void* ptr, size_t bytes, void* stream, void* ctx);
+  void* ctx;
+} lob_alloc;
+
+/* Statistics of the last lob_run_to_fixpoint. */
+typedef struct lob_stats {
+  uint32_t iterations;      /* iterations executed, counting the final one that found nothing new */
+  uint32_t semiring;
+  uint64_t derived;         /* facts in relations that are the head of some rule, at the end of the run */
+  uint64_t candidates;      /* candidate tuples emitted by all joins, summed over iterations */
+  uint64_t new_facts;       /* facts added or improved, summed over iterations */
+  uint64_t peak_bytes;      /* peak device memory held by the engine during the run */
+  double ms;                /* wall time of the run on the engine's stream (CUDA events) */
+  uint64_t kernel_launches; /* kernels launched by the run */
+} lob_stats;
+
+/* Create an engine on the current CUDA device.  `alloc` may be NULL (stream-
+ * ordered cudaMallocAsync is used); `cuda_stream` is a cudaStream_t or NULL
+ * for the legacy default stream. */
+int lob_create(lob_engine** out, const lob_alloc* alloc, void* cuda_stream);
+
+/* Release all device memory of the engine and the engine itself.  NULL is ignored. */
+void lob_destroy(lob_engine* e);
+
+/* Message of the last failing call on this engine ("" if none).  With e == NULL,
+ * the message of the last failed lob_create. */
+const char* lob_last_error(const lob_engine* e);
+
+/* Declare relation `name` (identifier: letter or '_' then letters, digits, '_')
+ * with 1 <= arity <= 8 columns.  Relations are the columnar tables of Sec. 3.3.
+ * *rel_id receives the relation's id (0, 1, 2, ... in declaration order).
+ * LOB_E_ARG for a duplicate name or bad arity. */
+int lob_declare_relation(lob_engine* e, const char* name, uint32_t arity, uint32_t* rel_id);
+
+/* Look up a declared relation by name. */
+int lob_relation_id(const lob_engine* e, const char* name, uint32_t* rel_id);
+
+/* Append n input facts to relation `rel` (the `load` of Sec. 3.3's table).
+ *   cols       arity x n u32, column-major: column c of row r at cols[c*n + r]
+ *   tags       n floats in [0,1], or NULL for tag 1; for the diff semirings a
+ *              non-NULL tags array makes these rows differentiable inputs
+ *   sample_ids n u32 sample ids (batched evaluation, Sec. 4.3), or NULL for sample 0
+ * Rows are numbered in load order across calls; that numbering is the
+ * alignment of lob_backward's per-relation gradients.  Duplicate rows are
+ * merged with the semiring's (+) when the run starts.  Valid before the first
+ * lob_run_to_fixpoint or after lob_reset. */
+int lob_load_relation(lob_engine* e, uint32_t rel, const uint32_t* cols, const float* tags,
+                      const uint32_t* sample_ids, uint64_t n, int mem);
+
+/* Add one rule, e.g. "path(x,z) :- path(x,y), edge(y,z)."  Terms are variables
+ * (identifiers) or u32 decimal constants; the body is a list of atoms and
+ * filters `a != b` / `a == b`.  Several rules may share a head (union).  Every
+ * head and filter variable must occur in a body atom (LOB_E_UNSAFE_RULE).
+ * The RAM operators this covers (Fig. 2): projection with permutation and
+ * constants, selection by (in)equality, n-way join, union. */
+int lob_add_rule(lob_engine* e, const char* text);
+
+/* Evaluate all rules to the least fixpoint with the given semiring (Algorithm 1
+ * with the semi-naive arms of the appendix's Join rule).  At most max_iters
+ * iterations run; on LOB_E_MAXITER the partial state stays readable.  A second
+ * call needs lob_reset first (LOB_E_STATE).  `stats` may be NULL. */
+int lob_run_to_fixpoint(lob_engine* e, int semiring, uint32_t max_iters, lob_stats* stats);
+
+/* Number of facts of `rel` after the run (or after loading, before it). */
+int lob_relation_size(lob_engine* e, uint32_t rel, uint64_t* n);
+
+/* Copy relation `rel` out, sorted by (sample id, column 0, column 1, ...).
+ *   cols       arity x capacity u32, column-major with stride `capacity`
+ *   tags       capacity floats or NULL (all 1 under LOB_UNIT)
+ *   sample_ids capacity u32 or NULL
+ * If the relation has more than `capacity` facts nothing is written,
+ * *n_out receives the size and LOB_E_CAPACITY is returned. */
+int lob_read_relation(lob_engine* e, uint32_t rel, uint32_t* cols, float* tags, uint32_t* sample_ids,
+                      uint64_t capacity, uint64_t* n_out, int mem);
+
+/* Reverse-mode gradient after a LOB_DIFF_* run (Sec. 3.4: differentiable
+ * versions of the probabilistic semirings).
+ *   grad_tags   d loss / d tag for every fact of out_rel, in lob_read_relation order
+ *   grad_inputs array indexed by relation id (length = number of declared
+ *               relations); entry k is NULL or points to one float per loaded
+ *               row of relation k, in load order; gradients are ADDED there.
+ * diff-max-min: each output's gradient goes to the input row that bounds its
+ * tag.  diff-add-mult: adjoints flow back through every recorded derivation
+ * (recomputed per iteration), zero through a clamped (+).  May be called once
+ * per output relation; LOB_E_STATE without a diff run. */
+int lob_backward(lob_engine* e, uint32_t out_rel, const float* grad_tags, float* const* grad_inputs, int mem);
+
+/* Drop all derived state and loaded facts but keep declarations and rules. */
+int lob_reset(lob_engine* e);
+
+/* Engine options (key, value):
+ *   "join_index"   0 auto, 1 dense offset table, 2 binary search   (default 0)
+ *   "dense_bits"   largest join-prefix width, in bits, indexed densely (default 24)
+ *   "radix_bits"   bits per radix-sort pass, 4..11                  (default 8)
+ *   "sync_check"   1: check CUDA errors after every kernel (debug)   (default 0)
+ * LOB_E_ARG for an unknown key or a value out of range. */
+int lob_set_option(lob_engine* e, const char* key, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOBSTER_H */

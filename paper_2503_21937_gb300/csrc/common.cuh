@@ -1,0 +1,209 @@
+// Shared device definitions of the fixpoint engine: packed-key layouts, the
+// semiring tag arithmetic, and warp/block scan helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+typedef unsigned int u32;
+typedef unsigned long long u64;
+
+#define LOB_DEV __device__ __forceinline__
+#define LOB_HD __host__ __device__ __forceinline__
+
+constexpr int kMaxArity = 8;
+constexpr int kMaxSlots = 16;   // variables of one rule
+constexpr int kMaxFilters = 8;
+
+// Every key type's all-ones value is never a valid packed key: each field is
+// stored with enough bits that its value is below the field's all-ones value.
+// Candidates dropped by a filter carry this key, sort last, and are removed by
+// the unique step.
+template <class K> LOB_HD K invalid_key() { return ~K(0); }
+
+// ---------------------------------------------------------------------------
+// packed keys
+// ---------------------------------------------------------------------------
+// A relation view packs (sample id, c_0, ..., c_{a-1}) into one integer, sample
+// in the top field, view column 0 next, the last view column in the low bits,
+// so that integer order is the lexicographic order of the columnar table
+// (Sec. 3.3: an arity-n relation is n column registers; Sec. 4.3 puts the
+// sample register in front).
+struct Layout {
+  int arity;
+  int bits;               // total key bits
+  int sshift, swidth;     // sample field (swidth 0: unbatched)
+  int shift[kMaxArity];   // view column j
+  int width[kMaxArity];
+  int key64;              // key stored as u64 (bits > 32) or u32
+};
+
+LOB_HD u64 field_of(u64 key, int shift, int width) {
+  return (key >> shift) & ((width >= 64) ? ~0ull : ((1ull << width) - 1ull));
+}
+// number of key bits below the first `p` view columns
+LOB_HD int rest_shift(const Layout& L, int p) { return p == 0 ? L.sshift : L.shift[p - 1]; }
+LOB_HD u64 shr64(u64 v, int s) { return s >= 64 ? 0ull : (v >> s); }
+LOB_HD u64 shl64(u64 v, int s) { return s >= 64 ? 0ull : (v << s); }
+
+LOB_DEV u64 load_key(const void* keys, int key64, u64 i) {
+  return key64 ? reinterpret_cast<const u64*>(keys)[i] : (u64)reinterpret_cast<const u32*>(keys)[i];
+}
+LOB_DEV void store_key(void* keys, int key64, u64 i, u64 v) {
+  if (key64) reinterpret_cast<u64*>(keys)[i] = v;
+  else reinterpret_cast<u32*>(keys)[i] = (u32)v;
+}
+LOB_DEV u64 invalid_of(int key64) { return key64 ? ~0ull : 0xFFFFFFFFull; }
+
+// ---------------------------------------------------------------------------
+// semirings (Sec. 3.1 table; Sec. 3.4).  `Stored` is the tag kept with a fact;
+// `Cand` is the tag carried by candidates and join intermediates.
+// ---------------------------------------------------------------------------
+enum SemiringId { SR_UNIT = 0, SR_MAX_MIN = 1, SR_ADD_MULT = 2, SR_DIFF_MAX_MIN = 3, SR_DIFF_ADD_MULT = 4 };
+
+struct SemUnit {
+  typedef u32 Stored;
+  typedef u32 Cand;
+  static constexpr bool kTags = false;
+  static constexpr bool kIdempotent = true;
+  LOB_DEV static Cand one() { return 1u; }
+  LOB_DEV static Cand from_stored(Stored) { return 1u; }
+  LOB_DEV static Cand mul(Cand, Cand) { return 1u; }
+  LOB_DEV static Cand add(Cand, Cand) { return 1u; }
+  LOB_DEV static Stored store(Cand) { return 1u; }
+  LOB_DEV static bool better(Stored, Stored) { return false; }
+};
+
+// max-min-prob: (+) = max, (x) = min; both exact in f32.
+struct SemMaxMin {
+  typedef float Stored;
+  typedef float Cand;
+  static constexpr bool kTags = true;
+  static constexpr bool kIdempotent = true;
+  LOB_DEV static Cand one() { return 1.0f; }
+  LOB_DEV static Cand from_stored(Stored s) { return s; }
+  LOB_DEV static Cand mul(Cand a, Cand b) { return fminf(a, b); }
+  LOB_DEV static Cand add(Cand a, Cand b) { return fmaxf(a, b); }
+  LOB_DEV static Stored store(Cand c) { return c; }
+  LOB_DEV static bool better(Stored a, Stored b) { return a > b; }
+};
+
+// add-mult-prob: (x) = a*b, (+) = min(1, a+b).  Because every tag is
+// non-negative, min(1, .) folded pairwise equals one clamp of the plain sum, so
+// candidates carry unclamped FP64 products/sums and the clamp and the single
+// rounding to f32 happen when a fact is stored.
+struct SemAddMult {
+  typedef float Stored;
+  typedef double Cand;
+  static constexpr bool kTags = true;
+  static constexpr bool kIdempotent = false;
+  LOB_DEV static Cand one() { return 1.0; }
+  LOB_DEV static Cand from_stored(Stored s) { return (double)s; }
+  LOB_DEV static Cand mul(Cand a, Cand b) { return a * b; }
+  LOB_DEV static Cand add(Cand a, Cand b) { return a + b; }
+  LOB_DEV static Stored store(Cand c) { return (float)fmin(1.0, c); }
+  LOB_DEV static bool better(Stored, Stored) { return false; }
+};
+
+// diff-max-min: a tag is (v, id) ordered by v, ties to the smaller input-fact
+// id.  Packed as (bits(v) << 32) | (0xFFFFFFFF - id): v >= 0, so the IEEE bits
+// order like the values, and u64 order is the tag order; (+) = max, (x) = min.
+struct SemDiffMaxMin {
+  typedef u64 Stored;
+  typedef u64 Cand;
+  static constexpr bool kTags = true;
+  static constexpr bool kIdempotent = true;
+  LOB_DEV static Cand one() { return ((u64)__float_as_uint(1.0f) << 32) | 0ull; }
+  LOB_DEV static Cand from_stored(Stored s) { return s; }
+  LOB_DEV static Cand mul(Cand a, Cand b) { return a < b ? a : b; }
+  LOB_DEV static Cand add(Cand a, Cand b) { return a > b ? a : b; }
+  LOB_DEV static Stored store(Cand c) { return c; }
+  LOB_DEV static bool better(Stored a, Stored b) { return a > b; }
+};
+LOB_HD u64 dmm_pack(float v, u32 id) {
+#ifdef __CUDA_ARCH__
+  u32 b = __float_as_uint(v);
+#else
+  union { float f; u32 u; } cv; cv.f = v; u32 b = cv.u;
+#endif
+  return ((u64)b << 32) | (u64)(0xFFFFFFFFu - id);
+}
+LOB_HD u32 dmm_id(u64 t) { return 0xFFFFFFFFu - (u32)(t & 0xFFFFFFFFull); }
+LOB_DEV float dmm_value(u64 t) { return __uint_as_float((u32)(t >> 32)); }
+
+// ---------------------------------------------------------------------------
+// scans
+// ---------------------------------------------------------------------------
+template <class T> LOB_DEV T warp_inclusive_sum(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T n = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+template <class T> LOB_DEV T warp_inclusive_max(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T n = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v = v > n ? v : n;
+  }
+  return v;
+}
+
+// Block-wide exclusive sum; `smem` needs blockDim.x/32 + 1 elements.  Returns
+// the exclusive prefix of `v` and writes the block total to *total.
+template <class T> LOB_DEV T block_exclusive_sum(T v, T* smem, T* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = warp_inclusive_sum(v);
+  if (lane == 31) smem[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < nw ? smem[lane] : T(0);
+    T wi = warp_inclusive_sum(w);
+    if (lane < nw) smem[lane] = wi - w;
+    if (lane == nw - 1) smem[nw] = wi;
+  }
+  __syncthreads();
+  T r = smem[warp] + inc - v;
+  *total = smem[nw];
+  __syncthreads();
+  return r;
+}
+
+template <class T> LOB_DEV T block_inclusive_max(T v, T* smem) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = warp_inclusive_max(v);
+  if (lane == 31) smem[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < nw ? smem[lane] : T(0);
+    T wi = warp_inclusive_max(w);
+    // exclusive max of warp totals
+    T ex = __shfl_up_sync(0xFFFFFFFFu, wi, 1);
+    if (lane < nw) smem[lane] = lane == 0 ? T(0) : ex;
+  }
+  __syncthreads();
+  T p = smem[warp];
+  __syncthreads();
+  return inc > p ? inc : p;
+}
+
+// first index i in [lo, hi) with a[i] > x (a sorted ascending)
+template <class T> LOB_DEV u64 upper_bound_dev(const T* a, u64 lo, u64 hi, T x) {
+  while (lo < hi) {
+    u64 mid = lo + ((hi - lo) >> 1);
+    if (a[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+// first index i in [lo, hi) with a[i] >= x
+template <class T> LOB_DEV u64 lower_bound_dev(const T* a, u64 lo, u64 hi, T x) {
+  while (lo < hi) {
+    u64 mid = lo + ((hi - lo) >> 1);
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}

@@ -1,0 +1,1043 @@
+// C ABI, memory management, planning and the semi-naive iteration driver.
+//
+// Per iteration k (Algorithm 1; the appendix's Join and Stratum rules):
+//   1. every rule arm whose delta relation has recent facts runs its join
+//      pipeline (count -> scan -> emit, one step per body atom) and appends
+//      candidate head tuples (packed keys + tags) to the head's buffer;
+//   2. per head relation: radix sort, unique with (+), then one fused pass that
+//      drops candidates already in the full relation F (or keeps them when
+//      their tag improves, for idempotent (+)), merges the rest into F and
+//      writes them as the next recent set; secondary sorted views of the
+//      relation receive the same new facts;
+//   3. stop when no relation has recent facts.
+#include <algorithm>
+#include <cstring>
+
+#include "engine.h"
+#include "scan.cuh"
+
+RuleAst parse_rule(const lob_engine& e, const char* text);
+bool valid_ident(const char* s);
+int backward_impl(lob_engine* e, u32 out_rel, const float* grad_tags, float* const* grad_inputs, int mem);
+
+static thread_local std::string g_create_err;
+
+// ---------------------------------------------------------------------------
+// memory and errors
+// ---------------------------------------------------------------------------
+void lob_engine::check(cudaError_t c, const char* what) {
+  if (c != cudaSuccess) {
+    cudaGetLastError();
+    if (c == cudaErrorMemoryAllocation) throw LobError(LOB_E_OOM, std::string(what) + ": out of device memory");
+    throw LobError(LOB_E_CUDA, std::string(what) + ": " + cudaGetErrorString(c));
+  }
+}
+
+void lob_engine::after_launch(const char* what) {
+  check(cudaGetLastError(), what);
+  if (opt_sync_check) check(cudaStreamSynchronize(stream), what);
+}
+
+void* lob_engine::dalloc(size_t bytes) {
+  if (!bytes) return nullptr;
+  void* p = nullptr;
+  if (custom_alloc) {
+    p = alloc.alloc(bytes, stream, alloc.ctx);
+  } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (!p) throw LobError(LOB_E_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  live_bytes += bytes;
+  peak_bytes = std::max(peak_bytes, live_bytes);
+  return p;
+}
+
+void lob_engine::dfree(void* p, size_t bytes) {
+  if (!p) return;
+  if (custom_alloc) alloc.release(p, bytes, stream, alloc.ctx);
+  else cudaFreeAsync(p, stream);
+  live_bytes -= bytes;
+}
+
+// Grow-only buffers reused across iterations (Sec. 4.1, buffer reuse): a
+// buffer is replaced only when a request exceeds its capacity, with slack.
+void lob_engine::ensure(DevBuf& b, size_t bytes, bool keep) {
+  if (b.cap >= bytes) return;
+  size_t cap = std::max(bytes, b.cap + b.cap / 2);
+  cap = (cap + 255) & ~(size_t)255;
+  void* p = dalloc(cap);
+  if (keep && b.p) check(cudaMemcpyAsync(p, b.p, b.cap, cudaMemcpyDeviceToDevice, stream), "grow copy");
+  dfree(b.p, b.cap);
+  b.p = p;
+  b.cap = cap;
+}
+
+void lob_engine::release(DevBuf& b) {
+  dfree(b.p, b.cap);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+u64 lob_engine::read_u64(const u64* dev) {
+  check(cudaMemcpyAsync(pinned, dev, sizeof(u64), cudaMemcpyDeviceToHost, stream), "readback");
+  check(cudaStreamSynchronize(stream), "readback sync");
+  return pinned[0];
+}
+
+void lob_engine::sync() { check(cudaStreamSynchronize(stream), "synchronize"); }
+
+static void release_view(lob_engine& e, ViewSt& v) {
+  for (DevBuf* b : {&v.keys, &v.tags, &v.stamps, &v.keys2, &v.tags2, &v.stamps2}) e.release(*b);
+  for (auto& kv : v.index) e.release(kv.second.offs);
+  v.index.clear();
+  v.n = 0;
+}
+
+static void release_derived(lob_engine& e) {
+  for (auto& r : e.rels) {
+    for (auto& v : r.views) release_view(e, v);
+    r.views.clear();
+    for (DevBuf* b : {&r.rkeys, &r.rtags, &r.nkeys, &r.ntags, &r.ckeys, &r.ctags, &r.ckeys2, &r.ctags2, &r.row_factor,
+                      &r.row_keys})
+      e.release(*b);
+    r.n_recent = r.n_next = r.n_cand = 0;
+  }
+  e.plans.clear();
+}
+
+void lob_engine::release_all() {
+  release_derived(*this);
+  for (auto& r : rels) {
+    for (auto& b : r.in_cols) release(b);
+    release(r.in_tags);
+    release(r.in_samples);
+  }
+  for (DevBuf* b : {&scratch, &cnt, &lo, &off, &part, &counts, &tmp_keys, &tmp_tags, &tmp_keys2, &tmp_tags2}) release(*b);
+  for (auto& side : bind)
+    for (auto& b : side) release(b);
+}
+
+// ---------------------------------------------------------------------------
+// layouts and planning
+// ---------------------------------------------------------------------------
+static int bitlen(u64 x) { return x ? 64 - __builtin_clzll(x) : 0; }
+
+static int cand_bytes(int sem) {
+  switch (sem) {
+    case SR_UNIT: return 0;
+    case SR_MAX_MIN: return 4;
+    default: return 8;
+  }
+}
+static int stored_bytes(int sem) {
+  switch (sem) {
+    case SR_UNIT: return 0;
+    case SR_DIFF_MAX_MIN: return 8;
+    default: return 4;
+  }
+}
+static bool sem_idempotent(int sem) { return sem == SR_UNIT || sem == SR_MAX_MIN || sem == SR_DIFF_MAX_MIN; }
+static bool sem_stamps(int sem) { return sem == SR_ADD_MULT || sem == SR_DIFF_ADD_MULT; }
+static int sem_kernel(int sem) { return sem == SR_DIFF_ADD_MULT ? SR_ADD_MULT : sem; }
+
+static void make_layout(const lob_engine& e, const RelSt& r, const int* perm, Layout& L) {
+  std::memset(&L, 0, sizeof(L));
+  L.arity = (int)r.arity;
+  int sh = 0;
+  for (int j = (int)r.arity - 1; j >= 0; j--) {
+    L.width[j] = r.width[perm[j]];
+    L.shift[j] = sh;
+    sh += L.width[j];
+  }
+  L.sshift = sh;
+  L.swidth = e.swidth;
+  L.bits = sh + e.swidth;
+  L.key64 = L.bits > 32;
+  if (L.bits > 64)
+    throw LobError(LOB_E_KEY_WIDTH, "relation '" + r.name + "' needs " + std::to_string(L.bits) +
+                                        " key bits (sample id + columns); at most 64 are supported");
+}
+
+static int find_view(lob_engine& e, RelSt& r, const int* perm) {
+  for (size_t i = 0; i < r.views.size(); i++)
+    if (std::equal(perm, perm + r.arity, r.views[i].perm)) return (int)i;
+  ViewSt v;
+  std::copy(perm, perm + r.arity, v.perm);
+  make_layout(e, r, perm, v.lay);
+  r.views.push_back(std::move(v));
+  return (int)r.views.size() - 1;
+}
+
+static ArmPlan plan_arm(lob_engine& e, const RuleAst& R, int delta, bool idempotent) {
+  ArmPlan A;
+  A.delta = delta;
+  for (int i = 0; i < delta; i++) A.before_rels.push_back(R.body[i].rel);
+  const int nv = (int)R.var_names.size();
+  std::vector<char> bound(nv, 0), used(R.body.size(), 0);
+  std::vector<std::vector<char>> bound_after;
+  {  // source: the delta atom read from the recent set (primary layout)
+    StepPlan s;
+    s.atom = delta;
+    s.view = 0;
+    const AtomAst& a = R.body[delta];
+    for (size_t c = 0; c < a.args.size(); c++) {
+      const Term& t = a.args[c];
+      ColAct act{};
+      if (!t.var) { act.op = OP_CHECK_CONST; act.cnst = t.v; act.slot = -1; }
+      else if (!bound[t.v]) { act.op = OP_BIND; act.slot = (int8_t)t.v; bound[t.v] = 1; }
+      else { act.op = OP_CHECK_SLOT; act.slot = (int8_t)t.v; }
+      s.act[c] = act;
+    }
+    used[delta] = 1;
+    A.steps.push_back(s);
+    bound_after.push_back(bound);
+  }
+  for (size_t n_used = 1; n_used < R.body.size(); n_used++) {
+    int best = -1, best_b = -1;
+    for (size_t i = 0; i < R.body.size(); i++) {
+      if (used[i]) continue;
+      int b = 0;
+      for (auto& t : R.body[i].args) b += (!t.var || bound[t.v]);
+      if (b > best_b) { best_b = b; best = (int)i; }
+    }
+    const AtomAst& a = R.body[best];
+    RelSt& rel = e.rels[a.rel];
+    int perm[kMaxArity];
+    int np = 0;
+    for (size_t c = 0; c < a.args.size(); c++)
+      if (!a.args[c].var || bound[a.args[c].v]) perm[np++] = (int)c;
+    const int prefix = np;
+    for (size_t c = 0; c < a.args.size(); c++)
+      if (a.args[c].var && !bound[a.args[c].v]) perm[np++] = (int)c;
+    StepPlan s;
+    s.atom = best;
+    s.view = find_view(e, rel, perm);
+    rel.views[s.view].probed = true;
+    s.prefix_len = prefix;
+    for (int j = 0; j < kMaxArity; j++) { s.prefix_slot[j] = -1; s.prefix_const[j] = 0; s.act[j] = ColAct{}; }
+    for (int j = 0; j < prefix; j++) {
+      const Term& t = a.args[perm[j]];
+      if (t.var) s.prefix_slot[j] = (int8_t)t.v;
+      else s.prefix_const[j] = t.v;
+    }
+    for (int j = prefix; j < (int)a.args.size(); j++) {
+      const Term& t = a.args[perm[j]];
+      ColAct act{};
+      act.slot = (int8_t)t.v;
+      if (!bound[t.v]) { act.op = OP_BIND; bound[t.v] = 1; }
+      else act.op = OP_CHECK_SLOT;
+      s.act[j] = act;
+    }
+    s.probe_old = best < delta && !idempotent && rel.idb;
+    used[best] = 1;
+    A.steps.push_back(s);
+    bound_after.push_back(bound);
+  }
+  // filters at the first step that binds all their variables
+  for (size_t f = 0; f < R.filters.size(); f++) {
+    const FilterAst& F = R.filters[f];
+    for (size_t s = 0; s < A.steps.size(); s++) {
+      bool ok = (!F.a.var || bound_after[s][F.a.v]) && (!F.b.var || bound_after[s][F.b.v]);
+      if (ok) { A.steps[s].filters.push_back((int)f); break; }
+    }
+  }
+  // live variables after each non-final step
+  for (size_t s = 0; s + 1 < A.steps.size(); s++) {
+    std::vector<char> need(nv, 0);
+    for (size_t q = s + 1; q < A.steps.size(); q++) {
+      for (auto& t : R.body[A.steps[q].atom].args)
+        if (t.var) need[t.v] = 1;
+      for (int f : A.steps[q].filters) {
+        if (R.filters[f].a.var) need[R.filters[f].a.v] = 1;
+        if (R.filters[f].b.var) need[R.filters[f].b.v] = 1;
+      }
+    }
+    for (auto& t : R.head.args)
+      if (t.var) need[t.v] = 1;
+    for (int v = 0; v < nv; v++)
+      if (need[v] && bound_after[s][v]) A.steps[s].live.push_back(v);
+  }
+  return A;
+}
+
+static void prepare(lob_engine& e, int sem) {
+  release_derived(e);
+  e.semiring = sem;
+  // column widths: bitlen(max + 1) of the loaded values, so that no field ever
+  // holds its all-ones value (the all-ones key marks dropped candidates)
+  u32* dmax = reinterpret_cast<u32*>(e.counts.p) + 32;
+  bool any_samples = false;
+  u32 max_sample = 0;
+  for (auto& r : e.rels) {
+    for (u32 c = 0; c < r.arity; c++) {
+      u32 m = 0;
+      if (r.n_in) {
+        reduce_max_u32(r.in_cols[0].as<u32>() + (u64)c * r.in_cap, r.n_in, dmax, e.stream);
+        e.after_launch("column max");
+        m = (u32)(e.read_u64(reinterpret_cast<u64*>(dmax)) & 0xFFFFFFFFull);
+      }
+      r.width[c] = r.n_in ? std::max(1, bitlen((u64)m + 1)) : 1;
+    }
+    if (r.in_has_samples && r.n_in) {
+      reduce_max_u32(r.in_samples.as<u32>(), r.n_in, dmax, e.stream);
+      e.after_launch("sample max");
+      max_sample = std::max(max_sample, (u32)(e.read_u64(reinterpret_cast<u64*>(dmax)) & 0xFFFFFFFFull));
+      any_samples = true;
+    }
+  }
+  e.swidth = any_samples ? bitlen((u64)max_sample + 1) : 0;
+  for (auto& r : e.rels) r.idb = false;
+  for (auto& R : e.rules) e.rels[R.head.rel].idb = true;
+  for (bool changed = true; changed;) {
+    changed = false;
+    for (auto& R : e.rules) {
+      RelSt& h = e.rels[R.head.rel];
+      for (size_t c = 0; c < R.head.args.size(); c++) {
+        const Term& t = R.head.args[c];
+        int need = 1;
+        if (!t.var) need = bitlen((u64)t.v + 1);
+        else
+          for (auto& a : R.body)
+            for (size_t q = 0; q < a.args.size(); q++)
+              if (a.args[q].var && a.args[q].v == t.v) need = std::max(need, e.rels[a.rel].width[q]);
+        if (need > h.width[c]) { h.width[c] = need; changed = true; }
+      }
+    }
+  }
+  for (auto& r : e.rels) {
+    int id[kMaxArity];
+    for (int j = 0; j < kMaxArity; j++) id[j] = j;
+    find_view(e, r, id);
+  }
+  const bool idem = sem_idempotent(sem);
+  for (auto& R : e.rules) {
+    RulePlan p;
+    p.ast = R;
+    for (size_t i = 0; i < R.body.size(); i++) p.arms.push_back(plan_arm(e, R, (int)i, idem));
+    e.plans.push_back(std::move(p));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// loading facts into the full relations (stamp 0) and the first recent sets
+// ---------------------------------------------------------------------------
+static void scratch_at_least(lob_engine& e, size_t bytes) { e.ensure(e.scratch, bytes); }
+
+// Re-encode n primary-layout facts into view `v`'s layout and sort them.
+// Returns pointers (into the engine's tmp buffers) to the sorted keys and tags.
+static std::pair<void*, void*> sort_view_rows(lob_engine& e, RelSt& r, ViewSt& v, const void* pkeys, const void* ptags,
+                                              u64 n) {
+  const int sem = e.semiring;
+  const int kb = v.lay.key64 ? 8 : 4, sb = stored_bytes(sem);
+  e.ensure(e.tmp_keys, n * kb);
+  e.ensure(e.tmp_keys2, n * kb);
+  if (sb) {
+    e.ensure(e.tmp_tags, n * sb);
+    e.ensure(e.tmp_tags2, n * sb);
+    e.check(cudaMemcpyAsync(e.tmp_tags.p, ptags, n * sb, cudaMemcpyDeviceToDevice, e.stream), "copy tags");
+  }
+  repack_keys(r.views[0].lay, r.views[0].perm, v.lay, v.perm, pkeys, e.tmp_keys.p, n, e.stream);
+  e.after_launch("repack");
+  void* k = e.tmp_keys.p;
+  void* t = e.tmp_tags.p;
+  scratch_at_least(e, sort_scratch_bytes(n, e.opt_radix_bits));
+  sort_pairs(v.lay.key64, sb, &k, &t, e.tmp_keys2.p, e.tmp_tags2.p, n, v.lay.bits, e.opt_radix_bits, e.scratch.p, e.stream);
+  e.after_launch("view sort");
+  e.launches += 1 + sort_kernel_launches(n, v.lay.bits, e.opt_radix_bits);
+  return {k, t};
+}
+
+static void load_facts(lob_engine& e) {
+  const int sem = e.semiring;
+  const int ks = sem_kernel(sem);
+  const int sb = stored_bytes(sem);
+  const bool stamps = sem_stamps(sem);
+  u64 id_base = 0;
+  for (auto& r : e.rels) {
+    r.id_base = (u32)id_base;
+    id_base += r.n_in;
+    if (id_base > 0xFFFFFFFEull) throw LobError(LOB_E_ARG, "more than 2^32-2 loaded rows");
+    ViewSt& V = r.views[0];
+    const u64 n = r.n_in;
+    V.n = 0;
+    r.n_recent = 0;
+    if (!n) continue;
+    const int kb = V.lay.key64 ? 8 : 4;
+    e.ensure(e.tmp_keys, n * kb);
+    e.ensure(e.tmp_keys2, n * kb);
+    e.ensure(e.tmp_tags, n * 4);
+    e.ensure(e.tmp_tags2, n * 4);
+    pack_rows(V.lay, r.in_cols[0].as<u32>(), r.in_cap, r.in_has_samples ? r.in_samples.as<u32>() : nullptr, n,
+              e.tmp_keys.p, e.tmp_tags.as<u32>(), e.stream);
+    e.after_launch("pack rows");
+    e.launches++;
+    if (sem == SR_DIFF_ADD_MULT) {
+      e.ensure(r.row_keys, n * kb);
+      e.check(cudaMemcpyAsync(r.row_keys.p, e.tmp_keys.p, n * kb, cudaMemcpyDeviceToDevice, e.stream), "row keys");
+      e.ensure(r.row_factor, n * 4);
+    }
+    void* k = e.tmp_keys.p;
+    void* rows = e.tmp_tags.p;
+    scratch_at_least(e, sort_scratch_bytes(n, e.opt_radix_bits));
+    sort_pairs(V.lay.key64, 4, &k, &rows, e.tmp_keys2.p, e.tmp_tags2.p, n, V.lay.bits, e.opt_radix_bits, e.scratch.p,
+               e.stream);
+    e.after_launch("load sort");
+    e.launches += sort_kernel_launches(n, V.lay.bits, e.opt_radix_bits);
+    e.ensure(V.keys, n * kb);
+    if (sb) e.ensure(V.tags, n * sb);
+    if (stamps) e.ensure(V.stamps, n * 4);
+    LoadUniqueArgs a{};
+    a.sem = ks;
+    a.key64 = V.lay.key64;
+    a.keys = k;
+    a.rows = reinterpret_cast<const u32*>(rows);
+    a.n = n;
+    a.raw_tags = r.in_has_tags ? r.in_tags.as<float>() : nullptr;
+    a.id_base = r.id_base;
+    a.differentiable = r.in_has_tags;
+    a.okeys = V.keys.p;
+    a.otags = V.tags.p;
+    a.ostamp = stamps ? V.stamps.as<u32>() : nullptr;
+    a.row_factor = sem == SR_DIFF_ADD_MULT ? r.row_factor.as<float>() : nullptr;
+    a.count_dev = e.counts.as<u64>();
+    scratch_at_least(e, unique_scratch_bytes(n));
+    load_unique(a, e.scratch.p, e.stream);
+    e.after_launch("load unique");
+    e.launches += 2 + scan_launches((n + 4095) / 4096);
+    V.n = e.read_u64(e.counts.as<u64>());
+    // recent = all loaded facts (Algorithm 1 starts with stable empty, recent = F_T)
+    e.ensure(r.rkeys, V.n * kb);
+    e.check(cudaMemcpyAsync(r.rkeys.p, V.keys.p, V.n * kb, cudaMemcpyDeviceToDevice, e.stream), "recent keys");
+    if (sb) {
+      e.ensure(r.rtags, V.n * sb);
+      e.check(cudaMemcpyAsync(r.rtags.p, V.tags.p, V.n * sb, cudaMemcpyDeviceToDevice, e.stream), "recent tags");
+    }
+    r.n_recent = V.n;
+    for (size_t vi = 1; vi < r.views.size(); vi++) {
+      ViewSt& W = r.views[vi];
+      auto kt = sort_view_rows(e, r, W, V.keys.p, V.tags.p, V.n);
+      const int wkb = W.lay.key64 ? 8 : 4;
+      e.ensure(W.keys, V.n * wkb);
+      e.check(cudaMemcpyAsync(W.keys.p, kt.first, V.n * wkb, cudaMemcpyDeviceToDevice, e.stream), "view keys");
+      if (sb) {
+        e.ensure(W.tags, V.n * sb);
+        e.check(cudaMemcpyAsync(W.tags.p, kt.second, V.n * sb, cudaMemcpyDeviceToDevice, e.stream), "view tags");
+      }
+      W.n = V.n;
+      if (stamps) {
+        e.ensure(W.stamps, V.n * 4);
+        e.check(cudaMemsetAsync(W.stamps.p, 0, V.n * 4, e.stream), "stamps");
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one iteration
+// ---------------------------------------------------------------------------
+static void ensure_index(lob_engine& e, ViewSt& v, int prefix) {
+  IndexSt& I = v.index[prefix];
+  if (I.valid) return;
+  const Layout& L = v.lay;
+  if (prefix == 0 && L.swidth == 0) {
+    I.mode = INDEX_BSEARCH;
+    I.valid = true;
+    return;
+  }
+  const int dbits = L.bits - rest_shift(L, prefix);
+  bool dense = dbits <= e.opt_dense_bits;
+  if (e.opt_join_index == 1) dense = dbits <= 30;
+  if (e.opt_join_index == 2) dense = false;
+  if (dense) {
+    I.mode = INDEX_DENSE;
+    I.domain = 1ull << dbits;
+    e.ensure(I.offs, (I.domain + 1) * 8);
+    build_dense_index(L, prefix, v.keys.p, v.n, I.offs.as<u64>(), I.domain, e.stream);
+    e.after_launch("dense index");
+    e.launches++;
+  } else {
+    I.mode = INDEX_BSEARCH;
+  }
+  I.valid = true;
+}
+
+static void fill_filters(const RuleAst& R, const std::vector<int>& fs, FilterP* out, int& n) {
+  n = 0;
+  for (int f : fs) {
+    const FilterAst& F = R.filters[f];
+    FilterP p{};
+    p.a_slot = F.a.var ? (int8_t)F.a.v : (int8_t)-1;
+    p.a_const = F.a.var ? 0 : F.a.v;
+    p.b_slot = F.b.var ? (int8_t)F.b.v : (int8_t)-1;
+    p.b_const = F.b.var ? 0 : F.b.v;
+    p.eq = F.eq ? 1 : 0;
+    out[n++] = p;
+  }
+}
+
+static void set_head_output(lob_engine& e, const RuleAst& R, StepParams& P, RelSt& H) {
+  P.out_packed = 1;
+  P.out_lay = H.views[0].lay;
+  for (int j = 0; j < kMaxArity; j++) { P.head_slot[j] = -1; P.head_const[j] = 0; }
+  for (size_t c = 0; c < R.head.args.size(); c++) {
+    if (R.head.args[c].var) P.head_slot[c] = (int8_t)R.head.args[c].v;
+    else P.head_const[c] = R.head.args[c].v;
+  }
+  P.out_keys = H.ckeys.p;
+  P.out_tags = H.ctags.p;
+  P.out_base = H.n_cand;
+}
+
+static void ensure_cand(lob_engine& e, RelSt& H, u64 extra) {
+  const int kb = H.views[0].lay.key64 ? 8 : 4;
+  const int cb = cand_bytes(e.semiring);
+  e.ensure(H.ckeys, (H.n_cand + extra) * kb, true);
+  if (cb) e.ensure(H.ctags, (H.n_cand + extra) * cb, true);
+}
+
+// Run one semi-naive arm of a rule for iteration k.  Δ-atom rows are the
+// recent facts of the delta relation (or, with `src_stamp`, the rows of its
+// primary view carrying that stamp).
+static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) {
+  const RuleAst& R = rp.ast;
+  RelSt& D = e.rels[R.body[A.delta].rel];
+  RelSt& H = e.rels[R.head.rel];
+  const int sem = sem_kernel(e.semiring);
+  const int cb = cand_bytes(e.semiring);
+  if (!D.n_recent) return;
+  StepParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.in_packed = 1;
+  P.in_keys = D.rkeys.p;
+  P.in_lay = D.views[0].lay;
+  std::copy(A.steps[0].act, A.steps[0].act + kMaxArity, P.in_act);
+  P.in_tags = D.rtags.p;
+  P.n_in = D.n_recent;
+  fill_filters(R, A.steps[0].filters, P.in_filters, P.n_in_filters);
+  if (A.steps.size() == 1) {
+    ensure_cand(e, H, P.n_in);
+    set_head_output(e, R, P, H);
+    project_rows(sem, P, e.stream);
+    e.after_launch("project");
+    e.launches++;
+    H.n_cand += P.n_in;
+    return;
+  }
+  int side = 0;
+  for (size_t s = 1; s < A.steps.size(); s++) {
+    const StepPlan& S = A.steps[s];
+    const bool last = s + 1 == A.steps.size();
+    RelSt& V = e.rels[R.body[S.atom].rel];
+    ViewSt& W = V.views[S.view];
+    if (!W.n) return;
+    ensure_index(e, W, S.prefix_len);
+    P.has_probe = 1;
+    P.v_keys = W.keys.p;
+    P.v_lay = W.lay;
+    P.v_tags = W.tags.p;
+    P.v_stamp = W.stamps.as<u32>();
+    P.v_n = W.n;
+    P.v_stamp_mode = STAMP_NONE;
+    if (S.probe_old) {  // facts older than the previous iteration's recent set
+      P.v_stamp_mode = STAMP_LT;
+      P.v_stamp_val = k - 1;
+    }
+    P.prefix_len = S.prefix_len;
+    std::copy(S.prefix_slot, S.prefix_slot + kMaxArity, P.prefix_slot);
+    std::copy(S.prefix_const, S.prefix_const + kMaxArity, P.prefix_const);
+    std::copy(S.act, S.act + kMaxArity, P.v_act);
+    const IndexSt& I = W.index[S.prefix_len];
+    P.index_mode = I.mode;
+    P.dense_offs = I.offs.as<u64>();
+    P.dense_domain = I.domain;
+    fill_filters(R, S.filters, P.filters, P.n_filters);
+    // count -> scan
+    e.ensure(e.cnt, P.n_in * 4);
+    e.ensure(e.lo, P.n_in * 8);
+    e.ensure(e.off, (P.n_in + 1) * 8);
+    P.cnt = e.cnt.as<u32>();
+    P.lo = e.lo.as<u64>();
+    join_count(sem, P, e.stream);
+    e.after_launch("join count");
+    scratch_at_least(e, scan_scratch_elems(P.n_in) * 8 + 64);
+    exclusive_scan<u32, u64>(e.cnt.as<u32>(), e.off.as<u64>(), P.n_in, e.counts.as<u64>(), e.scratch.as<u64>(), e.stream);
+    e.after_launch("join scan");
+    e.launches += 1 + scan_launches(P.n_in);
+    const u64 total = e.read_u64(e.counts.as<u64>());
+    if (!total) return;
+    // outputs
+    const int out_side = side ^ 1;
+    if (last) {
+      ensure_cand(e, H, total);
+      set_head_output(e, R, P, H);
+    } else {
+      P.out_packed = 0;
+      P.n_out_cols = (int)S.live.size();
+      for (size_t q = 0; q < S.live.size(); q++) {
+        e.ensure(e.bind[out_side][q], total * 4);
+        P.out_slot[q] = (int8_t)S.live[q];
+        P.out_cols[q] = e.bind[out_side][q].as<u32>();
+      }
+      e.ensure(e.bind[out_side][kMaxSlots], total * 4);
+      P.out_sample = e.bind[out_side][kMaxSlots].as<u32>();
+      if (cb) e.ensure(e.bind[out_side][kMaxSlots + 1], total * cb);
+      P.out_tags = e.bind[out_side][kMaxSlots + 1].p;
+      P.out_base = 0;
+    }
+    const u64 ntiles = (total + kEmitTile - 1) / kEmitTile;
+    e.ensure(e.part, (ntiles + 1) * 8);
+    lbs_partition(e.off.as<u64>(), P.n_in, total, e.part.as<u64>(), e.stream);
+    P.off = e.off.as<u64>();
+    P.total = total;
+    join_emit(sem, P, e.part.as<u64>(), e.stream);
+    e.after_launch("join emit");
+    e.launches += 2;
+    if (last) {
+      H.n_cand += total;
+      return;
+    }
+    // the binding table becomes the next step's input
+    side = out_side;
+    P.in_packed = 0;
+    P.n_in = total;
+    P.n_in_cols = (int)std::min(S.live.size(), (size_t)kMaxSlots);
+    for (int q = 0; q < P.n_in_cols; q++) {
+      P.in_slot[q] = (int8_t)S.live[q];
+      P.in_cols[q] = e.bind[side][q].as<u32>();
+    }
+    P.in_sample = e.bind[side][kMaxSlots].as<u32>();
+    P.in_tags = e.bind[side][kMaxSlots + 1].p;
+    P.n_in_filters = 0;
+  }
+}
+
+// sort + unique + difference/merge of one head relation's candidates
+static void dedup_relation(lob_engine& e, RelSt& H, u32 k) {
+  H.n_next = 0;
+  const u64 n = H.n_cand;
+  if (!n) return;
+  const int sem = e.semiring;
+  const int ks = sem_kernel(sem);
+  ViewSt& V = H.views[0];
+  const Layout& L = V.lay;
+  const int kb = L.key64 ? 8 : 4, cb = cand_bytes(sem), sb = stored_bytes(sem);
+  const bool stamps = sem_stamps(sem);
+  e.ensure(H.ckeys2, n * kb);
+  if (cb) e.ensure(H.ctags2, n * cb);
+  void* keys = H.ckeys.p;
+  void* tags = H.ctags.p;
+  scratch_at_least(e, sort_scratch_bytes(n, e.opt_radix_bits));
+  sort_pairs(L.key64, cb, &keys, &tags, H.ckeys2.p, H.ctags2.p, n, L.bits, e.opt_radix_bits, e.scratch.p, e.stream);
+  e.after_launch("candidate sort");
+  e.launches += sort_kernel_launches(n, L.bits, e.opt_radix_bits);
+  void* ukeys = keys == H.ckeys.p ? H.ckeys2.p : H.ckeys.p;
+  void* utags = tags == H.ctags.p ? H.ctags2.p : H.ctags.p;
+  scratch_at_least(e, unique_scratch_bytes(n));
+  unique_run(ks, L.key64, keys, tags, n, ukeys, utags, e.counts.as<u64>() + 1, e.scratch.p, e.stream);
+  e.after_launch("unique");
+  e.launches += 2 + scan_launches((n + 4095) / 4096);
+  const u64 nu = e.read_u64(e.counts.as<u64>() + 1);
+  if (!nu) return;
+  // difference against F fused with the merge into F
+  e.ensure(V.keys2, (V.n + nu) * kb);
+  if (sb) e.ensure(V.tags2, (V.n + nu) * sb);
+  if (stamps) e.ensure(V.stamps2, (V.n + nu) * 4);
+  e.ensure(H.nkeys, nu * kb);
+  if (sb) e.ensure(H.ntags, nu * sb);
+  MergeArgs M{};
+  M.sem = ks;
+  M.key64 = L.key64;
+  M.fkeys = V.keys.p; M.ftags = V.tags.p; M.fstamp = stamps ? V.stamps.as<u32>() : nullptr; M.nf = V.n;
+  M.ukeys = ukeys; M.utags = utags; M.nu = nu; M.u_stored = 0;
+  M.okeys = V.keys2.p; M.otags = V.tags2.p; M.ostamp = stamps ? V.stamps2.as<u32>() : nullptr;
+  M.rkeys = H.nkeys.p; M.rtags = H.ntags.p;
+  M.stamp = k;
+  M.counts_dev = e.counts.as<u64>() + 2;
+  scratch_at_least(e, merge_scratch_bytes(V.n, nu));
+  diff_merge(M, e.scratch.p, e.stream);
+  e.after_launch("difference+merge");
+  const u64 mt = (V.n + nu + 2047) / 2048;
+  e.launches += 3 + 2 * scan_launches(mt);
+  e.check(cudaMemcpyAsync(e.pinned, e.counts.as<u64>() + 2, 16, cudaMemcpyDeviceToHost, e.stream), "counts");
+  e.sync();
+  const u64 dups = e.pinned[0], nr = e.pinned[1];
+  V.n = V.n + nu - dups;
+  std::swap(V.keys, V.keys2);
+  std::swap(V.tags, V.tags2);
+  std::swap(V.stamps, V.stamps2);
+  for (auto& kv : V.index) kv.second.valid = false;
+  H.n_next = nr;
+  if (!nr) return;
+  // secondary views receive the same new / improved facts
+  for (size_t vi = 1; vi < H.views.size(); vi++) {
+    ViewSt& W = H.views[vi];
+    auto kt = sort_view_rows(e, H, W, H.nkeys.p, H.ntags.p, nr);
+    e.ensure(W.keys2, (W.n + nr) * kb);
+    if (sb) e.ensure(W.tags2, (W.n + nr) * sb);
+    if (stamps) e.ensure(W.stamps2, (W.n + nr) * 4);
+    MergeArgs M2{};
+    M2.sem = ks;
+    M2.key64 = W.lay.key64;
+    M2.fkeys = W.keys.p; M2.ftags = W.tags.p; M2.fstamp = stamps ? W.stamps.as<u32>() : nullptr; M2.nf = W.n;
+    M2.ukeys = kt.first; M2.utags = kt.second; M2.nu = nr; M2.u_stored = 1;
+    M2.okeys = W.keys2.p; M2.otags = W.tags2.p; M2.ostamp = stamps ? W.stamps2.as<u32>() : nullptr;
+    M2.rkeys = nullptr; M2.rtags = nullptr;
+    M2.stamp = k;
+    M2.counts_dev = e.counts.as<u64>() + 4;
+    scratch_at_least(e, merge_scratch_bytes(W.n, nr));
+    diff_merge(M2, e.scratch.p, e.stream);
+    e.after_launch("view merge");
+    e.launches += 3 + 2 * scan_launches((W.n + nr + 2047) / 2048);
+    const u64 d2 = e.read_u64(e.counts.as<u64>() + 4);
+    W.n = W.n + nr - d2;
+    std::swap(W.keys, W.keys2);
+    std::swap(W.tags, W.tags2);
+    std::swap(W.stamps, W.stamps2);
+    for (auto& kv : W.index) kv.second.valid = false;
+  }
+}
+
+static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
+  if (e.state != 0) throw LobError(LOB_E_STATE, "run_to_fixpoint was already called; call lob_reset first");
+  if (sem < 0 || sem > 4) throw LobError(LOB_E_ARG, "unknown semiring id");
+  e.peak_bytes = e.live_bytes;
+  e.launches = 0;
+  cudaEvent_t ev0, ev1;
+  e.check(cudaEventCreate(&ev0), "event");
+  e.check(cudaEventCreate(&ev1), "event");
+  e.check(cudaEventRecord(ev0, e.stream), "event");
+  prepare(e, sem);
+  load_facts(e);
+  lob_stats s{};
+  s.semiring = (u32)sem;
+  int rc = LOB_OK;
+  u32 k = 0;
+  for (;;) {
+    if (k >= max_iters) { rc = LOB_E_MAXITER; break; }
+    k++;
+    for (auto& r : e.rels) r.n_cand = 0;
+    for (auto& p : e.plans) {
+      for (auto& A : p.arms) {
+        if (!e.rels[p.ast.body[A.delta].rel].n_recent) continue;
+        bool skip = false;  // an atom before the delta atom has no old facts
+        for (u32 b : A.before_rels) {
+          const RelSt& br = e.rels[b];
+          if (br.views[0].n == br.n_recent) { skip = true; break; }
+        }
+        if (skip) continue;
+        run_arm(e, p, A, k);
+      }
+    }
+    u64 total_new = 0;
+    for (auto& r : e.rels) {
+      s.candidates += r.n_cand;
+      dedup_relation(e, r, k);
+      total_new += r.n_next;
+    }
+    for (auto& r : e.rels) {
+      std::swap(r.rkeys, r.nkeys);
+      std::swap(r.rtags, r.ntags);
+      r.n_recent = r.n_next;
+      r.n_next = 0;
+    }
+    s.new_facts += total_new;
+    if (!total_new) break;
+  }
+  e.check(cudaEventRecord(ev1, e.stream), "event");
+  e.sync();
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  s.iterations = k;
+  s.ms = ms;
+  for (auto& r : e.rels)
+    if (r.idb) s.derived += r.views[0].n;
+  s.peak_bytes = e.peak_bytes;
+  s.kernel_launches = e.launches;
+  e.stats = s;
+  e.last_iter = k;
+  e.state = 1;
+  e.ran_diff = sem == SR_DIFF_MAX_MIN || sem == SR_DIFF_ADD_MULT;
+  if (st) *st = s;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+template <class F>
+static int guarded(lob_engine* e, F&& f) {
+  if (!e) return LOB_E_ARG;
+  try {
+    e->err.clear();
+    cudaSetDevice(e->device);
+    return f();
+  } catch (const LobError& x) {
+    e->err = x.what();
+    return x.code;
+  } catch (const std::exception& x) {
+    e->err = x.what();
+    return LOB_E_ARG;
+  }
+}
+
+extern "C" {
+
+int lob_create(lob_engine** out, const lob_alloc* alloc, void* cuda_stream) {
+  g_create_err.clear();
+  if (!out) return LOB_E_ARG;
+  *out = nullptr;
+  lob_engine* e = new lob_engine();
+  if (cudaGetDevice(&e->device) != cudaSuccess) {
+    cudaGetLastError();
+    g_create_err = "no CUDA device";
+    delete e;
+    return LOB_E_CUDA;
+  }
+  e->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (alloc) {
+    if (!alloc->alloc || !alloc->release) {
+      g_create_err = "allocator needs both alloc and release";
+      delete e;
+      return LOB_E_ARG;
+    }
+    e->alloc = *alloc;
+    e->custom_alloc = true;
+  }
+  if (cudaMallocHost(&e->pinned, 64 * sizeof(u64)) != cudaSuccess) {
+    cudaGetLastError();
+    g_create_err = "pinned host allocation failed";
+    delete e;
+    return LOB_E_CUDA;
+  }
+  int rc = guarded(e, [&] {
+    e->ensure(e->counts, 64 * sizeof(u64) + 256);
+    return LOB_OK;
+  });
+  if (rc != LOB_OK) {
+    g_create_err = e->err;
+    cudaFreeHost(e->pinned);
+    delete e;
+    return rc;
+  }
+  *out = e;
+  return LOB_OK;
+}
+
+void lob_destroy(lob_engine* e) {
+  if (!e) return;
+  try {
+    cudaSetDevice(e->device);
+    e->release_all();
+    e->release(e->counts);
+    cudaStreamSynchronize(e->stream);
+  } catch (...) {
+  }
+  cudaFreeHost(e->pinned);
+  delete e;
+}
+
+const char* lob_last_error(const lob_engine* e) { return e ? e->err.c_str() : g_create_err.c_str(); }
+
+int lob_declare_relation(lob_engine* e, const char* name, uint32_t arity, uint32_t* rel_id) {
+  return guarded(e, [&] {
+    if (!valid_ident(name)) throw LobError(LOB_E_ARG, "invalid relation name");
+    if (arity < 1 || arity > (u32)kMaxArity) throw LobError(LOB_E_ARG, "arity must be 1..8");
+    if (e->rel_ids.count(name)) throw LobError(LOB_E_ARG, std::string("relation '") + name + "' already declared");
+    if (e->state != 0) throw LobError(LOB_E_STATE, "declare before running");
+    RelSt r;
+    r.name = name;
+    r.arity = arity;
+    const u32 id = (u32)e->rels.size();
+    e->rels.push_back(std::move(r));
+    e->rel_ids[name] = id;
+    if (rel_id) *rel_id = id;
+    return LOB_OK;
+  });
+}
+
+int lob_relation_id(const lob_engine* ce, const char* name, uint32_t* rel_id) {
+  lob_engine* e = const_cast<lob_engine*>(ce);
+  return guarded(e, [&] {
+    if (!name || !rel_id) throw LobError(LOB_E_ARG, "null argument");
+    auto it = e->rel_ids.find(name);
+    if (it == e->rel_ids.end()) throw LobError(LOB_E_UNKNOWN_REL, std::string("unknown relation '") + name + "'");
+    *rel_id = it->second;
+    return LOB_OK;
+  });
+}
+
+int lob_load_relation(lob_engine* e, uint32_t rel, const uint32_t* cols, const float* tags, const uint32_t* sample_ids,
+                      uint64_t n, int mem) {
+  return guarded(e, [&] {
+    if (rel >= e->rels.size()) throw LobError(LOB_E_UNKNOWN_REL, "unknown relation id");
+    if (e->state != 0) throw LobError(LOB_E_STATE, "load before running (or after lob_reset)");
+    if (mem != LOB_MEM_HOST && mem != LOB_MEM_DEVICE) throw LobError(LOB_E_ARG, "mem must be LOB_MEM_HOST or LOB_MEM_DEVICE");
+    if (!n) return LOB_OK;
+    if (!cols) throw LobError(LOB_E_ARG, "null cols");
+    RelSt& r = e->rels[rel];
+    const cudaMemcpyKind kind = mem == LOB_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const u64 need = r.n_in + n;
+    if (r.in_cols.empty()) r.in_cols.resize(1);
+    if (need > r.in_cap) {  // re-layout the column-major buffer with a larger stride
+      u64 cap = std::max<u64>(need, r.in_cap + r.in_cap / 2);
+      DevBuf nb;
+      nb.cap = 0;
+      e->ensure(nb, cap * r.arity * 4);
+      for (u32 c = 0; c < r.arity && r.n_in; c++)
+        e->check(cudaMemcpyAsync(nb.as<u32>() + (u64)c * cap, r.in_cols[0].as<u32>() + (u64)c * r.in_cap, r.n_in * 4,
+                                 cudaMemcpyDeviceToDevice, e->stream), "grow input");
+      e->release(r.in_cols[0]);
+      r.in_cols[0] = nb;
+      if (r.in_has_tags) e->ensure(r.in_tags, cap * 4, true);
+      if (r.in_has_samples) e->ensure(r.in_samples, cap * 4, true);
+      r.in_cap = cap;
+    }
+    for (u32 c = 0; c < r.arity; c++)
+      e->check(cudaMemcpyAsync(r.in_cols[0].as<u32>() + (u64)c * r.in_cap + r.n_in, cols + (u64)c * n, n * 4, kind,
+                               e->stream), "load columns");
+    if (tags && !r.in_has_tags) {
+      e->ensure(r.in_tags, r.in_cap * 4);
+      if (r.n_in) {  // earlier rows had tag 1
+        std::vector<float> ones(r.n_in, 1.0f);
+        e->check(cudaMemcpyAsync(r.in_tags.p, ones.data(), r.n_in * 4, cudaMemcpyHostToDevice, e->stream), "tags");
+        e->sync();
+      }
+      r.in_has_tags = true;
+    }
+    if (r.in_has_tags) {
+      if (tags) {
+        e->check(cudaMemcpyAsync(r.in_tags.as<float>() + r.n_in, tags, n * 4, kind, e->stream), "load tags");
+      } else {
+        std::vector<float> ones(n, 1.0f);
+        e->check(cudaMemcpyAsync(r.in_tags.as<float>() + r.n_in, ones.data(), n * 4, cudaMemcpyHostToDevice, e->stream),
+                 "tags");
+        e->sync();
+      }
+    }
+    if (sample_ids && !r.in_has_samples) {
+      e->ensure(r.in_samples, r.in_cap * 4);
+      if (r.n_in) e->check(cudaMemsetAsync(r.in_samples.p, 0, r.n_in * 4, e->stream), "samples");
+      r.in_has_samples = true;
+    }
+    if (r.in_has_samples) {
+      if (sample_ids)
+        e->check(cudaMemcpyAsync(r.in_samples.as<u32>() + r.n_in, sample_ids, n * 4, kind, e->stream), "load samples");
+      else
+        e->check(cudaMemsetAsync(r.in_samples.as<u32>() + r.n_in, 0, n * 4, e->stream), "samples");
+    }
+    if (mem == LOB_MEM_HOST) e->sync();  // the caller may reuse its host buffers on return
+    // values must leave the all-ones code free
+    u32* dmax = e->counts.as<u32>() + 32;
+    for (u32 c = 0; c < r.arity; c++) {
+      reduce_max_u32(r.in_cols[0].as<u32>() + (u64)c * r.in_cap + r.n_in, n, dmax, e->stream);
+      e->after_launch("column max");
+      if ((u32)(e->read_u64(reinterpret_cast<u64*>(dmax)) & 0xFFFFFFFFull) == 0xFFFFFFFFu)
+        throw LobError(LOB_E_ARG, "column value 0xFFFFFFFF is reserved");
+    }
+    r.n_in += n;
+    return LOB_OK;
+  });
+}
+
+int lob_add_rule(lob_engine* e, const char* text) {
+  return guarded(e, [&] {
+    if (!text) throw LobError(LOB_E_ARG, "null rule text");
+    if (e->state != 0) throw LobError(LOB_E_STATE, "add rules before running (or after lob_reset)");
+    e->rules.push_back(parse_rule(*e, text));
+    return LOB_OK;
+  });
+}
+
+int lob_run_to_fixpoint(lob_engine* e, int semiring, uint32_t max_iters, lob_stats* stats) {
+  return guarded(e, [&] { return run_fixpoint(*e, semiring, max_iters, stats); });
+}
+
+int lob_relation_size(lob_engine* e, uint32_t rel, uint64_t* n) {
+  return guarded(e, [&] {
+    if (rel >= e->rels.size()) throw LobError(LOB_E_UNKNOWN_REL, "unknown relation id");
+    if (!n) throw LobError(LOB_E_ARG, "null n");
+    RelSt& r = e->rels[rel];
+    *n = e->state == 1 && !r.views.empty() ? r.views[0].n : r.n_in;
+    return LOB_OK;
+  });
+}
+
+int lob_read_relation(lob_engine* e, uint32_t rel, uint32_t* cols, float* tags, uint32_t* sample_ids, uint64_t capacity,
+                      uint64_t* n_out, int mem) {
+  return guarded(e, [&] {
+    if (rel >= e->rels.size()) throw LobError(LOB_E_UNKNOWN_REL, "unknown relation id");
+    if (e->state != 1) throw LobError(LOB_E_STATE, "read after lob_run_to_fixpoint");
+    if (mem != LOB_MEM_HOST && mem != LOB_MEM_DEVICE) throw LobError(LOB_E_ARG, "bad mem");
+    RelSt& r = e->rels[rel];
+    ViewSt& V = r.views[0];
+    const u64 n = V.n;
+    if (n_out) *n_out = n;
+    if (n > capacity) throw LobError(LOB_E_CAPACITY, "capacity " + std::to_string(capacity) + " < " + std::to_string(n));
+    if (!n) return LOB_OK;
+    if (!cols) throw LobError(LOB_E_ARG, "null cols");
+    const int ks = sem_kernel(e->semiring);
+    if (mem == LOB_MEM_DEVICE) {
+      read_rows(ks, V.lay, V.perm, V.keys.p, V.tags.p, n, cols, capacity, tags, sample_ids, e->stream);
+      e->after_launch("read");
+      e->sync();
+      return LOB_OK;
+    }
+    DevBuf c, t, s;
+    e->ensure(c, n * r.arity * 4);
+    if (tags) e->ensure(t, n * 4);
+    if (sample_ids) e->ensure(s, n * 4);
+    read_rows(ks, V.lay, V.perm, V.keys.p, V.tags.p, n, c.as<u32>(), n, tags ? t.as<float>() : nullptr,
+              sample_ids ? s.as<u32>() : nullptr, e->stream);
+    e->after_launch("read");
+    for (u32 q = 0; q < r.arity; q++)
+      e->check(cudaMemcpyAsync(cols + (u64)q * capacity, c.as<u32>() + (u64)q * n, n * 4, cudaMemcpyDeviceToHost, e->stream),
+               "read cols");
+    if (tags) e->check(cudaMemcpyAsync(tags, t.p, n * 4, cudaMemcpyDeviceToHost, e->stream), "read tags");
+    if (sample_ids) e->check(cudaMemcpyAsync(sample_ids, s.p, n * 4, cudaMemcpyDeviceToHost, e->stream), "read samples");
+    e->sync();
+    e->release(c);
+    e->release(t);
+    e->release(s);
+    return LOB_OK;
+  });
+}
+
+int lob_backward(lob_engine* e, uint32_t out_rel, const float* grad_tags, float* const* grad_inputs, int mem) {
+  return guarded(e, [&] { return backward_impl(e, out_rel, grad_tags, grad_inputs, mem); });
+}
+
+int lob_reset(lob_engine* e) {
+  return guarded(e, [&] {
+    e->sync();
+    release_derived(*e);
+    for (auto& r : e->rels) {
+      for (auto& b : r.in_cols) e->release(b);
+      r.in_cols.clear();
+      e->release(r.in_tags);
+      e->release(r.in_samples);
+      r.n_in = r.in_cap = 0;
+      r.in_has_tags = r.in_has_samples = false;
+    }
+    e->state = 0;
+    e->ran_diff = false;
+    return LOB_OK;
+  });
+}
+
+int lob_set_option(lob_engine* e, const char* key, int64_t value) {
+  return guarded(e, [&] {
+    if (!key) throw LobError(LOB_E_ARG, "null key");
+    std::string k = key;
+    if (k == "join_index" && value >= 0 && value <= 2) e->opt_join_index = (int)value;
+    else if (k == "dense_bits" && value >= 1 && value <= 30) e->opt_dense_bits = (int)value;
+    else if (k == "radix_bits" && value >= 4 && value <= 11) e->opt_radix_bits = sort_supported_radix_bits((int)value);
+    else if (k == "sync_check" && (value == 0 || value == 1)) e->opt_sync_check = (int)value;
+    else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
+    return LOB_OK;
+  });
+}
+
+}  // extern "C"

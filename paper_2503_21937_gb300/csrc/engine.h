@@ -1,0 +1,150 @@
+// Host-side state of one fixpoint engine (internal).
+#pragma once
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/lobster.h"
+#include "kernels.h"
+
+struct LobError : std::runtime_error {
+  int code;
+  LobError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+// ---------------------------------------------------------------------------
+// rules
+// ---------------------------------------------------------------------------
+struct Term {
+  bool var = false;
+  u32 v = 0;  // slot or constant
+};
+struct AtomAst {
+  u32 rel = 0;
+  std::vector<Term> args;
+};
+struct FilterAst {
+  Term a, b;
+  bool eq = false;
+};
+struct RuleAst {
+  std::string text;
+  AtomAst head;
+  std::vector<AtomAst> body;
+  std::vector<FilterAst> filters;
+  std::vector<std::string> var_names;
+};
+
+// ---------------------------------------------------------------------------
+// device memory
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+struct IndexSt {
+  int mode = 0;  // INDEX_DENSE / INDEX_BSEARCH
+  u64 domain = 0;
+  bool valid = false;
+  DevBuf offs;
+};
+
+struct ViewSt {
+  int perm[kMaxArity] = {0};
+  Layout lay{};
+  DevBuf keys, tags, stamps;     // current sorted rows
+  DevBuf keys2, tags2, stamps2;  // merge target
+  u64 n = 0;
+  bool probed = false;
+  std::map<int, IndexSt> index;  // by prefix length
+};
+
+struct RelSt {
+  std::string name;
+  u32 arity = 0;
+  bool idb = false;
+  // loaded input rows, columnar, in load order
+  std::vector<DevBuf> in_cols;
+  DevBuf in_tags, in_samples;
+  u64 n_in = 0, in_cap = 0;
+  bool in_has_tags = false, in_has_samples = false;
+  std::vector<u64> in_chunks_tagged;  // (row_begin, row_end, tagged) triples flattened
+  int width[kMaxArity] = {0};
+  std::vector<ViewSt> views;  // [0] = primary (identity permutation)
+  DevBuf rkeys, rtags;        // recent (primary layout)
+  u64 n_recent = 0;
+  DevBuf nkeys, ntags;        // next recent
+  u64 n_next = 0;
+  DevBuf ckeys, ctags, ckeys2, ctags2;  // candidates + sort ping-pong
+  u64 n_cand = 0;
+  // gradient routing of loaded rows
+  DevBuf row_factor, row_keys;
+  u32 id_base = 0;
+};
+
+// ---------------------------------------------------------------------------
+// plans
+// ---------------------------------------------------------------------------
+struct StepPlan {
+  int atom = -1;
+  int view = 0;
+  int prefix_len = 0;
+  int8_t prefix_slot[kMaxArity];
+  u32 prefix_const[kMaxArity];
+  ColAct act[kMaxArity];
+  bool probe_old = false;
+  std::vector<int> filters;
+  std::vector<int> live;  // slots materialised after this step
+};
+struct ArmPlan {
+  int delta = 0;
+  std::vector<StepPlan> steps;
+  std::vector<u32> before_rels;  // relations of body atoms before the delta atom
+};
+struct RulePlan {
+  RuleAst ast;
+  std::vector<ArmPlan> arms;
+};
+
+struct lob_engine {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  lob_alloc alloc{};
+  bool custom_alloc = false;
+  std::string err;
+  size_t live_bytes = 0, peak_bytes = 0;
+  std::vector<RelSt> rels;
+  std::map<std::string, u32> rel_ids;
+  std::vector<RuleAst> rules;
+  std::vector<RulePlan> plans;
+  // options
+  int opt_join_index = 0, opt_dense_bits = 24, opt_radix_bits = 8, opt_sync_check = 0;
+  // run state
+  int state = 0;  // 0 loading, 1 ran
+  int semiring = 0;
+  int swidth = 0;
+  bool ran_diff = false;
+  u32 last_iter = 0;
+  lob_stats stats{};
+  // scratch and transient buffers
+  DevBuf scratch, cnt, lo, off, part, counts, tmp_keys, tmp_tags, tmp_keys2, tmp_tags2;
+  DevBuf bind[2][kMaxSlots + 2];  // binding tables (cols..., sample, tags) ping-pong
+  u64* pinned = nullptr;           // host readback slots
+  u64 launches = 0;
+
+  // memory
+  void* dalloc(size_t bytes);
+  void dfree(void* p, size_t bytes);
+  void ensure(DevBuf& b, size_t bytes, bool keep = false);
+  void release(DevBuf& b);
+  void release_all();
+  // helpers
+  void check(cudaError_t e, const char* what);
+  void after_launch(const char* what);
+  u64 read_u64(const u64* dev);
+  void sync();
+};

@@ -1,0 +1,378 @@
+// Join pipeline kernels: the APM instructions count / join / gather and
+// gather<(x)> of Sec. 3.2 and the appendix's join_impl rule, re-designed as
+//   count:  per input row, the [lo, hi) range of matching rows of a sorted
+//           relation view, found through a dense offset table or binary search;
+//   scan:   exclusive prefix sum of the counts (scan.cuh);
+//   emit:   load-balanced expansion -- each 2048-output tile finds the input
+//           row of every output by a shared-memory max-scan of row starts, so
+//           a skewed row (a hub vertex) is spread over many tiles -- fused
+//           with the gather of the matched columns, the projection to the
+//           head, the selection filters and the tag product (x).
+// The index is a relation view sorted by its join columns, so the matches of
+// a row are one contiguous range (the paper's hash index maps keys to row
+// indices; a sorted view gives the same lookup and coalesced emission).
+#include "kernels.h"
+
+namespace {
+
+LOB_DEV bool apply_act(const ColAct& a, u32 v, u32* val) {
+  if (a.op == OP_BIND) {
+    val[a.slot] = v;
+    return true;
+  }
+  if (a.op == OP_CHECK_SLOT) return val[a.slot] == v;
+  return v == a.cnst;
+}
+
+LOB_DEV bool eval_filter(const FilterP& f, const u32* val) {
+  u32 a = f.a_slot >= 0 ? val[f.a_slot] : f.a_const;
+  u32 b = f.b_slot >= 0 ? val[f.b_slot] : f.b_const;
+  return (a == b) == (f.eq != 0);
+}
+
+LOB_DEV bool stamp_ok(u32 s, int mode, u32 v) {
+  s &= 0x7FFFFFFFu;
+  return mode == STAMP_LT ? s < v : s == v;
+}
+
+template <class Sem>
+LOB_DEV bool read_input(const StepParams& P, u64 r, u32* val, u32& sample, typename Sem::Cand& tag) {
+  typedef typename Sem::Stored S;
+  typedef typename Sem::Cand C;
+  if (P.in_packed) {
+    if (P.in_stamp_mode != STAMP_NONE && !stamp_ok(P.in_stamp[r], P.in_stamp_mode, P.in_stamp_val)) return false;
+    const u64 key = load_key(P.in_keys, P.in_lay.key64, r);
+    sample = P.in_lay.swidth ? (u32)field_of(key, P.in_lay.sshift, P.in_lay.swidth) : 0u;
+#pragma unroll
+    for (int j = 0; j < kMaxArity; j++) {
+      if (j >= P.in_lay.arity) break;
+      if (!apply_act(P.in_act[j], (u32)field_of(key, P.in_lay.shift[j], P.in_lay.width[j]), val)) return false;
+    }
+    for (int f = 0; f < P.n_in_filters; f++)
+      if (!eval_filter(P.in_filters[f], val)) return false;
+    if constexpr (Sem::kTags) tag = Sem::from_stored(reinterpret_cast<const S*>(P.in_tags)[r]);
+    else tag = Sem::one();
+  } else {
+    sample = P.in_sample[r];
+    if (sample == 0xFFFFFFFFu) return false;
+    for (int k = 0; k < P.n_in_cols; k++) val[P.in_slot[k]] = P.in_cols[k][r];
+    if constexpr (Sem::kTags) tag = reinterpret_cast<const C*>(P.in_tags)[r];
+    else tag = Sem::one();
+  }
+  return true;
+}
+
+template <class K>
+LOB_DEV u64 lower_bound_keys(const K* a, u64 n, K x) {
+  u64 lo = 0, hi = n;
+  while (lo < hi) {
+    u64 mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+LOB_DEV u64 lower_bound_any(const void* keys, int key64, u64 n, u64 x) {
+  if (key64) return lower_bound_keys(reinterpret_cast<const u64*>(keys), n, x);
+  if (x > 0xFFFFFFFFull) return n;
+  return lower_bound_keys(reinterpret_cast<const u32*>(keys), n, (u32)x);
+}
+
+// range of view rows whose first prefix_len view columns (and sample) match
+LOB_DEV bool probe_range(const StepParams& P, const u32* val, u32 sample, u64& lo, u64& hi) {
+  const Layout& L = P.v_lay;
+  const int p = P.prefix_len;
+  if (p == 0 && L.swidth == 0) {
+    lo = 0;
+    hi = P.v_n;
+    return hi > 0;
+  }
+  const int rs = rest_shift(L, p);
+  u64 pv = 0;
+  if (L.swidth) {
+    if ((u64)sample >> L.swidth) return false;
+    pv |= (u64)sample << (L.sshift - rs);
+  }
+  for (int j = 0; j < p; j++) {
+    const u32 x = P.prefix_slot[j] >= 0 ? val[P.prefix_slot[j]] : P.prefix_const[j];
+    if (L.width[j] < 32 && (x >> L.width[j])) return false;
+    pv |= (u64)x << (L.shift[j] - rs);
+  }
+  if (P.index_mode == INDEX_DENSE) {
+    lo = P.dense_offs[pv];
+    hi = P.dense_offs[pv + 1];
+  } else {
+    const u64 klo = pv << rs;
+    const u64 khi = klo + (1ull << rs);
+    lo = lower_bound_any(P.v_keys, L.key64, P.v_n, klo);
+    hi = khi < klo ? P.v_n : lower_bound_any(P.v_keys, L.key64, P.v_n, khi);
+  }
+  return hi > lo;
+}
+
+template <class Sem>
+LOB_DEV void write_output(const StepParams& P, u64 o, bool ok, const u32* val, u32 sample, typename Sem::Cand tag) {
+  typedef typename Sem::Cand C;
+  if (P.out_packed) {
+    const Layout& L = P.out_lay;
+    u64 key;
+    if (!ok) {
+      key = invalid_of(L.key64);
+    } else {
+      key = L.swidth ? (u64)sample << L.sshift : 0ull;
+#pragma unroll
+      for (int j = 0; j < kMaxArity; j++) {
+        if (j >= L.arity) break;
+        const u32 x = P.head_slot[j] >= 0 ? val[P.head_slot[j]] : P.head_const[j];
+        key |= (u64)x << L.shift[j];
+      }
+    }
+    store_key(P.out_keys, L.key64, o, key);
+  } else {
+    P.out_sample[o] = ok ? sample : 0xFFFFFFFFu;
+    if (ok)
+      for (int k = 0; k < P.n_out_cols; k++) P.out_cols[k][o] = val[P.out_slot[k]];
+  }
+  if constexpr (Sem::kTags) reinterpret_cast<C*>(P.out_tags)[o] = tag;
+}
+
+template <class Sem>
+__global__ void __launch_bounds__(256) k_join_count(const __grid_constant__ StepParams P) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < P.n_in; r += stride) {
+    u32 val[kMaxSlots];
+    u32 sample;
+    typename Sem::Cand tag;
+    u64 lo = 0, hi = 0;
+    if (read_input<Sem>(P, r, val, sample, tag)) probe_range(P, val, sample, lo, hi);
+    P.cnt[r] = (u32)(hi - lo);
+    P.lo[r] = lo;
+  }
+}
+
+__global__ void k_lbs_partition(const u64* __restrict__ off, u64 n_in, u64 ntiles, u64* __restrict__ part) {
+  const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > ntiles) return;
+  if (t == ntiles) {
+    part[t] = n_in - 1;
+    return;
+  }
+  const u64 j = t * (u64)kEmitTile;
+  part[t] = upper_bound_dev<u64>(off, 0, n_in, j) - 1;
+}
+
+template <class Sem>
+__global__ void __launch_bounds__(256) k_join_emit(const __grid_constant__ StepParams P, const u64* __restrict__ part) {
+  typedef typename Sem::Stored S;
+  constexpr int kItems = kEmitTile / 256;
+  __shared__ u32 row_of[kEmitTile];
+  __shared__ u32 sm[256 / 32 + 1];
+  const u64 j0 = (u64)blockIdx.x * kEmitTile;
+  const u64 r0 = part[blockIdx.x];
+  const u64 r_end = part[blockIdx.x + 1];
+  for (int i = threadIdx.x; i < kEmitTile; i += 256) row_of[i] = 0;
+  __syncthreads();
+  for (u64 r = r0 + 1 + threadIdx.x; r <= r_end; r += 256) {
+    const u64 o = P.off[r];
+    if (o < j0 + kEmitTile) atomicMax(&row_of[o - j0], (u32)(r - r0));
+  }
+  __syncthreads();
+  // inclusive max-scan: tile position -> input row (relative to r0)
+  u32 loc[kItems];
+  u32 m = 0;
+#pragma unroll
+  for (int i = 0; i < kItems; i++) {
+    const u32 x = row_of[threadIdx.x * kItems + i];
+    m = x > m ? x : m;
+    loc[i] = m;
+  }
+  const u32 inc = block_inclusive_max<u32>(m, sm);
+  // exclusive prefix of thread maxima = inclusive of the previous thread
+  __shared__ u32 th_inc[256];
+  th_inc[threadIdx.x] = inc;
+  __syncthreads();
+  const u32 ex = threadIdx.x ? th_inc[threadIdx.x - 1] : 0u;
+#pragma unroll
+  for (int i = 0; i < kItems; i++) row_of[threadIdx.x * kItems + i] = loc[i] > ex ? loc[i] : ex;
+  __syncthreads();
+#pragma unroll 1
+  for (int i = 0; i < kItems; i++) {
+    const u64 j = j0 + (u64)i * 256 + threadIdx.x;
+    if (j >= P.total) break;
+    const u64 r = r0 + row_of[j - j0];
+    const u64 v = P.lo[r] + (j - P.off[r]);
+    u32 val[kMaxSlots];
+    u32 sample;
+    typename Sem::Cand tag;
+    read_input<Sem>(P, r, val, sample, tag);
+    bool ok = P.v_stamp_mode == STAMP_NONE || stamp_ok(P.v_stamp[v], P.v_stamp_mode, P.v_stamp_val);
+    const u64 vk = load_key(P.v_keys, P.v_lay.key64, v);
+#pragma unroll
+    for (int c = 0; c < kMaxArity; c++) {
+      if (c >= P.v_lay.arity) break;
+      if (c >= P.prefix_len && ok) ok = apply_act(P.v_act[c], (u32)field_of(vk, P.v_lay.shift[c], P.v_lay.width[c]), val);
+    }
+    for (int f = 0; f < P.n_filters && ok; f++) ok = eval_filter(P.filters[f], val);
+    if constexpr (Sem::kTags) tag = Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v]));
+    write_output<Sem>(P, P.out_base + j, ok, val, sample, tag);
+  }
+}
+
+template <class Sem>
+__global__ void __launch_bounds__(256) k_project(const __grid_constant__ StepParams P) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < P.n_in; r += stride) {
+    u32 val[kMaxSlots];
+    u32 sample;
+    typename Sem::Cand tag = Sem::one();
+    const bool ok = read_input<Sem>(P, r, val, sample, tag);
+    write_output<Sem>(P, P.out_base + r, ok, val, sample, tag);
+  }
+}
+
+__global__ void k_dense_index(const void* __restrict__ keys, int key64, u64 n, int rs, u64* __restrict__ offs, u64 domain) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 p = (u64)blockIdx.x * blockDim.x + threadIdx.x; p <= domain; p += stride)
+    offs[p] = p == domain ? n : lower_bound_any(keys, key64, n, p << rs);
+}
+
+struct Perm {
+  int p[kMaxArity];
+};
+
+__global__ void k_repack(Layout from, Perm pf, Layout to, Perm pt, const void* __restrict__ in, void* __restrict__ out, u64 n) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const u64 k = load_key(in, from.key64, i);
+    u32 rel[kMaxArity];
+    for (int j = 0; j < from.arity; j++) rel[pf.p[j]] = (u32)field_of(k, from.shift[j], from.width[j]);
+    u64 o = from.swidth ? field_of(k, from.sshift, from.swidth) << to.sshift : 0ull;
+    for (int j = 0; j < to.arity; j++) o |= (u64)rel[pt.p[j]] << to.shift[j];
+    store_key(out, to.key64, i, o);
+  }
+}
+
+__global__ void k_pack_rows(Layout L, const u32* __restrict__ cols, u64 stride_c, const u32* __restrict__ samples, u64 n,
+                            void* __restrict__ keys, u32* __restrict__ rows) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    u64 k = (L.swidth && samples) ? (u64)samples[i] << L.sshift : 0ull;
+    for (int j = 0; j < L.arity; j++) k |= (u64)cols[(u64)j * stride_c + i] << L.shift[j];
+    store_key(keys, L.key64, i, k);
+    rows[i] = (u32)i;
+  }
+}
+
+template <class Sem>
+__global__ void k_read_rows(Layout L, Perm perm, const void* __restrict__ keys, const void* __restrict__ tags, u64 n,
+                            u32* __restrict__ cols, u64 stride_c, float* __restrict__ otags, u32* __restrict__ samples) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const u64 k = load_key(keys, L.key64, i);
+    for (int j = 0; j < L.arity; j++) cols[(u64)perm.p[j] * stride_c + i] = (u32)field_of(k, L.shift[j], L.width[j]);
+    if (samples) samples[i] = L.swidth ? (u32)field_of(k, L.sshift, L.swidth) : 0u;
+    if (otags) {
+      float t = 1.0f;
+      if constexpr (std::is_same<Sem, SemDiffMaxMin>::value) t = dmm_value(reinterpret_cast<const u64*>(tags)[i]);
+      else if constexpr (Sem::kTags) t = reinterpret_cast<const float*>(tags)[i];
+      otags[i] = t;
+    }
+  }
+}
+
+__global__ void k_reduce_max(const u32* __restrict__ a, u64 n, u32* __restrict__ out) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  u32 m = 0;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) m = max(m, a[i]);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+inline unsigned grid_for(u64 n, int threads = 256) {
+  u64 b = (n + threads - 1) / threads;
+  const u64 cap = 152ull * 16;  // enough resident blocks to fill every SM
+  if (b > cap) b = cap;
+  return (unsigned)(b ? b : 1);
+}
+
+template <template <class> class Launch, class... A>
+void by_sem(int sem, A&&... a) {
+  switch (sem) {
+    case SR_UNIT: Launch<SemUnit>::go(a...); break;
+    case SR_MAX_MIN: Launch<SemMaxMin>::go(a...); break;
+    case SR_DIFF_MAX_MIN: Launch<SemDiffMaxMin>::go(a...); break;
+    default: Launch<SemAddMult>::go(a...); break;
+  }
+}
+
+template <class Sem> struct CountL {
+  static void go(const StepParams& P, cudaStream_t st) { k_join_count<Sem><<<grid_for(P.n_in), 256, 0, st>>>(P); }
+};
+template <class Sem> struct EmitL {
+  static void go(const StepParams& P, const u64* part, cudaStream_t st) {
+    const u64 tiles = (P.total + kEmitTile - 1) / kEmitTile;
+    k_join_emit<Sem><<<(unsigned)tiles, 256, 0, st>>>(P, part);
+  }
+};
+template <class Sem> struct ProjL {
+  static void go(const StepParams& P, cudaStream_t st) { k_project<Sem><<<grid_for(P.n_in), 256, 0, st>>>(P); }
+};
+template <class Sem> struct ReadL {
+  static void go(const Layout& L, const Perm& p, const void* keys, const void* tags, u64 n, u32* cols, u64 stride,
+                 float* otags, u32* samples, cudaStream_t st) {
+    k_read_rows<Sem><<<grid_for(n), 256, 0, st>>>(L, p, keys, tags, n, cols, stride, otags, samples);
+  }
+};
+
+}  // namespace
+
+void join_count(int sem, const StepParams& P, cudaStream_t st) {
+  if (P.n_in) by_sem<CountL>(sem, P, st);
+}
+
+void lbs_partition(const u64* off, u64 n_in, u64 total, u64* part, cudaStream_t st) {
+  const u64 ntiles = (total + kEmitTile - 1) / kEmitTile;
+  k_lbs_partition<<<(unsigned)((ntiles + 1 + 255) / 256), 256, 0, st>>>(off, n_in, ntiles, part);
+}
+
+void join_emit(int sem, const StepParams& P, const u64* part, cudaStream_t st) {
+  if (P.total) by_sem<EmitL>(sem, P, part, st);
+}
+
+void project_rows(int sem, const StepParams& P, cudaStream_t st) {
+  if (P.n_in) by_sem<ProjL>(sem, P, st);
+}
+
+void build_dense_index(const Layout& L, int prefix_len, const void* keys, u64 n, u64* offs, u64 domain, cudaStream_t st) {
+  k_dense_index<<<grid_for(domain + 1), 256, 0, st>>>(keys, L.key64, n, rest_shift(L, prefix_len), offs, domain);
+}
+
+void repack_keys(const Layout& from, const int* perm_from, const Layout& to, const int* perm_to, const void* in, void* out,
+                 u64 n, cudaStream_t st) {
+  if (!n) return;
+  Perm a, b;
+  for (int j = 0; j < kMaxArity; j++) {
+    a.p[j] = j < from.arity ? perm_from[j] : 0;
+    b.p[j] = j < to.arity ? perm_to[j] : 0;
+  }
+  k_repack<<<grid_for(n), 256, 0, st>>>(from, a, to, b, in, out, n);
+}
+
+void pack_rows(const Layout& L, const u32* cols, u64 stride, const u32* samples, u64 n, void* keys, u32* rows,
+               cudaStream_t st) {
+  if (n) k_pack_rows<<<grid_for(n), 256, 0, st>>>(L, cols, stride, samples, n, keys, rows);
+}
+
+void read_rows(int sem, const Layout& L, const int* perm, const void* keys, const void* tags, u64 n, u32* cols,
+               u64 stride, float* otags, u32* samples, cudaStream_t st) {
+  if (!n) return;
+  Perm p;
+  for (int j = 0; j < kMaxArity; j++) p.p[j] = j < L.arity ? perm[j] : 0;
+  by_sem<ReadL>(sem, L, p, keys, tags, n, cols, stride, otags, samples, st);
+}
+
+void reduce_max_u32(const u32* a, u64 n, u32* out_dev, cudaStream_t st) {
+  cudaMemsetAsync(out_dev, 0, sizeof(u32), st);
+  if (n) k_reduce_max<<<grid_for(n), 256, 0, st>>>(a, n, out_dev);
+}

@@ -1,0 +1,115 @@
+// Host-callable launch wrappers of the engine's kernels (internal interface
+// between the host driver and the kernel translation units).
+#pragma once
+#include <type_traits>
+#include "common.cuh"
+
+// ---------------------------------------------------------------------------
+// radix sort (sort.cu)
+// ---------------------------------------------------------------------------
+int sort_supported_radix_bits(int rb);
+size_t sort_scratch_bytes(u64 n, int rb);
+// Stable LSD sort of n (key, payload) pairs on the low `bits` key bits.  keys,
+// pay point at the input and are updated to whichever buffer holds the result
+// (the inputs or ktmp/ptmp).  pay_bytes is 0 (no payload), 4 or 8.
+void sort_pairs(int key64, int pay_bytes, void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits, int rb,
+                void* scratch, cudaStream_t st);
+int sort_kernel_launches(u64 n, int bits, int rb);
+
+// ---------------------------------------------------------------------------
+// unique, difference + merge, load normalisation (dedup.cu)
+// ---------------------------------------------------------------------------
+size_t unique_scratch_bytes(u64 n);
+// Sorted (keys, Cand tags) -> unique keys with (+)-reduced Cand tags; invalid
+// keys dropped; *count_dev receives the unique count.
+void unique_run(int sem, int key64, const void* keys, const void* tags, u64 n, void* okeys, void* otags, u64* count_dev,
+                void* scratch, cudaStream_t st);
+
+struct MergeArgs {
+  int sem, key64;
+  const void* fkeys; const void* ftags; const u32* fstamp; u64 nf;  // F: sorted, unique, Stored tags
+  const void* ukeys; const void* utags; u64 nu; int u_stored;       // U: sorted, unique; Cand tags unless u_stored
+  void* okeys; void* otags; u32* ostamp;                            // F' (room for nf + nu)
+  void* rkeys; void* rtags;                                         // R: new or improved facts (nullable)
+  u32 stamp;                                                        // stamp of new / improved facts
+  u64* counts_dev;                                                  // [0] = #dups of U in F, [1] = |R|
+};
+size_t merge_scratch_bytes(u64 nf, u64 nu);
+void diff_merge(const MergeArgs& a, void* scratch, cudaStream_t st);
+
+struct LoadUniqueArgs {
+  int sem, key64;
+  const void* keys; const u32* rows; u64 n;  // sorted (key, row) pairs
+  const float* raw_tags; u32 id_base; int differentiable;
+  void* okeys; void* otags; u32* ostamp; float* row_factor;
+  u64* count_dev;
+};
+void load_unique(const LoadUniqueArgs& a, void* scratch, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// joins and projections (join.cu)
+// ---------------------------------------------------------------------------
+enum ColOp : int8_t { OP_BIND = 0, OP_CHECK_SLOT = 1, OP_CHECK_CONST = 2 };
+struct ColAct {
+  int8_t op, slot;
+  u32 cnst;
+};
+struct FilterP {
+  int8_t a_slot, b_slot, eq;  // slot -1: use the constant
+  u32 a_const, b_const;
+};
+enum { STAMP_NONE = 0, STAMP_LT = 1, STAMP_EQ = 2 };
+enum { INDEX_DENSE = 1, INDEX_BSEARCH = 2 };
+
+// One step of a join pipeline: rows of an input table (a packed relation
+// segment or a materialised binding table) optionally joined with one
+// relation view, filtered, and written as a binding table or as packed head
+// keys (candidates).
+struct StepParams {
+  // input rows
+  int in_packed;
+  const void* in_keys; Layout in_lay; ColAct in_act[kMaxArity];
+  const u32* in_stamp; int in_stamp_mode; u32 in_stamp_val;     // packed input: stamp filter
+  int n_in_cols; int8_t in_slot[kMaxSlots]; const u32* in_cols[kMaxSlots];
+  const u32* in_sample;                                          // binding tables: sample column, 0xFFFFFFFF = dropped row
+  const void* in_tags;                                           // Stored (packed) / Cand (binding) tags
+  const u64* in_rowids;                                          // binding tables (backward): per-row fact rows
+  u64 n_in;
+  int n_in_filters; FilterP in_filters[kMaxFilters];
+  // probe
+  int has_probe;
+  const void* v_keys; Layout v_lay; const void* v_tags; const u32* v_stamp; u64 v_n;
+  int v_stamp_mode; u32 v_stamp_val;
+  int prefix_len; int8_t prefix_slot[kMaxArity]; u32 prefix_const[kMaxArity];
+  ColAct v_act[kMaxArity];
+  int index_mode; const u64* dense_offs; u64 dense_domain;
+  int n_filters; FilterP filters[kMaxFilters];
+  // output
+  int out_packed;
+  void* out_keys; Layout out_lay; int8_t head_slot[kMaxArity]; u32 head_const[kMaxArity];
+  int n_out_cols; int8_t out_slot[kMaxSlots]; u32* out_cols[kMaxSlots];
+  u32* out_sample;
+  void* out_tags;
+  u64 out_base;
+  // count / scan products
+  u32* cnt; u64* lo; const u64* off; u64 total;
+};
+
+void join_count(int sem, const StepParams& P, cudaStream_t st);
+constexpr int kEmitTile = 2048;
+// part[t] = last input row whose output range starts at or before t * kEmitTile
+void lbs_partition(const u64* off, u64 n_in, u64 total, u64* part, cudaStream_t st);
+void join_emit(int sem, const StepParams& P, const u64* part, cudaStream_t st);
+void project_rows(int sem, const StepParams& P, cudaStream_t st);
+
+void build_dense_index(const Layout& L, int prefix_len, const void* keys, u64 n, u64* offs, u64 domain, cudaStream_t st);
+// re-encode keys of layout `from` into layout `to`; view column j of `to` is
+// relation column perm_to[j], view column j of `from` is relation column perm_from[j]
+void repack_keys(const Layout& from, const int* perm_from, const Layout& to, const int* perm_to, const void* in, void* out,
+                 u64 n, cudaStream_t st);
+void pack_rows(const Layout& L, const u32* cols, u64 stride, const u32* samples, u64 n, void* keys, u32* rows,
+               cudaStream_t st);
+void read_rows(int sem, const Layout& L, const int* perm, const void* keys, const void* tags, u64 n, u32* cols,
+               u64 stride, float* otags, u32* samples, cudaStream_t st);
+void reduce_max_u32(const u32* a, u64 n, u32* out_dev, cudaStream_t st);
+void gather_cand_tags(int sem, const void* stored, const u64* idx, u64 n, void* out, cudaStream_t st);

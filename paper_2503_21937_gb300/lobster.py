@@ -1,0 +1,249 @@
+"""Python binding of the engine's C ABI (``include/lobster.h``).
+
+Argument marshalling only: every step of the fixpoint runs in the CUDA
+library ``liblobster.so``.  There is no CPU fallback; if the library is missing
+or no GPU is present the calls raise.
+
+Inputs may be numpy arrays (host memory) or CUDA torch tensors (device
+memory, used in place on the current torch stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblobster.so")
+
+LOB_OK = 0
+ERRORS = {-1: "LOB_E_ARG", -2: "LOB_E_PARSE", -3: "LOB_E_UNKNOWN_REL", -4: "LOB_E_UNSAFE_RULE", -5: "LOB_E_OOM",
+          -6: "LOB_E_MAXITER", -7: "LOB_E_TIMEOUT", -8: "LOB_E_CUDA", -9: "LOB_E_CAPACITY", -10: "LOB_E_STATE",
+          -11: "LOB_E_KEY_WIDTH"}
+SEMIRINGS = {"unit": 0, "max_min": 1, "add_mult": 2, "diff_max_min": 3, "diff_add_mult": 4}
+MEM_HOST, MEM_DEVICE = 0, 1
+
+# every symbol declared in include/lobster.h (checked by the tests)
+EXPORTS = ["lob_create", "lob_destroy", "lob_last_error", "lob_declare_relation", "lob_relation_id",
+           "lob_load_relation", "lob_add_rule", "lob_run_to_fixpoint", "lob_relation_size", "lob_read_relation",
+           "lob_backward", "lob_reset", "lob_set_option"]
+
+_lib = None
+
+
+class LobsterError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_uint32), ("semiring", ctypes.c_uint32), ("derived", ctypes.c_uint64),
+                ("candidates", ctypes.c_uint64), ("new_facts", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
+                ("ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load liblobster.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2503_21937_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, vp, u32, u64 = ctypes.POINTER, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+    lib.lob_create.argtypes = [P(vp), vp, vp]
+    lib.lob_destroy.argtypes = [vp]
+    lib.lob_destroy.restype = None
+    lib.lob_last_error.argtypes = [vp]
+    lib.lob_last_error.restype = ctypes.c_char_p
+    lib.lob_declare_relation.argtypes = [vp, ctypes.c_char_p, u32, P(u32)]
+    lib.lob_relation_id.argtypes = [vp, ctypes.c_char_p, P(u32)]
+    lib.lob_load_relation.argtypes = [vp, u32, vp, vp, vp, u64, ctypes.c_int]
+    lib.lob_add_rule.argtypes = [vp, ctypes.c_char_p]
+    lib.lob_run_to_fixpoint.argtypes = [vp, ctypes.c_int, u32, P(Stats)]
+    lib.lob_relation_size.argtypes = [vp, u32, P(u64)]
+    lib.lob_read_relation.argtypes = [vp, u32, vp, vp, vp, u64, P(u64), ctypes.c_int]
+    lib.lob_backward.argtypes = [vp, u32, vp, vp, ctypes.c_int]
+    lib.lob_reset.argtypes = [vp]
+    lib.lob_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_int64]
+    _lib = lib
+    return lib
+
+
+_ATOM = re.compile(r"([A-Za-z_][A-Za-z0-9_]*)\s*\(([^()]*)\)")
+
+
+def relation_arities(program: str) -> dict:
+    """Relation name -> arity for every atom in the program text."""
+    out = {}
+    for line in program.splitlines():
+        line = re.split(r"//|#|%", line)[0]
+        for name, args in _ATOM.findall(line):
+            out[name] = len([a for a in args.split(",") if a.strip()])
+    return out
+
+
+def split_rules(program: str) -> list:
+    text = "\n".join(re.split(r"//|#|%", l)[0] for l in program.splitlines())
+    return [r.strip() + "." for r in text.split(".") if r.strip()]
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+@dataclass
+class Relation:
+    cols: object   # (arity, n) uint32 numpy array or torch int32 tensor
+    tags: object   # (n,) float32
+    samples: object
+
+
+class Engine:
+    """One fixpoint engine on the current CUDA device."""
+
+    def __init__(self, stream=None):
+        self.lib = load_library()
+        self.h = ctypes.c_void_p()
+        stream = _torch_stream() if stream is None else stream
+        rc = self.lib.lob_create(ctypes.byref(self.h), None, ctypes.c_void_p(stream) if stream else None)
+        if rc != LOB_OK:
+            raise LobsterError(rc, self.lib.lob_last_error(None).decode())
+        self.ids = {}
+        self.arity = {}
+
+    def close(self):
+        if self.h:
+            self.lib.lob_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _chk(self, rc):
+        if rc != LOB_OK:
+            raise LobsterError(rc, self.lib.lob_last_error(self.h).decode())
+        return rc
+
+    def declare(self, name: str, arity: int) -> int:
+        rid = ctypes.c_uint32()
+        self._chk(self.lib.lob_declare_relation(self.h, name.encode(), arity, ctypes.byref(rid)))
+        self.ids[name] = rid.value
+        self.arity[name] = arity
+        return rid.value
+
+    def program(self, text: str):
+        """Declare every relation the program mentions (arity from its atoms) and add its rules."""
+        for name, ar in relation_arities(text).items():
+            if name not in self.ids:
+                self.declare(name, ar)
+        for r in split_rules(text):
+            self.add_rule(r)
+
+    def add_rule(self, text: str):
+        self._chk(self.lib.lob_add_rule(self.h, text.encode()))
+
+    def set_option(self, key: str, value: int):
+        self._chk(self.lib.lob_set_option(self.h, key.encode(), int(value)))
+
+    def load(self, name: str, cols, tags=None, samples=None):
+        """cols: (arity, n) array/tensor or a sequence of n-long columns."""
+        rid = self.ids[name]
+        if _is_torch(cols) or (isinstance(cols, (list, tuple)) and cols and _is_torch(cols[0])):
+            import torch
+            c = cols if _is_torch(cols) else torch.stack(list(cols))
+            c = c.to(torch.int32).contiguous()
+            n = c.shape[1]
+            t = tags.to(torch.float32).contiguous() if tags is not None else None
+            s = samples.to(torch.int32).contiguous() if samples is not None else None
+            self._chk(self.lib.lob_load_relation(self.h, rid, c.data_ptr(), t.data_ptr() if t is not None else None,
+                                                 s.data_ptr() if s is not None else None, n, MEM_DEVICE))
+            return
+        c = np.ascontiguousarray(np.asarray(cols, dtype=np.uint32).reshape(len(cols), -1))
+        n = c.shape[1]
+        t = np.ascontiguousarray(np.asarray(tags, np.float32)) if tags is not None else None
+        s = np.ascontiguousarray(np.asarray(samples, np.uint32)) if samples is not None else None
+        self._chk(self.lib.lob_load_relation(self.h, rid, c.ctypes.data, t.ctypes.data if t is not None else None,
+                                             s.ctypes.data if s is not None else None, n, MEM_HOST))
+
+    def run(self, semiring="unit", max_iters: int = 1 << 30) -> dict:
+        sr = SEMIRINGS[semiring] if isinstance(semiring, str) else int(semiring)
+        st = Stats()
+        self._chk(self.lib.lob_run_to_fixpoint(self.h, sr, max_iters, ctypes.byref(st)))
+        return st.as_dict()
+
+    def size(self, name: str) -> int:
+        n = ctypes.c_uint64()
+        self._chk(self.lib.lob_relation_size(self.h, self.ids[name], ctypes.byref(n)))
+        return n.value
+
+    def read(self, name: str, device: bool = False) -> Relation:
+        n = self.size(name)
+        ar = self.arity[name]
+        if device:
+            import torch
+            cols = torch.empty((ar, max(n, 1)), dtype=torch.int32, device="cuda")
+            tags = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+            smp = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+            got = ctypes.c_uint64()
+            self._chk(self.lib.lob_read_relation(self.h, self.ids[name], cols.data_ptr(), tags.data_ptr(),
+                                                 smp.data_ptr(), max(n, 1), ctypes.byref(got), MEM_DEVICE))
+            return Relation(cols[:, :n], tags[:n], smp[:n])
+        cols = np.zeros((ar, max(n, 1)), np.uint32)
+        tags = np.zeros(max(n, 1), np.float32)
+        smp = np.zeros(max(n, 1), np.uint32)
+        got = ctypes.c_uint64()
+        self._chk(self.lib.lob_read_relation(self.h, self.ids[name], cols.ctypes.data, tags.ctypes.data,
+                                             smp.ctypes.data, max(n, 1), ctypes.byref(got), MEM_HOST))
+        return Relation(cols[:, :n], tags[:n], smp[:n])
+
+    def backward(self, out_name: str, grad, grad_inputs: dict):
+        """grad: gradient per fact of out_name (read order).  grad_inputs: name ->
+        float32 array (host) or tensor (device) of the relation's loaded-row count;
+        gradients are added into them."""
+        device = _is_torch(grad)
+        nrel = max(self.ids.values()) + 1
+        ptrs = (ctypes.c_void_p * nrel)()
+        keep = []
+        if device:
+            g = grad.to(dtype=__import__("torch").float32).contiguous()
+            for k, v in grad_inputs.items():
+                ptrs[self.ids[k]] = v.data_ptr()
+            gp = g.data_ptr()
+        else:
+            g = np.ascontiguousarray(np.asarray(grad, np.float32))
+            for k, v in grad_inputs.items():
+                assert v.dtype == np.float32 and v.flags["C_CONTIGUOUS"]
+                ptrs[self.ids[k]] = v.ctypes.data
+            gp = g.ctypes.data
+        keep.append(g)
+        self._chk(self.lib.lob_backward(self.h, self.ids[out_name], gp, ptrs, MEM_DEVICE if device else MEM_HOST))
+
+    def reset(self):
+        self._chk(self.lib.lob_reset(self.h))

@@ -1,0 +1,53 @@
+"""Helpers shared by the engine tests: run the CUDA engine and the CPU oracle on
+the same seeded inputs and compare."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+
+def engine_run(program: str, inputs: dict, semiring: str = "unit", max_iters: int = 1 << 30, options=None,
+               read=None):
+    """Run the CUDA engine.  inputs: name -> (cols, tags, samples).
+    Returns (engine, stats, {relation: Relation})."""
+    from paper_2503_21937_gb300 import Engine
+    e = Engine()
+    e.program(program)
+    for k, v in (options or {}).items():
+        e.set_option(k, v)
+    for name, spec in inputs.items():
+        cols, tags, samples = (list(spec) + [None, None])[:3]
+        if name not in e.ids:
+            e.declare(name, len(cols))
+        e.load(name, cols, None if tags is None else np.asarray(tags, np.float32), samples)
+    st = e.run(semiring, max_iters)
+    names = read if read is not None else list(e.ids)
+    return e, st, {n: e.read(n) for n in names}
+
+
+def oracle_run(program: str, inputs: dict, semiring: str = "unit"):
+    return oracle.run(program, {k: (v[0], None if (len(v) < 2 or v[1] is None) else np.asarray(v[1], np.float32)
+                                    .astype(np.float64), v[2] if len(v) > 2 else None)
+                                for k, v in inputs.items()}, semiring)
+
+
+def compare(program: str, inputs: dict, semiring: str = "unit", rels=None, rtol=1e-5, options=None):
+    """Engine vs oracle: key sets bit-exact, tags per semiring tolerance.
+    Returns (engine stats, oracle result)."""
+    res = oracle_run(program, inputs, semiring)
+    e, st, got = engine_run(program, inputs, semiring, options=options, read=rels)
+    for name, rel in got.items():
+        want = res.relation(name)
+        assert rel.cols.shape == want.cols.shape, (name, rel.cols.shape, want.cols.shape)
+        assert np.array_equal(rel.samples, want.samples), name
+        assert np.array_equal(rel.cols, want.cols), name
+        if semiring in ("max_min", "diff_max_min"):
+            # min / max are exact: the f32 tag equals the oracle's value bitwise
+            assert np.array_equal(rel.tags, want.tags.astype(np.float32)), name
+        elif semiring in ("add_mult", "diff_add_mult"):
+            np.testing.assert_allclose(rel.tags, want.tags, rtol=rtol, atol=0, err_msg=name)
+        else:
+            assert np.all(rel.tags == 1.0)
+    e.close()
+    return st, res

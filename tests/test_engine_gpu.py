@@ -1,0 +1,142 @@
+"""Engine vs oracle parity on the GPU (through the C ABI)."""
+import numpy as np
+import pytest
+
+from paper_2503_21937_gb300 import workloads as W
+from tests.common import compare, engine_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2503_21937_gb300 import build
+    build.build()
+    import torch
+    assert torch.cuda.is_available()
+
+
+# ---------------------------------------------------------------------------
+# unit semiring
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [2, 3, 65, 700])
+def test_tc_chain(n):
+    a, b = W.ktree_chain(n)
+    st, _ = compare(W.TC_PROGRAM, {"edge": ((a, b),)})
+    assert st["derived"] == n * (n - 1) // 2
+
+
+@pytest.mark.parametrize("n,m,seed", [(40, 80, 1), (300, 900, 2), (2000, 5000, 3)])
+def test_tc_random(n, m, seed):
+    a, b = W.erdos_renyi(n, m, seed_index=100 + seed)
+    compare(W.TC_PROGRAM, {"edge": ((a, b),)})
+
+
+def test_tc_config1_full_size():
+    a, b = W.erdos_renyi(1000, 3000)
+    st, res = compare(W.TC_PROGRAM, {"edge": ((a, b),)})
+    assert st["derived"] == res.relation("path").cols.shape[1]
+
+
+def test_sg_random_tree():
+    parent, child, depth = W.random_tree(3000, seed_index=22)
+    st, _ = compare(W.SG_PROGRAM, {"parent": ((parent, child),)})
+
+
+def test_tc_power_law_small():
+    s, d = W.chung_lu_power_law(1500, 6000, seed_index=23)
+    compare(W.TC_PROGRAM, {"edge": ((s, d),)})
+
+
+def test_andersen_small():
+    A = W.andersen_program(4000, 12000, seed_index=33)
+    compare(W.ANDERSEN_PROGRAM, {k: ((v[0], v[1]),) for k, v in A.items()}, rels=["pt"])
+
+
+def test_filters_constants_repeats():
+    edge = (np.array([0, 1, 1, 2, 3, 5, 5], np.uint32), np.array([1, 1, 2, 2, 0, 5, 6], np.uint32))
+    prog = ("loop(x) :- edge(x,x).\n"
+            "fromzero(y) :- edge(0,y).\n"
+            "twohop(x,z) :- edge(x,y), edge(y,z), x != z.\n"
+            "same(x) :- edge(x,y), x == 1.\n"
+            "tagged(x,7) :- edge(x,y), edge(y,x).\n")
+    compare(prog, {"edge": (edge,)})
+
+
+def test_duplicate_inputs_and_empty_relation():
+    a = np.array([0, 0, 1, 1, 2], np.uint32)
+    b = np.array([1, 1, 2, 2, 3], np.uint32)
+    prog = W.TC_PROGRAM + "other(x) :- nothing(x).\n"
+    compare(prog, {"edge": ((a, b),), "nothing": ((np.zeros(0, np.uint32),),)})
+
+
+# ---------------------------------------------------------------------------
+# probabilistic semirings
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("semiring", ["max_min", "add_mult", "diff_max_min", "diff_add_mult"])
+@pytest.mark.parametrize("side", [5, 24])
+def test_grid_reach(semiring, side):
+    g = W.grid_reach_instance(side, sub=side)
+    src, dst, p = g["edge"]
+    compare(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, semiring)
+
+
+@pytest.mark.parametrize("semiring", ["max_min", "add_mult"])
+def test_tc_probabilistic_random(semiring):
+    a, b = W.erdos_renyi(60, 150, seed_index=120)
+    p = W.stream(121).prob(len(a))
+    compare(W.TC_PROGRAM, {"edge": ((a, b), p)}, semiring)
+
+
+@pytest.mark.parametrize("semiring", ["unit", "max_min", "add_mult"])
+def test_kinship_nonlinear(semiring):
+    s = W.stream(130)
+    n, r, a, b, p = W.kinship_instance(s)
+    c1, c2, c3 = W.composition_table()
+    compare(W.KIN_PROGRAM, {"fact": ((r, a, b), p), "comp": ((c1, c2, c3),)}, semiring, rels=["kin"])
+
+
+def test_batched_reach_matches_oracle():
+    B = W.batched_instance(12)
+    e = B["edge"]
+    inputs = {"edge": ((e[0], e[1]), e[2], e[3]), "start": ((B["start"][0],), None, B["start"][2])}
+    for sr in ("unit", "max_min", "add_mult"):
+        compare(W.REACH_PROGRAM, inputs, sr, rels=["reach"])
+
+
+def test_batched_kinship_matches_oracle():
+    B = W.batched_instance(10)
+    f = B["fact"]
+    c = B["comp"]
+    inputs = {"fact": ((f[0], f[1], f[2]), f[3], f[4]), "comp": ((c[0], c[1], c[2]), None, c[4])}
+    compare(W.KIN_PROGRAM, inputs, "add_mult", rels=["kin"])
+
+
+# ---------------------------------------------------------------------------
+# errors
+# ---------------------------------------------------------------------------
+
+def test_max_iters_error_keeps_state():
+    from paper_2503_21937_gb300 import LobsterError
+    a, b = W.ktree_chain(50)
+    with pytest.raises(LobsterError) as ei:
+        engine_run(W.TC_PROGRAM, {"edge": ((a, b),)}, max_iters=3)
+    assert "MAXITER" in str(ei.value)
+
+
+def test_parse_and_unknown_relation_errors():
+    from paper_2503_21937_gb300 import Engine, LobsterError
+    e = Engine()
+    e.declare("edge", 2)
+    e.declare("path", 2)
+    with pytest.raises(LobsterError, match="PARSE"):
+        e.add_rule("path(x,y) :- edge(x,y)")
+    with pytest.raises(LobsterError, match="UNKNOWN_REL"):
+        e.add_rule("path(x,y) :- edgez(x,y).")
+    with pytest.raises(LobsterError, match="UNSAFE"):
+        e.add_rule("path(x,w) :- edge(x,y).")
+    with pytest.raises(LobsterError, match="E_ARG"):
+        e.add_rule("path(x,y) :- edge(x,y,z).")
+    e.close()
