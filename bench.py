@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of the semi-naive fixpoint engine.
+
+Workload (one "step" = every hot-path step, load + fixpoint, on both programs):
+  * same generation on a seeded random tree of 50,000 nodes (branching U{1..4}):
+        sg(x,y) :- parent(p,x), parent(p,y), x != y.
+        sg(x,y) :- parent(a,x), sg(a,b), parent(b,y).
+  * transitive closure on a seeded Chung-Lu power-law digraph (gamma 2.1) of
+    20,000 nodes and 100,000 edges:
+        path(x,y) :- edge(x,y).      path(x,z) :- path(x,y), edge(y,z).
+  unit semiring, u32 ids; metric = derived tuples (|sg| + |path|) per second.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2503_21937_gb300 import workloads as W  # noqa: E402
+
+METRIC = "derived tuples/s (fixpoint)"
+UNIT = "tuples/s"
+WORKLOAD = "same-generation 50k-node random tree + transitive closure 20k-node/100k-edge power-law graph (unit semiring)"
+SG_NODES, TC_NODES, TC_EDGES = 50_000, 20_000, 100_000
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2503_21937_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """dram bytes per launch for `kernel` from the committed ncu summary, or None
+    when the summary was taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("source_hash") != kernel_source_hash():
+        return None
+    k = t.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch_full_size")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_inputs(sg_nodes=SG_NODES, tc_nodes=TC_NODES, tc_edges=TC_EDGES):
+    parent, child, _ = W.random_tree(sg_nodes)
+    s, d = W.chung_lu_power_law(tc_nodes, tc_edges)
+    return {"sg": (W.SG_PROGRAM, {"parent": np.stack([parent, child])}),
+            "tc": (W.TC_PROGRAM, {"edge": np.stack([s, d])})}
+
+
+def cpu_oracle_sample(budget_s: float = 20.0):
+    """Time the oracle on reduced instances of the same generators."""
+    import oracle
+    oracle.build()
+    inputs = make_inputs(sg_nodes=2000, tc_nodes=600, tc_edges=3000)
+    t0 = time.perf_counter()
+    derived = 0
+    reps = 0
+    while True:
+        for name, (prog, rels) in inputs.items():
+            res = oracle.run(prog, {k: (v,) for k, v in rels.items()})
+            head = "sg" if name == "sg" else "path"
+            derived += res.relation(head).cols.shape[1]
+        reps += 1
+        if time.perf_counter() - t0 > budget_s / 2 or reps >= 5:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": derived / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x (same generation on a 2,000-node random tree + transitive closure on a "
+                      f"600-node/3,000-edge power-law graph), naive FP64 std::map oracle, single thread, "
+                      f"{dt:.1f} s"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    inputs = make_inputs(sg_nodes=1500, tc_nodes=500, tc_edges=2500)
+
+    def step():
+        n = 0
+        for name, (prog, rels) in inputs.items():
+            res = oracle.run(prog, {k: (v,) for k, v in rels.items()})
+            n += res.relation("sg" if name == "sg" else "path").cols.shape[1]
+        return n
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    tot = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = tot / dt
+    sample = ("per step: same generation on a 1,500-node random tree + transitive closure on a 500-node/"
+              "2,500-edge power-law graph (reduced instances of the benchmark's generators)")
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": WORKLOAD + " [oracle sample]"},
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ---------------------------------------------------------------------------
+# the engine arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=1, help="extra steps with per-kernel CUDA-event timing")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    from paper_2503_21937_gb300 import Engine, build
+    build.build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    inputs = make_inputs()
+    dev = {name: {k: torch.from_numpy(v.astype(np.int32)).cuda() for k, v in rels.items()}
+           for name, (_, rels) in inputs.items()}
+    engines = {}
+    with torch.cuda.stream(stream):
+        for name, (prog, rels) in inputs.items():
+            e = Engine(stream=stream.cuda_stream)
+            e.program(prog)
+            engines[name] = e
+    heads = {"sg": "sg", "tc": "path"}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def step(profile=False):
+        st_all = {}
+        for name, e in engines.items():
+            e.reset()
+            e.set_option("profile", 1 if profile else 0)
+            for rel, t in dev[name].items():
+                e.load(rel, t)
+            st_all[name] = e.run("unit")
+        return st_all
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, derived, launches, iters = [], [], 0, {}
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.fill_(1)  # L2 flush between timed steps (256 MiB write), outside the timed interval
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = step()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            derived.append(sum(s["derived"] for s in st.values()))
+            launches += sum(s["kernel_launches"] for s in st.values())
+            iters = {k: s["iterations"] for k, s in st.items()}
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = derived[0] * args.steps * world / (total_ms / 1000.0)
+
+    # per-kernel CUDA-event timing on extra steps (not part of the timed value)
+    prof = {}
+    with torch.cuda.stream(stream):
+        for _ in range(args.profile_steps):
+            step(profile=True)
+    for e in engines.values():
+        for k, v in e.profile().items():
+            p = prof.setdefault(k, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+            for f in p:
+                p[f] += v[f]
+        e.profile_reset()
+        e.set_option("profile", 0)
+    peak, peak_kind = load_peaks()
+    tot_k = sum(v["ms"] for v in prof.values()) or 1.0
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 4), "share": round(v["ms"] / tot_k, 4),
+                   "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None,
+                   "frac": round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak, 4) if v["ms"] > 0 else None}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
+    roofline = None
+    if dom:
+        name, v = dom
+        per_launch_bytes = v["bytes"] / v["launches"]
+        per_launch_s = v["ms"] / v["launches"] / 1e3
+        ach = per_launch_bytes / per_launch_s / 1e9
+        roofline = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(ach / peak, 4), "peak_source": peak_kind,
+                    "algorithmic_bytes_per_launch": per_launch_bytes, "traffic": ncu_traffic(name)}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_in = {name: {k: torch.from_numpy(v.astype(np.int32)).pin_memory() for k, v in rels.items()}
+                   for name, (_, rels) in inputs.items()}
+        h2d = sum(t.numel() * 4 for rels in host_in.values() for t in rels.values())
+        outs = {}
+        d2h = 0
+        e2e_ms = []
+        with torch.cuda.stream(stream):
+            for it in range(args.steps + 1):
+                t0 = time.perf_counter()
+                nbytes = 0
+                for name, e in engines.items():
+                    e.reset()
+                    for rel, t in host_in[name].items():
+                        e.load(rel, t.numpy().view(np.uint32))
+                    e.run("unit")
+                    h = heads[name]
+                    n = e.size(h)
+                    if h not in outs or outs[h].shape[1] < n:
+                        outs[h] = torch.empty((2, n), dtype=torch.int32).pin_memory()
+                    e.read_into(h, outs[h].numpy())
+                    nbytes += n * 2 * 4
+                dt = (time.perf_counter() - t0) * 1e3
+                if it > 0:  # first pass allocates the pinned output buffers
+                    e2e_ms.append(dt)
+                d2h = nbytes
+        e2e = {"value": derived[0] / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "sg_tree_nodes": SG_NODES, "tc_nodes": TC_NODES,
+                           "tc_edges": TC_EDGES, "semiring": "unit", "parallelism": "replicas" if world > 1 else "1 GPU",
+                           "l2": "flushed between timed steps (256 MiB write)",
+                           "derived_per_step": derived[0], "iterations": iters},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "kernels": kernels}
+        print(json.dumps(line))
+    for e in engines.values():
+        e.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -152,8 +152,21 @@ int lob_reset(lob_engine* e);
  *   "dense_bits"   largest join-prefix width, in bits, indexed densely (default 24)
  *   "radix_bits"   bits per radix-sort pass, 4..11                  (default 8)
  *   "sync_check"   1: check CUDA errors after every kernel (debug)   (default 0)
+ *   "profile"      1: time every kernel launch with CUDA events      (default 0)
  * LOB_E_ARG for an unknown key or a value out of range. */
 int lob_set_option(lob_engine* e, const char* key, int64_t value);
+
+/* Per-kernel timing (engine option "profile" = 1).  Every kernel launch is
+ * bracketed by CUDA events on the engine's stream; launches, milliseconds and
+ * algorithmic bytes (the bytes the step must read and write, from the sizes
+ * it processes) accumulate per kernel name until lob_profile_reset.
+ * lob_profile_count synchronises the stream and returns the number of names;
+ * lob_profile_entry copies entry i (names in sorted order, NUL-terminated,
+ * truncated to name_cap). */
+int lob_profile_count(lob_engine* e, uint32_t* n);
+int lob_profile_entry(lob_engine* e, uint32_t i, char* name, size_t name_cap, uint64_t* launches, double* ms,
+                      double* bytes);
+int lob_profile_reset(lob_engine* e);
 
 #ifdef __cplusplus
 }

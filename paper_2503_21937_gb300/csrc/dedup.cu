@@ -316,14 +316,19 @@ void dispatch_unique(int key64, const void* keys, const void* tags, u64 n, void*
   u64* tile = reinterpret_cast<u64*>(scratch);
   u64* ws = tile + tiles + 1;
   typedef typename Sem::Cand C;
+  const double kb = key64 ? 8 : 4, cb = Sem::kTags ? sizeof(C) : 0;
   if (key64) {
-    k_unique_count<u64><<<(unsigned)tiles, kUThreads, 0, st>>>((const u64*)keys, n, tile);
-    exclusive_scan<u64, u64>(tile, tile, tiles, count_dev, ws, st);
-    k_unique_write<u64, Sem><<<(unsigned)tiles, kUThreads, 0, st>>>((const u64*)keys, (const C*)tags, n, tile, (u64*)okeys, (C*)otags);
+    { ProfScope ps("unique_count", n * kb, st);
+      k_unique_count<u64><<<(unsigned)tiles, kUThreads, 0, st>>>((const u64*)keys, n, tile); }
+    { ProfScope ps("unique_scan", tiles * 16.0, st); exclusive_scan<u64, u64>(tile, tile, tiles, count_dev, ws, st); }
+    { ProfScope ps("unique_write", n * (kb + cb), st);
+      k_unique_write<u64, Sem><<<(unsigned)tiles, kUThreads, 0, st>>>((const u64*)keys, (const C*)tags, n, tile, (u64*)okeys, (C*)otags); }
   } else {
-    k_unique_count<u32><<<(unsigned)tiles, kUThreads, 0, st>>>((const u32*)keys, n, tile);
-    exclusive_scan<u64, u64>(tile, tile, tiles, count_dev, ws, st);
-    k_unique_write<u32, Sem><<<(unsigned)tiles, kUThreads, 0, st>>>((const u32*)keys, (const C*)tags, n, tile, (u32*)okeys, (C*)otags);
+    { ProfScope ps("unique_count", n * kb, st);
+      k_unique_count<u32><<<(unsigned)tiles, kUThreads, 0, st>>>((const u32*)keys, n, tile); }
+    { ProfScope ps("unique_scan", tiles * 16.0, st); exclusive_scan<u64, u64>(tile, tile, tiles, count_dev, ws, st); }
+    { ProfScope ps("unique_write", n * (kb + cb), st);
+      k_unique_write<u32, Sem><<<(unsigned)tiles, kUThreads, 0, st>>>((const u32*)keys, (const C*)tags, n, tile, (u32*)okeys, (C*)otags); }
   }
 }
 
@@ -341,11 +346,19 @@ void merge_impl(const MergeArgs& a, void* scratch, cudaStream_t st) {
   c.ok = (K*)a.okeys; c.ot = (typename Sem::Stored*)a.otags; c.os = a.ostamp;
   c.rk = (K*)a.rkeys; c.rt = (typename Sem::Stored*)a.rtags;
   c.stamp = a.stamp;
-  k_merge_path<K><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, st>>>(c.fk, a.nf, c.uk, a.nu, tiles + 1, apart);
-  k_diffmerge_count<K, Sem><<<(unsigned)tiles, kMThreads, 0, st>>>(c, apart, tdup, tr);
-  exclusive_scan<u64, u64>(tdup, tdup, tiles, a.counts_dev, ws, st);
-  exclusive_scan<u64, u64>(tr, tr, tiles, a.counts_dev + 1, ws, st);
-  k_diffmerge_write<K, Sem><<<(unsigned)tiles, kMThreads, 0, st>>>(c, apart, tdup, tr);
+  const double kb = sizeof(K), sb = Sem::kTags ? sizeof(typename Sem::Stored) : 0, ub = a.u_stored ? sb : (Sem::kTags ? sizeof(typename Sem::Cand) : 0);
+  const double fsb = a.fstamp ? 4 : 0;
+  { ProfScope ps("merge_path", (tiles + 1) * 8.0, st);
+    k_merge_path<K><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, st>>>(c.fk, a.nf, c.uk, a.nu, tiles + 1, apart); }
+  { ProfScope ps("diffmerge_count", (a.nf + a.nu) * kb, st);
+    k_diffmerge_count<K, Sem><<<(unsigned)tiles, kMThreads, 0, st>>>(c, apart, tdup, tr); }
+  { ProfScope ps("diffmerge_scan", tiles * 32.0, st);
+    exclusive_scan<u64, u64>(tdup, tdup, tiles, a.counts_dev, ws, st);
+    exclusive_scan<u64, u64>(tr, tr, tiles, a.counts_dev + 1, ws, st); }
+  // algorithmic: read F and U once; write F' (<= nf + nu rows) and R (<= nu rows)
+  { ProfScope ps("diffmerge_write", a.nf * (kb + sb + fsb) + a.nu * (kb + ub) + (a.nf + a.nu) * (kb + sb + fsb) +
+                                        (a.rkeys ? a.nu * (kb + sb) : 0.0), st);
+    k_diffmerge_write<K, Sem><<<(unsigned)tiles, kMThreads, 0, st>>>(c, apart, tdup, tr); }
 }
 
 template <class K, class Sem>

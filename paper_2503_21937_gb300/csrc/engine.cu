@@ -21,6 +21,53 @@ bool valid_ident(const char* s);
 int backward_impl(lob_engine* e, u32 out_rel, const float* grad_tags, float* const* grad_inputs, int mem);
 
 static thread_local std::string g_create_err;
+thread_local KernelProfiler* g_prof = nullptr;
+
+// ---------------------------------------------------------------------------
+// per-kernel CUDA-event timing
+// ---------------------------------------------------------------------------
+cudaEvent_t EngineProfiler::take() {
+  if (pool.empty()) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) throw LobError(LOB_E_CUDA, "cudaEventCreate failed");
+    return ev;
+  }
+  cudaEvent_t ev = pool.back();
+  pool.pop_back();
+  return ev;
+}
+void EngineProfiler::begin(const char* name, cudaStream_t st) {
+  cudaEvent_t a = take();
+  cudaEventRecord(a, st);
+  open.push_back({name, a});
+}
+void EngineProfiler::end(const char* name, double bytes, cudaStream_t st) {
+  if (open.empty()) return;
+  cudaEvent_t b = take();
+  cudaEventRecord(b, st);
+  Open o = open.back();
+  open.pop_back();
+  done.push_back({name, o.a, b, bytes});
+}
+void EngineProfiler::flush() {
+  for (auto& d : done) {
+    cudaEventSynchronize(d.b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, d.a, d.b);
+    ProfAgg& g = agg[d.name];
+    g.launches++;
+    g.ms += ms;
+    g.bytes += d.bytes;
+    pool.push_back(d.a);
+    pool.push_back(d.b);
+  }
+  done.clear();
+}
+EngineProfiler::~EngineProfiler() {
+  for (auto& d : done) { cudaEventDestroy(d.a); cudaEventDestroy(d.b); }
+  for (auto& o : open) cudaEventDestroy(o.a);
+  for (auto ev : pool) cudaEventDestroy(ev);
+}
 
 // ---------------------------------------------------------------------------
 // memory and errors
@@ -746,6 +793,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   }
   e.check(cudaEventRecord(ev1, e.stream), "event");
   e.sync();
+  e.prof.flush();
   float ms = 0;
   cudaEventElapsedTime(&ms, ev0, ev1);
   cudaEventDestroy(ev0);
@@ -770,6 +818,10 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
 template <class F>
 static int guarded(lob_engine* e, F&& f) {
   if (!e) return LOB_E_ARG;
+  struct ProfOn {
+    explicit ProfOn(lob_engine* e) { g_prof = e->opt_profile ? &e->prof : nullptr; }
+    ~ProfOn() { g_prof = nullptr; }
+  } on(e);
   try {
     e->err.clear();
     cudaSetDevice(e->device);
@@ -1009,6 +1061,42 @@ int lob_backward(lob_engine* e, uint32_t out_rel, const float* grad_tags, float*
   return guarded(e, [&] { return backward_impl(e, out_rel, grad_tags, grad_inputs, mem); });
 }
 
+int lob_profile_count(lob_engine* e, uint32_t* n) {
+  return guarded(e, [&] {
+    if (!n) throw LobError(LOB_E_ARG, "null n");
+    e->sync();
+    e->prof.flush();
+    *n = (uint32_t)e->prof.agg.size();
+    return LOB_OK;
+  });
+}
+
+int lob_profile_entry(lob_engine* e, uint32_t i, char* name, size_t name_cap, uint64_t* launches, double* ms,
+                      double* bytes) {
+  return guarded(e, [&] {
+    if (i >= e->prof.agg.size()) throw LobError(LOB_E_ARG, "profile index out of range");
+    auto it = e->prof.agg.begin();
+    std::advance(it, i);
+    if (name && name_cap) {
+      std::strncpy(name, it->first.c_str(), name_cap - 1);
+      name[name_cap - 1] = 0;
+    }
+    if (launches) *launches = it->second.launches;
+    if (ms) *ms = it->second.ms;
+    if (bytes) *bytes = it->second.bytes;
+    return LOB_OK;
+  });
+}
+
+int lob_profile_reset(lob_engine* e) {
+  return guarded(e, [&] {
+    e->sync();
+    e->prof.flush();
+    e->prof.agg.clear();
+    return LOB_OK;
+  });
+}
+
 int lob_reset(lob_engine* e) {
   return guarded(e, [&] {
     e->sync();
@@ -1035,6 +1123,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "dense_bits" && value >= 1 && value <= 30) e->opt_dense_bits = (int)value;
     else if (k == "radix_bits" && value >= 4 && value <= 11) e->opt_radix_bits = sort_supported_radix_bits((int)value);
     else if (k == "sync_check" && (value == 0 || value == 1)) e->opt_sync_check = (int)value;
+    else if (k == "profile" && (value == 0 || value == 1)) e->opt_profile = (int)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

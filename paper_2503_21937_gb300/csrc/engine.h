@@ -110,6 +110,31 @@ struct RulePlan {
   std::vector<ArmPlan> arms;
 };
 
+struct ProfAgg {
+  u64 launches = 0;
+  double ms = 0, bytes = 0;
+};
+struct EngineProfiler : KernelProfiler {
+  struct Open {
+    const char* name;
+    cudaEvent_t a;
+  };
+  struct Done {
+    std::string name;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Open> open;
+  std::vector<Done> done;
+  std::map<std::string, ProfAgg> agg;
+  cudaEvent_t take();
+  void begin(const char* name, cudaStream_t st) override;
+  void end(const char* name, double bytes, cudaStream_t st) override;
+  void flush();
+  ~EngineProfiler();
+};
+
 struct lob_engine {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -122,7 +147,8 @@ struct lob_engine {
   std::vector<RuleAst> rules;
   std::vector<RulePlan> plans;
   // options
-  int opt_join_index = 0, opt_dense_bits = 24, opt_radix_bits = 8, opt_sync_check = 0;
+  int opt_join_index = 0, opt_dense_bits = 24, opt_radix_bits = 8, opt_sync_check = 0, opt_profile = 0;
+  EngineProfiler prof;
   // run state
   int state = 0;  // 0 loading, 1 ran
   int semiring = 0;

@@ -327,30 +327,51 @@ template <class Sem> struct ReadL {
 
 }  // namespace
 
+static double input_row_bytes(int sem, const StepParams& P) {
+  const double tb = sem == SR_UNIT ? 0 : (sem == SR_MAX_MIN ? 4 : 8);
+  if (P.in_packed) return (P.in_lay.key64 ? 8 : 4) + (sem == SR_UNIT ? 0 : (sem == SR_DIFF_MAX_MIN ? 8 : 4));
+  return 4.0 * (P.n_in_cols + 1) + tb;
+}
+static double output_row_bytes(int sem, const StepParams& P) {
+  const double tb = sem == SR_UNIT ? 0 : (sem == SR_MAX_MIN ? 4 : 8);
+  if (P.out_packed) return (P.out_lay.key64 ? 8 : 4) + tb;
+  return 4.0 * (P.n_out_cols + 1) + tb;
+}
+
 void join_count(int sem, const StepParams& P, cudaStream_t st) {
+  // read each input row once, two index words per row, write count + lo
+  ProfScope ps("join_count", P.n_in * (input_row_bytes(sem, P) + 16.0 + 12.0), st);
   if (P.n_in) by_sem<CountL>(sem, P, st);
 }
 
 void lbs_partition(const u64* off, u64 n_in, u64 total, u64* part, cudaStream_t st) {
   const u64 ntiles = (total + kEmitTile - 1) / kEmitTile;
+  ProfScope ps("join_partition", (ntiles + 1) * 8.0, st);
   k_lbs_partition<<<(unsigned)((ntiles + 1 + 255) / 256), 256, 0, st>>>(off, n_in, ntiles, part);
 }
 
 void join_emit(int sem, const StepParams& P, const u64* part, cudaStream_t st) {
+  // read the input rows and their offsets once, each matched view row once,
+  // write every output row once
+  const double vb = (P.v_lay.key64 ? 8 : 4) + (sem == SR_UNIT ? 0 : (sem == SR_DIFF_MAX_MIN ? 8 : 4));
+  ProfScope ps("join_emit", P.n_in * (input_row_bytes(sem, P) + 16.0) + P.total * (vb + output_row_bytes(sem, P)), st);
   if (P.total) by_sem<EmitL>(sem, P, part, st);
 }
 
 void project_rows(int sem, const StepParams& P, cudaStream_t st) {
+  ProfScope ps("project", P.n_in * (input_row_bytes(sem, P) + output_row_bytes(sem, P)), st);
   if (P.n_in) by_sem<ProjL>(sem, P, st);
 }
 
 void build_dense_index(const Layout& L, int prefix_len, const void* keys, u64 n, u64* offs, u64 domain, cudaStream_t st) {
+  ProfScope ps("index_build", (domain + 1) * 8.0 + n * (L.key64 ? 8.0 : 4.0), st);
   k_dense_index<<<grid_for(domain + 1), 256, 0, st>>>(keys, L.key64, n, rest_shift(L, prefix_len), offs, domain);
 }
 
 void repack_keys(const Layout& from, const int* perm_from, const Layout& to, const int* perm_to, const void* in, void* out,
                  u64 n, cudaStream_t st) {
   if (!n) return;
+  ProfScope ps("view_repack", n * ((from.key64 ? 8.0 : 4.0) + (to.key64 ? 8.0 : 4.0)), st);
   Perm a, b;
   for (int j = 0; j < kMaxArity; j++) {
     a.p[j] = j < from.arity ? perm_from[j] : 0;
@@ -361,6 +382,7 @@ void repack_keys(const Layout& from, const int* perm_from, const Layout& to, con
 
 void pack_rows(const Layout& L, const u32* cols, u64 stride, const u32* samples, u64 n, void* keys, u32* rows,
                cudaStream_t st) {
+  ProfScope ps("load_pack", n * (4.0 * L.arity + (samples ? 4.0 : 0.0) + (L.key64 ? 8.0 : 4.0) + 4.0), st);
   if (n) k_pack_rows<<<grid_for(n), 256, 0, st>>>(L, cols, stride, samples, n, keys, rows);
 }
 

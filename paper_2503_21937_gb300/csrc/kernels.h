@@ -5,6 +5,28 @@
 #include "common.cuh"
 
 // ---------------------------------------------------------------------------
+// per-kernel timing (CUDA events on the launching stream), enabled per engine
+// ---------------------------------------------------------------------------
+struct KernelProfiler {
+  virtual void begin(const char* name, cudaStream_t st) = 0;
+  // `bytes`: algorithmic bytes of this launch (what the step must read + write)
+  virtual void end(const char* name, double bytes, cudaStream_t st) = 0;
+  virtual ~KernelProfiler() {}
+};
+extern thread_local KernelProfiler* g_prof;
+struct ProfScope {
+  const char* name;
+  double bytes;
+  cudaStream_t st;
+  ProfScope(const char* n, double b, cudaStream_t s) : name(n), bytes(b), st(s) {
+    if (g_prof) g_prof->begin(name, st);
+  }
+  ~ProfScope() {
+    if (g_prof) g_prof->end(name, bytes, st);
+  }
+};
+
+// ---------------------------------------------------------------------------
 // radix sort (sort.cu)
 // ---------------------------------------------------------------------------
 int sort_supported_radix_bits(int rb);

@@ -108,10 +108,20 @@ void sort_impl(void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits,
   K* dst_k = reinterpret_cast<K*>(ktmp);
   P* src_p = reinterpret_cast<P*>(*pay);
   P* dst_p = reinterpret_cast<P*>(ptmp);
+  constexpr double kb = sizeof(K), pb = std::is_same<P, NoPay>::value ? 0 : sizeof(P);
   for (int shift = 0; shift < bits; shift += RB) {
-    k_radix_upsweep<K, RB><<<(unsigned)ntiles, kSortThreads, 0, st>>>(src_k, n, shift, hist, ntiles);
-    exclusive_scan<u32, u32>(hist, hist, (u64)D * ntiles, nullptr, scan_ws, st);
-    k_radix_scatter<K, P, RB><<<(unsigned)ntiles, kSortThreads, 0, st>>>(src_k, src_p, dst_k, dst_p, n, shift, hist, ntiles);
+    {
+      ProfScope ps("radix_upsweep", n * kb + (double)D * ntiles * 4, st);
+      k_radix_upsweep<K, RB><<<(unsigned)ntiles, kSortThreads, 0, st>>>(src_k, n, shift, hist, ntiles);
+    }
+    {
+      ProfScope ps("radix_digit_scan", (double)D * ntiles * 8, st);
+      exclusive_scan<u32, u32>(hist, hist, (u64)D * ntiles, nullptr, scan_ws, st);
+    }
+    {
+      ProfScope ps("radix_scatter", 2.0 * n * (kb + pb) + (double)D * ntiles * 4, st);
+      k_radix_scatter<K, P, RB><<<(unsigned)ntiles, kSortThreads, 0, st>>>(src_k, src_p, dst_k, dst_p, n, shift, hist, ntiles);
+    }
     std::swap(src_k, dst_k);
     std::swap(src_p, dst_p);
   }

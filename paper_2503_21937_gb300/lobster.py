@@ -29,7 +29,8 @@ MEM_HOST, MEM_DEVICE = 0, 1
 # every symbol declared in include/lobster.h (checked by the tests)
 EXPORTS = ["lob_create", "lob_destroy", "lob_last_error", "lob_declare_relation", "lob_relation_id",
            "lob_load_relation", "lob_add_rule", "lob_run_to_fixpoint", "lob_relation_size", "lob_read_relation",
-           "lob_backward", "lob_reset", "lob_set_option"]
+           "lob_backward", "lob_reset", "lob_set_option", "lob_profile_count", "lob_profile_entry",
+           "lob_profile_reset"]
 
 _lib = None
 
@@ -73,6 +74,10 @@ def load_library(path: str = LIB_PATH):
     lib.lob_backward.argtypes = [vp, u32, vp, vp, ctypes.c_int]
     lib.lob_reset.argtypes = [vp]
     lib.lob_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_int64]
+    lib.lob_profile_count.argtypes = [vp, P(u32)]
+    lib.lob_profile_entry.argtypes = [vp, u32, ctypes.c_char_p, ctypes.c_size_t, P(u64), P(ctypes.c_double),
+                                      P(ctypes.c_double)]
+    lib.lob_profile_reset.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -223,6 +228,17 @@ class Engine:
                                              smp.ctypes.data, max(n, 1), ctypes.byref(got), MEM_HOST))
         return Relation(cols[:, :n], tags[:n], smp[:n])
 
+    def read_into(self, name: str, cols, tags=None, samples=None) -> int:
+        """Read into preallocated host arrays: cols (arity, capacity) uint32/int32
+        C-contiguous, tags/samples (capacity,) or None.  Returns the row count."""
+        cap = cols.shape[1]
+        got = ctypes.c_uint64()
+        self._chk(self.lib.lob_read_relation(self.h, self.ids[name], cols.ctypes.data,
+                                             tags.ctypes.data if tags is not None else None,
+                                             samples.ctypes.data if samples is not None else None, cap,
+                                             ctypes.byref(got), MEM_HOST))
+        return got.value
+
     def backward(self, out_name: str, grad, grad_inputs: dict):
         """grad: gradient per fact of out_name (read order).  grad_inputs: name ->
         float32 array (host) or tensor (device) of the relation's loaded-row count;
@@ -247,3 +263,19 @@ class Engine:
 
     def reset(self):
         self._chk(self.lib.lob_reset(self.h))
+
+    def profile(self) -> dict:
+        """kernel name -> {launches, ms, bytes} accumulated since the last profile_reset."""
+        n = ctypes.c_uint32()
+        self._chk(self.lib.lob_profile_count(self.h, ctypes.byref(n)))
+        out = {}
+        buf = ctypes.create_string_buffer(128)
+        for i in range(n.value):
+            la, ms, by = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
+            self._chk(self.lib.lob_profile_entry(self.h, i, buf, 128, ctypes.byref(la), ctypes.byref(ms),
+                                                 ctypes.byref(by)))
+            out[buf.value.decode()] = {"launches": la.value, "ms": ms.value, "bytes": by.value}
+        return out
+
+    def profile_reset(self):
+        self._chk(self.lib.lob_profile_reset(self.h))
