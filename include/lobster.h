@@ -168,6 +168,29 @@ int lob_profile_entry(lob_engine* e, uint32_t i, char* name, size_t name_cap, ui
                       double* bytes);
 int lob_profile_reset(lob_engine* e);
 
+/* Allocation-free sort + deduplication of a small batch of rows.  The paper
+ * has no counterpart to this call; it exists for callers that cannot allocate
+ * device memory when they need the step: latency-critical paths where
+ * cudaMalloc / cudaFree would synchronise the device, plug-ins inside an
+ * application that owns and budgets all device memory, and processes that have
+ * split the GPU's memory among tenants ahead of time.
+ *   cols      device memory, arity x n u32, column-major (arity 1 or 2)
+ *   out_cols  device memory, arity x n u32, column-major with stride n; gets
+ *             the distinct rows in lexicographic order
+ *   n_out     device memory, one u64; gets the number of distinct rows
+ * The call works in one fixed scratch array compiled into the library (about
+ * 4.3 MB, held on every GPU that loads the library until the process exits)
+ * and allocates nothing.  n > LOB_NOALLOC_MAX_ROWS returns LOB_E_CAPACITY;
+ * a bad arity or a null pointer returns LOB_E_ARG.  The first call on a device
+ * looks up the scratch array's device address; make that first call before
+ * any stream capture.  All calls on a device share the scratch array, so
+ * calls whose work overlaps on the GPU race: order them (one stream, or
+ * events).  A row whose every column is 0xFFFFFFFF is dropped.  The work is
+ * queued on cuda_stream (NULL: legacy default stream); the call does not wait. */
+#define LOB_NOALLOC_MAX_ROWS 262144u
+int lob_unique_rows_noalloc(const uint32_t* cols, uint32_t arity, uint64_t n, uint32_t* out_cols, uint64_t* n_out,
+                            void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

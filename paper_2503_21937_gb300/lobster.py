@@ -30,7 +30,8 @@ MEM_HOST, MEM_DEVICE = 0, 1
 EXPORTS = ["lob_create", "lob_destroy", "lob_last_error", "lob_declare_relation", "lob_relation_id",
            "lob_load_relation", "lob_add_rule", "lob_run_to_fixpoint", "lob_relation_size", "lob_read_relation",
            "lob_backward", "lob_reset", "lob_set_option", "lob_profile_count", "lob_profile_entry",
-           "lob_profile_reset"]
+           "lob_profile_reset", "lob_unique_rows_noalloc"]
+NOALLOC_MAX_ROWS = 262144
 
 _lib = None
 
@@ -78,6 +79,7 @@ def load_library(path: str = LIB_PATH):
     lib.lob_profile_entry.argtypes = [vp, u32, ctypes.c_char_p, ctypes.c_size_t, P(u64), P(ctypes.c_double),
                                       P(ctypes.c_double)]
     lib.lob_profile_reset.argtypes = [vp]
+    lib.lob_unique_rows_noalloc.argtypes = [vp, u32, u64, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -112,6 +114,18 @@ def _torch_stream():
     except Exception:
         pass
     return None
+
+
+def unique_rows_noalloc(cols, out_cols, n_out, stream=None) -> int:
+    """Distinct rows of a (arity, n) int32 CUDA tensor, sorted, written into the
+    caller's out_cols ((arity, n) int32 CUDA tensor) and n_out (one int64 CUDA
+    element), without any device allocation by the library.  Returns the status
+    code of lob_unique_rows_noalloc (0 on success)."""
+    lib = load_library()
+    arity, n = cols.shape
+    stream = _torch_stream() if stream is None else stream
+    return lib.lob_unique_rows_noalloc(cols.data_ptr(), arity, n, out_cols.data_ptr(), n_out.data_ptr(),
+                                       ctypes.c_void_p(stream) if stream else None)
 
 
 @dataclass
