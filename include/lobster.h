@@ -168,6 +168,35 @@ int lob_profile_entry(lob_engine* e, uint32_t i, char* name, size_t name_cap, ui
                       double* bytes);
 int lob_profile_reset(lob_engine* e);
 
+/* Kernel-level primitives on caller device buffers (mem = device), used by the
+ * kernel tests and microbenchmarks.  They use the engine's stream and scratch
+ * buffers, leave its relations untouched and synchronise before returning.
+ *
+ * lob_prim_sort: stable LSD radix sort (the APM `sort`, Sec. 3.2) of n keys
+ * (key_bytes 4 or 8) on their low key_bits bits, in place, with an optional
+ * payload (payload_bytes 0, 4 or 8) moved along; n < 2^32. */
+int lob_prim_sort(lob_engine* e, void* keys, void* payload, uint64_t n, uint32_t key_bits, uint32_t key_bytes,
+                  uint32_t payload_bytes);
+/* lob_prim_exclusive_scan: out[i] = in[0] + ... + in[i-1] (the APM `scan`);
+ * *total (host) = sum of all n inputs. */
+int lob_prim_exclusive_scan(lob_engine* e, const uint32_t* in, uint64_t* out, uint64_t n, uint64_t* total);
+/* lob_prim_unique: collapse runs of equal keys of a sorted array (the APM
+ * `unique<(+)>`), reducing the run's tags with the semiring's (+) (tags:
+ * none for LOB_UNIT, f32 for max-min, f64 unclamped sums for the add-mult
+ * semirings, u64 (value bits << 32 | 0xFFFFFFFF - id) for diff-max-min).  The
+ * all-ones key is treated as absent.  *n_out (host) = number of distinct keys. */
+int lob_prim_unique(lob_engine* e, int semiring, const void* keys, const void* tags, uint64_t n, uint32_t key_bytes,
+                    void* out_keys, void* out_tags, uint64_t* n_out);
+/* lob_prim_diff_merge: with F (sorted, distinct keys, stored tags) and U
+ * (sorted, distinct keys, candidate tags as for lob_prim_unique), write
+ * out = F merged with the keys of U not in F (for the idempotent semirings a
+ * key of U in F replaces F's tag when U's is larger) and r = the new or
+ * improved facts of U (the delta-vs-full difference).  out needs room for
+ * nf + nu rows, r for nu rows; *n_out and *n_r (host) get their sizes. */
+int lob_prim_diff_merge(lob_engine* e, int semiring, const void* f_keys, const void* f_tags, uint64_t nf,
+                        const void* u_keys, const void* u_tags, uint64_t nu, uint32_t key_bytes, void* out_keys,
+                        void* out_tags, void* r_keys, void* r_tags, uint64_t* n_out, uint64_t* n_r);
+
 /* Allocation-free sort + deduplication of a small batch of rows.  The paper
  * has no counterpart to this call; it exists for callers that cannot allocate
  * device memory when they need the step: latency-critical paths where

@@ -18,15 +18,24 @@ LOB_DEV bool is_head(const K* keys, u64 idx, K k) {
   return k != invalid_key<K>() && (idx == 0 || keys[idx - 1] != k);
 }
 
+// Both unique kernels walk a 4096-key tile in 16 rounds of 256 consecutive
+// keys (coalesced loads); element i is a run head when it differs from i-1.
 template <class K>
 __global__ void __launch_bounds__(kUThreads) k_unique_count(const K* __restrict__ keys, u64 n, u64* __restrict__ tile_cnt) {
   __shared__ u64 sm[kUThreads / 32 + 1];
-  const u64 base = (u64)blockIdx.x * kUTile + (u64)threadIdx.x * kUItems;
+  const u64 base = (u64)blockIdx.x * kUTile;
+  K cur[kUItems], prev[kUItems];
+#pragma unroll
+  for (int i = 0; i < kUItems; i++) {  // all loads first
+    const u64 idx = base + (u64)i * kUThreads + threadIdx.x;
+    cur[i] = idx < n ? keys[idx] : invalid_key<K>();
+    prev[i] = (idx < n && idx > 0) ? keys[idx - 1] : invalid_key<K>();
+  }
   u64 c = 0;
 #pragma unroll
   for (int i = 0; i < kUItems; i++) {
-    u64 idx = base + i;
-    if (idx < n) c += is_head(keys, idx, keys[idx]);
+    const u64 idx = base + (u64)i * kUThreads + threadIdx.x;
+    c += idx < n && cur[i] != invalid_key<K>() && (idx == 0 || prev[i] != cur[i]);
   }
   u64 total;
   block_exclusive_sum<u64>(c, sm, &total);
@@ -37,28 +46,45 @@ template <class K, class Sem>
 __global__ void __launch_bounds__(kUThreads) k_unique_write(const K* __restrict__ keys, const typename Sem::Cand* __restrict__ tags,
                                                             u64 n, const u64* __restrict__ tile_off, K* __restrict__ okeys,
                                                             typename Sem::Cand* __restrict__ otags) {
-  __shared__ u64 sm[kUThreads / 32 + 1];
-  const u64 base = (u64)blockIdx.x * kUTile + (u64)threadIdx.x * kUItems;
+  __shared__ u32 wsum[kUThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const u64 base = (u64)blockIdx.x * kUTile;
+  u64 o = tile_off[blockIdx.x];
+  K cur[kUItems];
   u32 heads = 0;
 #pragma unroll
-  for (int i = 0; i < kUItems; i++) {
-    u64 idx = base + i;
-    if (idx < n && is_head(keys, idx, keys[idx])) heads |= 1u << i;
+  for (int i = 0; i < kUItems; i++) {  // all loads first
+    const u64 idx = base + (u64)i * kUThreads + threadIdx.x;
+    cur[i] = idx < n ? keys[idx] : invalid_key<K>();
+    const K pv = (idx < n && idx > 0) ? keys[idx - 1] : invalid_key<K>();
+    heads |= (u32)(idx < n && cur[i] != invalid_key<K>() && (idx == 0 || pv != cur[i])) << i;
   }
-  u64 total;
-  u64 o = tile_off[blockIdx.x] + block_exclusive_sum<u64>((u64)__popc(heads), sm, &total);
 #pragma unroll 1
   for (int i = 0; i < kUItems; i++) {
-    if (!(heads >> i & 1u)) continue;
-    const u64 idx = base + i;
-    const K k = keys[idx];
-    okeys[o] = k;
-    if constexpr (Sem::kTags) {
-      typename Sem::Cand acc = tags[idx];
-      for (u64 j = idx + 1; j < n && keys[j] == k; j++) acc = Sem::add(acc, tags[j]);
-      otags[o] = acc;
+    const u64 idx = base + (u64)i * kUThreads + threadIdx.x;
+    const K k = cur[i];
+    const bool head = heads >> i & 1u;
+    const u32 bal = __ballot_sync(0xFFFFFFFFu, head);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    u32 before = 0, round = 0;
+#pragma unroll
+    for (int w = 0; w < kUThreads / 32; w++) {
+      const u32 c = wsum[w];
+      before += w < warp ? c : 0u;
+      round += c;
     }
-    o++;
+    if (head) {
+      const u64 pos = o + before + __popc(bal & ((1u << lane) - 1u));
+      okeys[pos] = k;
+      if constexpr (Sem::kTags) {
+        typename Sem::Cand acc = tags[idx];
+        for (u64 j = idx + 1; j < n && keys[j] == k; j++) acc = Sem::add(acc, tags[j]);
+        otags[pos] = acc;
+      }
+    }
+    o += round;
+    __syncthreads();
   }
 }
 
@@ -100,8 +126,18 @@ LOB_DEV MergeTile<K> load_merge_tile(const K* A, u64 na, const K* B, u64 nb, con
   const u64 b1 = d1 - a1;
   t.na_t = a1 - t.a0;
   t.nb_t = b1 - t.b0;
-  for (u64 i = threadIdx.x; i < t.na_t; i += kMThreads) sk[i] = A[t.a0 + i];
-  for (u64 i = threadIdx.x; i < t.nb_t; i += kMThreads) sk[t.na_t + i] = B[t.b0 + i];
+  K v[kMItems];
+  const u64 nt = t.na_t + t.nb_t;
+#pragma unroll
+  for (int j = 0; j < kMItems; j++) {  // coalesced, all loads in flight together
+    const u64 i = (u64)j * kMThreads + threadIdx.x;
+    v[j] = i < t.na_t ? A[t.a0 + i] : (i < nt ? B[t.b0 + (i - t.na_t)] : K(0));
+  }
+#pragma unroll
+  for (int j = 0; j < kMItems; j++) {
+    const u64 i = (u64)j * kMThreads + threadIdx.x;
+    if (i < nt) sk[i] = v[j];
+  }
   __syncthreads();
   return t;
 }

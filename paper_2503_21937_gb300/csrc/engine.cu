@@ -90,7 +90,7 @@ void* lob_engine::dalloc(size_t bytes) {
   void* p = nullptr;
   if (custom_alloc) {
     p = alloc.alloc(bytes, stream, alloc.ctx);
-  } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+  } else if (cudaMallocFromPoolAsync(&p, bytes, pool, stream) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
   }
@@ -364,6 +364,16 @@ static void prepare(lob_engine& e, int sem) {
     for (size_t i = 0; i < R.body.size(); i++) p.arms.push_back(plan_arm(e, R, (int)i, idem));
     e.plans.push_back(std::move(p));
   }
+  // A secondary view is merged every iteration only if an arm whose delta
+  // relation can have recent facts after iteration 1 (a rule head) probes it;
+  // arms whose delta is a plain input relation run in iteration 1 only.  The
+  // add-mult runs keep every view current (their views carry stamps).
+  for (auto& p : e.plans)
+    for (auto& A : p.arms) {
+      const bool late = e.rels[p.ast.body[A.delta].rel].idb || sem_stamps(sem);
+      for (size_t s = 1; s < A.steps.size(); s++)
+        if (late) e.rels[p.ast.body[A.steps[s].atom].rel].views[A.steps[s].view].maintained = true;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -509,6 +519,25 @@ static void ensure_index(lob_engine& e, ViewSt& v, int prefix) {
   I.valid = true;
 }
 
+// Re-derive a secondary view from the primary view (tags as payload).
+static void rebuild_view(lob_engine& e, RelSt& r, ViewSt& W) {
+  const ViewSt& V = r.views[0];
+  const int sb = stored_bytes(e.semiring), kb = W.lay.key64 ? 8 : 4;
+  if (sem_stamps(e.semiring)) throw LobError(LOB_E_STATE, "stale view in a stamped run");
+  W.n = V.n;
+  if (V.n) {
+    auto kt = sort_view_rows(e, r, W, V.keys.p, V.tags.p, V.n);
+    e.ensure(W.keys, V.n * kb);
+    e.check(cudaMemcpyAsync(W.keys.p, kt.first, V.n * kb, cudaMemcpyDeviceToDevice, e.stream), "view keys");
+    if (sb) {
+      e.ensure(W.tags, V.n * sb);
+      e.check(cudaMemcpyAsync(W.tags.p, kt.second, V.n * sb, cudaMemcpyDeviceToDevice, e.stream), "view tags");
+    }
+  }
+  W.stale = false;
+  for (auto& kv : W.index) kv.second.valid = false;
+}
+
 static void fill_filters(const RuleAst& R, const std::vector<int>& fs, FilterP* out, int& n) {
   n = 0;
   for (int f : fs) {
@@ -577,6 +606,7 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
     const bool last = s + 1 == A.steps.size();
     RelSt& V = e.rels[R.body[S.atom].rel];
     ViewSt& W = V.views[S.view];
+    if (W.stale) rebuild_view(e, V, W);
     if (!W.n) return;
     ensure_index(e, W, S.prefix_len);
     P.has_probe = 1;
@@ -719,6 +749,10 @@ static void dedup_relation(lob_engine& e, RelSt& H, u32 k) {
   // secondary views receive the same new / improved facts
   for (size_t vi = 1; vi < H.views.size(); vi++) {
     ViewSt& W = H.views[vi];
+    if (!W.maintained) {
+      W.stale = true;
+      continue;
+    }
     auto kt = sort_view_rows(e, H, W, H.nkeys.p, H.ntags.p, nr);
     e.ensure(W.keys2, (W.n + nr) * kb);
     if (sb) e.ensure(W.tags2, (W.n + nr) * sb);
@@ -858,9 +892,27 @@ int lob_create(lob_engine** out, const lob_alloc* alloc, void* cuda_stream) {
     e->alloc = *alloc;
     e->custom_alloc = true;
   }
+  if (!e->custom_alloc) {
+    // Sec. 4.1 (buffer reuse): an engine-owned pool whose release threshold
+    // keeps freed blocks reserved, so repeated runs do not map memory again.
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = e->device;
+    uint64_t keep = ~0ull;
+    if (cudaMemPoolCreate(&e->pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(e->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaGetLastError();
+      g_create_err = "cudaMemPoolCreate failed";
+      if (e->pool) cudaMemPoolDestroy(e->pool);
+      delete e;
+      return LOB_E_CUDA;
+    }
+  }
   if (cudaMallocHost(&e->pinned, 64 * sizeof(u64)) != cudaSuccess) {
     cudaGetLastError();
     g_create_err = "pinned host allocation failed";
+    if (e->pool) cudaMemPoolDestroy(e->pool);
     delete e;
     return LOB_E_CUDA;
   }
@@ -871,6 +923,7 @@ int lob_create(lob_engine** out, const lob_alloc* alloc, void* cuda_stream) {
   if (rc != LOB_OK) {
     g_create_err = e->err;
     cudaFreeHost(e->pinned);
+    if (e->pool) cudaMemPoolDestroy(e->pool);
     delete e;
     return rc;
   }
@@ -887,6 +940,7 @@ void lob_destroy(lob_engine* e) {
     cudaStreamSynchronize(e->stream);
   } catch (...) {
   }
+  if (e->pool) cudaMemPoolDestroy(e->pool);
   cudaFreeHost(e->pinned);
   delete e;
 }
@@ -1093,6 +1147,93 @@ int lob_profile_reset(lob_engine* e) {
     e->sync();
     e->prof.flush();
     e->prof.agg.clear();
+    return LOB_OK;
+  });
+}
+
+int lob_prim_sort(lob_engine* e, void* keys, void* payload, uint64_t n, uint32_t key_bits, uint32_t key_bytes,
+                  uint32_t payload_bytes) {
+  return guarded(e, [&] {
+    if ((key_bytes != 4 && key_bytes != 8) || (payload_bytes != 0 && payload_bytes != 4 && payload_bytes != 8) ||
+        key_bits > key_bytes * 8 || (n && !keys) || (n && payload_bytes && !payload))
+      throw LobError(LOB_E_ARG, "bad sort arguments");
+    if (n > 0xFFFFFFFFull) throw LobError(LOB_E_ARG, "sort supports fewer than 2^32 keys");
+    if (n < 2) return LOB_OK;
+    e->ensure(e->tmp_keys, n * key_bytes);
+    if (payload_bytes) e->ensure(e->tmp_tags, n * payload_bytes);
+    scratch_at_least(*e, sort_scratch_bytes(n, e->opt_radix_bits));
+    void* k = keys;
+    void* p = payload;
+    sort_pairs(key_bytes == 8, payload_bytes, &k, &p, e->tmp_keys.p, e->tmp_tags.p, n, (int)key_bits, e->opt_radix_bits,
+               e->scratch.p, e->stream);
+    e->after_launch("sort");
+    if (k != keys) e->check(cudaMemcpyAsync(keys, k, n * key_bytes, cudaMemcpyDeviceToDevice, e->stream), "copy back");
+    if (payload_bytes && p != payload)
+      e->check(cudaMemcpyAsync(payload, p, n * payload_bytes, cudaMemcpyDeviceToDevice, e->stream), "copy back");
+    e->sync();
+    return LOB_OK;
+  });
+}
+
+int lob_prim_exclusive_scan(lob_engine* e, const uint32_t* in, uint64_t* out, uint64_t n, uint64_t* total) {
+  return guarded(e, [&] {
+    if ((n && (!in || !out)) || !total) throw LobError(LOB_E_ARG, "bad scan arguments");
+    scratch_at_least(*e, scan_scratch_elems(n) * 8 + 64);
+    exclusive_scan<u32, u64>(in, reinterpret_cast<u64*>(out), n, e->counts.as<u64>(), e->scratch.as<u64>(), e->stream);
+    e->after_launch("scan");
+    *total = e->read_u64(e->counts.as<u64>());
+    return LOB_OK;
+  });
+}
+
+int lob_prim_unique(lob_engine* e, int semiring, const void* keys, const void* tags, uint64_t n, uint32_t key_bytes,
+                    void* out_keys, void* out_tags, uint64_t* n_out) {
+  return guarded(e, [&] {
+    if (semiring < 0 || semiring > 4 || (key_bytes != 4 && key_bytes != 8) || !n_out || (n && (!keys || !out_keys)) ||
+        (n && semiring != LOB_UNIT && (!tags || !out_tags)))
+      throw LobError(LOB_E_ARG, "bad unique arguments");
+    scratch_at_least(*e, unique_scratch_bytes(n));
+    unique_run(sem_kernel(semiring), key_bytes == 8, keys, tags, n, out_keys, out_tags, e->counts.as<u64>() + 1,
+               e->scratch.p, e->stream);
+    e->after_launch("unique");
+    *n_out = e->read_u64(e->counts.as<u64>() + 1);
+    return LOB_OK;
+  });
+}
+
+int lob_prim_diff_merge(lob_engine* e, int semiring, const void* f_keys, const void* f_tags, uint64_t nf,
+                        const void* u_keys, const void* u_tags, uint64_t nu, uint32_t key_bytes, void* out_keys,
+                        void* out_tags, void* r_keys, void* r_tags, uint64_t* n_out, uint64_t* n_r) {
+  return guarded(e, [&] {
+    if (semiring < 0 || semiring > 4 || (key_bytes != 4 && key_bytes != 8) || !n_out || !n_r)
+      throw LobError(LOB_E_ARG, "bad merge arguments");
+    if (!nu) {
+      *n_out = nf;
+      *n_r = 0;
+      if (nf) {
+        e->check(cudaMemcpyAsync(out_keys, f_keys, nf * key_bytes, cudaMemcpyDeviceToDevice, e->stream), "copy");
+        const int sb = stored_bytes(semiring);
+        if (sb) e->check(cudaMemcpyAsync(out_tags, f_tags, nf * sb, cudaMemcpyDeviceToDevice, e->stream), "copy");
+      }
+      e->sync();
+      return LOB_OK;
+    }
+    MergeArgs M{};
+    M.sem = sem_kernel(semiring);
+    M.key64 = key_bytes == 8;
+    M.fkeys = f_keys; M.ftags = f_tags; M.fstamp = nullptr; M.nf = nf;
+    M.ukeys = u_keys; M.utags = u_tags; M.nu = nu; M.u_stored = 0;
+    M.okeys = out_keys; M.otags = out_tags; M.ostamp = nullptr;
+    M.rkeys = r_keys; M.rtags = r_tags;
+    M.stamp = 1;
+    M.counts_dev = e->counts.as<u64>() + 2;
+    scratch_at_least(*e, merge_scratch_bytes(nf, nu));
+    diff_merge(M, e->scratch.p, e->stream);
+    e->after_launch("merge");
+    e->check(cudaMemcpyAsync(e->pinned, e->counts.as<u64>() + 2, 16, cudaMemcpyDeviceToHost, e->stream), "counts");
+    e->sync();
+    *n_out = nf + nu - e->pinned[0];
+    *n_r = e->pinned[1];
     return LOB_OK;
   });
 }

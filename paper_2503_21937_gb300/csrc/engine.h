@@ -60,6 +60,8 @@ struct ViewSt {
   DevBuf keys2, tags2, stamps2;  // merge target
   u64 n = 0;
   bool probed = false;
+  bool maintained = false;  // merged with new facts every iteration
+  bool stale = false;       // behind the primary view; rebuilt before its next probe
   std::map<int, IndexSt> index;  // by prefix length
 };
 
@@ -138,6 +140,7 @@ struct EngineProfiler : KernelProfiler {
 struct lob_engine {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;  // engine-owned pool; freed blocks stay reserved for reuse
   lob_alloc alloc{};
   bool custom_alloc = false;
   std::string err;

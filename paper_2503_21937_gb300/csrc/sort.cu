@@ -3,13 +3,16 @@
 // the Stratum rule of the appendix).
 //
 // One pass per RB-bit digit, least significant first.  Each pass:
-//   1. upsweep: per 4096-key tile, a digit histogram in shared memory;
+//   1. upsweep: per 4096-key tile, a digit histogram (per-warp shared-memory
+//      counters);
 //   2. scan of the digit-major histogram matrix -> each (digit, tile) output base;
-//   3. scatter: each warp ranks its 512 keys stably with __match_any_sync
-//      (keys with equal digits in one 32-key round get consecutive ranks in lane
-//      order; a per-warp running count carries ranks across rounds), warps are
-//      combined per digit in shared memory, and every key is written to
-//      base + rank.  Rank order = input order, so each pass is stable.
+//   3. scatter: each warp ranks its keys stably with a ballot multisplit (keys
+//      with equal digits in one 32-key round -- found by intersecting one ballot
+//      per digit bit -- get consecutive ranks in lane order; a
+//      per-warp running count carries ranks across rounds), warps are combined
+//      per digit, the tile is reordered by digit in shared memory, and each
+//      digit's run is stored to consecutive global addresses.  Rank order =
+//      input order, so each pass is stable.
 // No block waits on another block.
 #include "kernels.h"
 #include "scan.cuh"
@@ -18,54 +21,106 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortRounds = 16;                        // 32-key rounds per warp
-constexpr int kWarpKeys = 32 * kSortRounds;            // 512
-constexpr int kSortTile = kWarpKeys * kSortWarps;      // 4096
 
 struct NoPay {};
 
-template <class K, int RB>
+// keys per thread (4096-key tiles)
+template <class K, class P>
+struct SortCfg {
+  static constexpr int kPayBytes = std::is_same<P, NoPay>::value ? 0 : (int)sizeof(P);
+  static constexpr int kItems = 16;
+  static constexpr int kTile = kSortThreads * kItems;
+  static constexpr int kSmem = kTile * ((int)sizeof(K) + kPayBytes);
+};
+
+template <class K, class P, int RB>
 __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const K* __restrict__ keys, u64 n, int shift,
                                                                 u32* __restrict__ hist, u64 ntiles) {
   constexpr int D = 1 << RB;
-  __shared__ u32 h[D];
-  for (int d = threadIdx.x; d < D; d += kSortThreads) h[d] = 0;
+  constexpr int IT = SortCfg<K, P>::kItems;
+  __shared__ u32 h[kSortWarps][D];
+  for (int i = threadIdx.x; i < kSortWarps * D; i += kSortThreads) (&h[0][0])[i] = 0;
   __syncthreads();
-  const u64 base = (u64)blockIdx.x * kSortTile;
-#pragma unroll 4
-  for (int i = threadIdx.x; i < kSortTile; i += kSortThreads) {
-    u64 idx = base + i;
-    if (idx < n) atomicAdd(&h[(u32)((keys[idx] >> shift) & (K)(D - 1))], 1u);
+  const int warp = threadIdx.x >> 5;
+  const u64 tbase = (u64)blockIdx.x * SortCfg<K, P>::kTile;
+  K k[IT];
+#pragma unroll
+  for (int r = 0; r < IT; r++) {  // issue every load before the first use
+    const u64 idx = tbase + (u64)r * kSortThreads + threadIdx.x;
+    k[r] = idx < n ? keys[idx] : K(0);
+  }
+#pragma unroll
+  for (int r = 0; r < IT; r++) {
+    const u64 idx = tbase + (u64)r * kSortThreads + threadIdx.x;
+    if (idx < n) atomicAdd(&h[warp][(u32)((k[r] >> shift) & (K)(D - 1))], 1u);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < D; d += kSortThreads) hist[(u64)d * ntiles + blockIdx.x] = h[d];
+  for (int d = threadIdx.x; d < D; d += kSortThreads) {
+    u32 t = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) t += h[w][d];
+    hist[(u64)d * ntiles + blockIdx.x] = t;
+  }
 }
 
+// Lanes of this warp holding the same RB-bit digit (and a valid key): the
+// intersection over the digit's bits of the ballot of lanes agreeing on that bit.
+template <int RB>
+LOB_DEV u32 same_digit_lanes(u32 d, bool valid) {
+  u32 m = __ballot_sync(0xFFFFFFFFu, valid);
+#pragma unroll
+  for (int b = 0; b < RB; b++) {
+    const bool bit = (d >> b) & 1u;
+    const u32 v = __ballot_sync(0xFFFFFFFFu, bit);
+    m &= bit ? v : ~v;
+  }
+  return m;
+}
+
+// One LSD pass.  Warp w ranks its 32*IT keys (in input order) per digit with a
+// ballot multisplit; the tile's keys are then placed in shared memory in
+// (digit, input order) order and written out run by run, so each digit's run
+// of the tile goes to consecutive global addresses (coalesced stores).
 template <class K, class P, int RB>
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restrict__ keys, const P* __restrict__ pay,
-                                                                K* __restrict__ okeys, P* __restrict__ opay, u64 n,
-                                                                int shift, const u32* __restrict__ offs, u64 ntiles) {
+__global__ void __launch_bounds__(kSortThreads, 2) k_radix_scatter(const K* __restrict__ keys, const P* __restrict__ pay,
+                                                                   K* __restrict__ okeys, P* __restrict__ opay, u64 n,
+                                                                   int shift, const u32* __restrict__ offs, u64 ntiles) {
   constexpr int D = 1 << RB;
+  constexpr int IT = SortCfg<K, P>::kItems;
+  constexpr int TILE = SortCfg<K, P>::kTile;
   constexpr bool kPay = !std::is_same<P, NoPay>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  K* sk = reinterpret_cast<K*>(smem_raw);
+  P* sp = reinterpret_cast<P*>(sk + TILE);
   __shared__ u32 wh[kSortWarps][D];
+  __shared__ u32 dstart[D];
+  __shared__ u32 gbase[D];
+  __shared__ u32 sm[kSortThreads / 32 + 1];
   for (int i = threadIdx.x; i < kSortWarps * D; i += kSortThreads) (&wh[0][0])[i] = 0;
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const u32 lt_mask = (1u << lane) - 1u;
-  const u64 wbase = (u64)blockIdx.x * kSortTile + (u64)warp * kWarpKeys;
-  K k[kSortRounds];
-  P p[kSortRounds];
-  u32 rank[kSortRounds];
+  const u64 tbase = (u64)blockIdx.x * TILE;
+  const int tile_n = (int)min((u64)TILE, n - tbase);
+  const int wofs = warp * 32 * IT;  // this warp's first key within the tile
+  const K* kin = keys + tbase + wofs;
+  K k[IT];
+  P p[IT];
+  u32 rank[IT];
 #pragma unroll
-  for (int r = 0; r < kSortRounds; r++) {
-    const u64 idx = wbase + (u64)r * 32 + lane;
-    const bool valid = idx < n;
-    k[r] = valid ? keys[idx] : K(0);
+  for (int r = 0; r < IT; r++) {  // issue every load before the ranking starts
+    const int o = r * 32 + lane;
+    const bool valid = wofs + o < tile_n;
+    k[r] = valid ? kin[o] : K(0);
     if constexpr (kPay) {
-      if (valid) p[r] = pay[idx];
+      if (valid) p[r] = pay[tbase + wofs + o];
     }
-    const u32 d = valid ? (u32)((k[r] >> shift) & (K)(D - 1)) : (u32)D;
-    const u32 peers = __match_any_sync(0xFFFFFFFFu, d);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < IT; r++) {
+    const bool valid = wofs + r * 32 + lane < tile_n;
+    const u32 d = valid ? (u32)((k[r] >> shift) & (K)(D - 1)) : 0u;
+    const u32 peers = same_digit_lanes<RB>(d, valid);
     u32 base = 0;
     if (valid) base = wh[warp][d];
     rank[r] = base + __popc(peers & lt_mask);
@@ -74,34 +129,59 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restr
     __syncwarp();
   }
   __syncthreads();
-  // per digit: exclusive prefix over warps (tile-local offset of each warp's run)
+  // per digit: exclusive offsets of the warps, tile total
   for (int d = threadIdx.x; d < D; d += kSortThreads) {
     u32 s = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; w++) {
-      u32 c = wh[w][d];
+      const u32 c = wh[w][d];
       wh[w][d] = s;
       s += c;
+    }
+    dstart[d] = s;
+  }
+  __syncthreads();
+  {
+    const u32 t = threadIdx.x < D ? dstart[threadIdx.x] : 0u;
+    u32 tot;
+    const u32 ex = block_exclusive_sum<u32>(t, sm, &tot);
+    if (threadIdx.x < D) {
+      dstart[threadIdx.x] = ex;
+      gbase[threadIdx.x] = offs[(u64)threadIdx.x * ntiles + blockIdx.x];
     }
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kSortRounds; r++) {
-    const u64 idx = wbase + (u64)r * 32 + lane;
-    if (idx < n) {
+  for (int r = 0; r < IT; r++) {
+    if (wofs + r * 32 + lane < tile_n) {
       const u32 d = (u32)((k[r] >> shift) & (K)(D - 1));
-      const u64 pos = (u64)offs[(u64)d * ntiles + blockIdx.x] + wh[warp][d] + rank[r];
-      okeys[pos] = k[r];
-      if constexpr (kPay) opay[pos] = p[r];
+      const u32 lp = dstart[d] + wh[warp][d] + rank[r];
+      sk[lp] = k[r];
+      if constexpr (kPay) sp[lp] = p[r];
     }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < tile_n; i += kSortThreads) {
+    const K key = sk[i];
+    const u32 d = (u32)((key >> shift) & (K)(D - 1));
+    const u64 pos = (u64)gbase[d] + (u32)(i - dstart[d]);
+    okeys[pos] = key;
+    if constexpr (kPay) opay[pos] = sp[i];
   }
 }
 
 template <class K, class P, int RB>
 void sort_impl(void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits, void* scratch, cudaStream_t st) {
   constexpr int D = 1 << RB;
+  constexpr int TILE = SortCfg<K, P>::kTile;
+  constexpr int SMEM = SortCfg<K, P>::kSmem;
   if (n <= 1 || bits <= 0) return;
-  const u64 ntiles = (n + kSortTile - 1) / kSortTile;
+  const u64 ntiles = (n + TILE - 1) / TILE;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_radix_scatter<K, P, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    attr_set = true;
+  }
   u32* hist = reinterpret_cast<u32*>(scratch);
   u32* scan_ws = hist + (u64)D * ntiles + 1;
   K* src_k = reinterpret_cast<K*>(*keys);
@@ -112,7 +192,7 @@ void sort_impl(void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits,
   for (int shift = 0; shift < bits; shift += RB) {
     {
       ProfScope ps("radix_upsweep", n * kb + (double)D * ntiles * 4, st);
-      k_radix_upsweep<K, RB><<<(unsigned)ntiles, kSortThreads, 0, st>>>(src_k, n, shift, hist, ntiles);
+      k_radix_upsweep<K, P, RB><<<(unsigned)ntiles, kSortThreads, 0, st>>>(src_k, n, shift, hist, ntiles);
     }
     {
       ProfScope ps("radix_digit_scan", (double)D * ntiles * 8, st);
@@ -120,7 +200,8 @@ void sort_impl(void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits,
     }
     {
       ProfScope ps("radix_scatter", 2.0 * n * (kb + pb) + (double)D * ntiles * 4, st);
-      k_radix_scatter<K, P, RB><<<(unsigned)ntiles, kSortThreads, 0, st>>>(src_k, src_p, dst_k, dst_p, n, shift, hist, ntiles);
+      k_radix_scatter<K, P, RB><<<(unsigned)ntiles, kSortThreads, SMEM, st>>>(src_k, src_p, dst_k, dst_p, n, shift, hist,
+                                                                               ntiles);
     }
     std::swap(src_k, dst_k);
     std::swap(src_p, dst_p);
@@ -142,9 +223,11 @@ void sort_rb(int rb, void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int
 
 int sort_supported_radix_bits(int rb) { return (rb == 4 || rb == 6 || rb == 8) ? rb : 8; }
 
+constexpr int kMinSortTile = kSortThreads * 16;
+
 size_t sort_scratch_bytes(u64 n, int rb) {
   rb = sort_supported_radix_bits(rb);
-  const u64 ntiles = (n + kSortTile - 1) / kSortTile;
+  const u64 ntiles = (n + kMinSortTile - 1) / kMinSortTile;
   const u64 h = ((u64)1 << rb) * ntiles;
   return (h + 1 + scan_scratch_elems(h) + 64) * sizeof(u32);
 }
@@ -166,7 +249,7 @@ void sort_pairs(int key64, int pay_bytes, void** keys, void** pay, void* ktmp, v
 int sort_kernel_launches(u64 n, int bits, int rb) {
   if (n <= 1 || bits <= 0) return 0;
   rb = sort_supported_radix_bits(rb);
-  const u64 ntiles = (n + kSortTile - 1) / kSortTile;
+  const u64 ntiles = (n + kMinSortTile - 1) / kMinSortTile;
   const u64 h = ((u64)1 << rb) * ntiles;
   int scan = 0;
   for (u64 m = h;; m = (m + kScanTile - 1) / kScanTile) {

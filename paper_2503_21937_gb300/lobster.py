@@ -30,7 +30,8 @@ MEM_HOST, MEM_DEVICE = 0, 1
 EXPORTS = ["lob_create", "lob_destroy", "lob_last_error", "lob_declare_relation", "lob_relation_id",
            "lob_load_relation", "lob_add_rule", "lob_run_to_fixpoint", "lob_relation_size", "lob_read_relation",
            "lob_backward", "lob_reset", "lob_set_option", "lob_profile_count", "lob_profile_entry",
-           "lob_profile_reset", "lob_unique_rows_noalloc"]
+           "lob_profile_reset", "lob_prim_sort", "lob_prim_exclusive_scan", "lob_prim_unique",
+           "lob_prim_diff_merge", "lob_unique_rows_noalloc"]
 NOALLOC_MAX_ROWS = 262144
 
 _lib = None
@@ -80,6 +81,11 @@ def load_library(path: str = LIB_PATH):
                                       P(ctypes.c_double)]
     lib.lob_profile_reset.argtypes = [vp]
     lib.lob_unique_rows_noalloc.argtypes = [vp, u32, u64, vp, vp, vp]
+    lib.lob_prim_sort.argtypes = [vp, vp, vp, u64, u32, u32, u32]
+    lib.lob_prim_exclusive_scan.argtypes = [vp, vp, vp, u64, P(u64)]
+    lib.lob_prim_unique.argtypes = [vp, ctypes.c_int, vp, vp, u64, u32, vp, vp, P(u64)]
+    lib.lob_prim_diff_merge.argtypes = [vp, ctypes.c_int, vp, vp, u64, vp, vp, u64, u32, vp, vp, vp, vp, P(u64),
+                                        P(u64)]
     _lib = lib
     return lib
 
@@ -277,6 +283,36 @@ class Engine:
 
     def reset(self):
         self._chk(self.lib.lob_reset(self.h))
+
+    # kernel-level primitives on CUDA tensors (used by the kernel tests)
+    def prim_sort(self, keys, payload=None, key_bits=None):
+        kb = keys.element_size()
+        pb = payload.element_size() if payload is not None else 0
+        bits = kb * 8 if key_bits is None else key_bits
+        self._chk(self.lib.lob_prim_sort(self.h, keys.data_ptr(), payload.data_ptr() if payload is not None else None,
+                                         keys.numel(), bits, kb, pb))
+
+    def prim_scan(self, x, out):
+        tot = ctypes.c_uint64()
+        self._chk(self.lib.lob_prim_exclusive_scan(self.h, x.data_ptr(), out.data_ptr(), x.numel(), ctypes.byref(tot)))
+        return tot.value
+
+    def prim_unique(self, semiring, keys, tags, out_keys, out_tags):
+        n = ctypes.c_uint64()
+        sr = SEMIRINGS[semiring] if isinstance(semiring, str) else semiring
+        self._chk(self.lib.lob_prim_unique(self.h, sr, keys.data_ptr(), tags.data_ptr() if tags is not None else None,
+                                           keys.numel(), keys.element_size(), out_keys.data_ptr(),
+                                           out_tags.data_ptr() if out_tags is not None else None, ctypes.byref(n)))
+        return n.value
+
+    def prim_diff_merge(self, semiring, fk, ft, uk, ut, ok, ot, rk, rt):
+        no, nr = ctypes.c_uint64(), ctypes.c_uint64()
+        sr = SEMIRINGS[semiring] if isinstance(semiring, str) else semiring
+        p = lambda t: t.data_ptr() if t is not None else None
+        self._chk(self.lib.lob_prim_diff_merge(self.h, sr, p(fk), p(ft), fk.numel(), p(uk), p(ut), uk.numel(),
+                                               fk.element_size(), p(ok), p(ot), p(rk), p(rt), ctypes.byref(no),
+                                               ctypes.byref(nr)))
+        return no.value, nr.value
 
     def profile(self) -> dict:
         """kernel name -> {launches, ms, bytes} accumulated since the last profile_reset."""
