@@ -163,6 +163,8 @@ void lob_engine::release_all() {
   for (DevBuf* b : {&scratch, &cnt, &lo, &off, &part, &counts, &tmp_keys, &tmp_tags, &tmp_keys2, &tmp_tags2}) release(*b);
   for (auto& side : bind)
     for (auto& b : side) release(b);
+  for (auto& side : bfact)
+    for (auto& b : side) release(b);
 }
 
 // ---------------------------------------------------------------------------
@@ -538,6 +540,8 @@ static void rebuild_view(lob_engine& e, RelSt& r, ViewSt& W) {
   for (auto& kv : W.index) kv.second.valid = false;
 }
 
+void engine_ensure_index(lob_engine& e, ViewSt& v, int prefix) { ensure_index(e, v, prefix); }
+
 static void fill_filters(const RuleAst& R, const std::vector<int>& fs, FilterP* out, int& n) {
   n = 0;
   for (int f : fs) {
@@ -794,9 +798,12 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   s.semiring = (u32)sem;
   int rc = LOB_OK;
   u32 k = 0;
+  e.iter_counts.clear();
   for (;;) {
     if (k >= max_iters) { rc = LOB_E_MAXITER; break; }
     k++;
+    e.iter_counts.emplace_back();
+    for (auto& r : e.rels) e.iter_counts.back().emplace_back(r.views[0].n, r.n_recent);
     for (auto& r : e.rels) r.n_cand = 0;
     for (auto& p : e.plans) {
       for (auto& A : p.arms) {

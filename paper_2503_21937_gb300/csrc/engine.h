@@ -162,6 +162,8 @@ struct lob_engine {
   // scratch and transient buffers
   DevBuf scratch, cnt, lo, off, part, counts, tmp_keys, tmp_tags, tmp_keys2, tmp_tags2;
   DevBuf bind[2][kMaxSlots + 2];  // binding tables (cols..., sample, tags) ping-pong
+  DevBuf bfact[2][2 * kMaxArity];  // backward: per carried body fact, its row and tag
+  std::vector<std::vector<std::pair<u64, u64>>> iter_counts;  // per iteration: (|F|, |recent|) per relation
   u64* pinned = nullptr;           // host readback slots
   u64 launches = 0;
 
@@ -177,3 +179,5 @@ struct lob_engine {
   u64 read_u64(const u64* dev);
   void sync();
 };
+
+void engine_ensure_index(lob_engine& e, ViewSt& v, int prefix);

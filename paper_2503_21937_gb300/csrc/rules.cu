@@ -140,6 +140,8 @@ struct RuleParser {
     expect(T_DOT, "'.'");
     if (peek().k != T_END) fail("one rule per call: text after '.'");
     if (r.body.empty()) fail("rule without a body atom");
+    if (r.body.size() > (size_t)kMaxArity) throw LobError(LOB_E_ARG, "rule has more than 8 body atoms");
+    if (r.filters.size() > (size_t)kMaxFilters) throw LobError(LOB_E_ARG, "rule has more than 8 filters");
     // range restriction: every variable must occur in a body atom
     std::vector<char> bound(r.var_names.size(), 0);
     for (auto& a : r.body)
