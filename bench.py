@@ -186,6 +186,72 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------------------
+# batched differentiable reasoning: one launch for 512 samples vs a loop
+# ---------------------------------------------------------------------------
+BATCH_PROGRAM = W.REACH_PROGRAM + W.KIN_PROGRAM
+
+
+def _batched_tensors(B, sel=None):
+    """Device tensors of the batched instance, restricted to sample `sel`
+    (ids kept) when given."""
+    import torch
+
+    def pick(sids):
+        return np.ones(len(sids), bool) if sel is None else sids == sel
+
+    e, st, f, c = B["edge"], B["start"], B["fact"], B["comp"]
+    me, ms, mf, mc = pick(e[3]), pick(st[2]), pick(f[4]), pick(c[4])
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a).astype(np.int32)).cuda()
+    F = lambda a: torch.from_numpy(np.ascontiguousarray(a).astype(np.float32)).cuda()
+    return {"edge": (T(np.stack([e[0][me], e[1][me]])), F(e[2][me]), T(e[3][me])),
+            "start": (T(st[0][ms][None, :]), None, T(st[2][ms])),
+            "fact": (T(np.stack([f[0][mf], f[1][mf], f[2][mf]])), F(f[3][mf]), T(f[4][mf])),
+            "comp": (T(np.stack([c[0][mc], c[1][mc], c[2][mc]])), None, T(c[4][mc]))}
+
+
+def batched_fwd_bwd(n_samples=512, loop_samples=32, reps=3):
+    """Forward + backward (torch.autograd) samples/s of the batched workload in
+    one engine launch, against the same API called once per sample."""
+    import torch
+    from paper_2503_21937_gb300.autograd import fixpoint
+    B = W.batched_instance(n_samples)
+    full = _batched_tensors(B)
+    singles = [_batched_tensors(B, i) for i in range(loop_samples)]
+
+    def fwd_bwd(inp, semiring):
+        ins = {k: (v[0], v[1].clone().requires_grad_(True) if v[1] is not None else None, v[2]) for k, v in inp.items()}
+        out = fixpoint(BATCH_PROGRAM, ins, semiring, outputs=["reach", "kin"])
+        loss = out["reach"][1].sum() + out["kin"][1].sum()
+        loss.backward()
+        return out
+
+    res = {}
+    for semiring in ("diff_add_mult", "diff_max_min"):
+        fwd_bwd(full, semiring)
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fwd_bwd(full, semiring)
+            torch.cuda.synchronize()
+            t.append(time.perf_counter() - t0)
+        batched = n_samples / min(t)
+        fwd_bwd(singles[0], semiring)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in singles:
+            fwd_bwd(s, semiring)
+        torch.cuda.synchronize()
+        loop = loop_samples / (time.perf_counter() - t0)
+        res[semiring] = {"batched_samples_per_s": round(batched, 1), "per_sample_loop_samples_per_s": round(loop, 1),
+                         "speedup": round(batched / loop, 1), "batched_ms": round(1e3 * min(t), 2)}
+    return {"metric": "batched fwd+bwd samples/s vs per-sample (same GB300)", "samples": n_samples,
+            "loop_sample_subset": loop_samples,
+            "workload": "512 samples: grid reachability (side U{8..48}) + 20-relation kinship composition, f32 tags, "
+                        "torch.autograd backward of sum(tags)", "results": res}
+
+
+# ---------------------------------------------------------------------------
 # the engine arm
 # ---------------------------------------------------------------------------
 def main():
@@ -197,6 +263,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=1, help="extra steps with per-kernel CUDA-event timing")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched fwd+bwd measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -327,6 +394,9 @@ def main():
         e2e = {"value": derived[0] / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)}
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_fwd_bwd()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample()
@@ -339,7 +409,7 @@ def main():
                            "l2": "flushed between timed steps (256 MiB write)",
                            "derived_per_step": derived[0], "iterations": iters},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "kernels": kernels}
+                "clocks": clk, "kernels": kernels, "batched": batched}
         print(json.dumps(line))
     for e in engines.values():
         e.close()

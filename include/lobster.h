@@ -153,6 +153,8 @@ int lob_reset(lob_engine* e);
  *   "radix_bits"   bits per radix-sort pass, 4..11                  (default 8)
  *   "sync_check"   1: check CUDA errors after every kernel (debug)   (default 0)
  *   "profile"      1: time every kernel launch with CUDA events      (default 0)
+ *   "max_candidates" candidates sorted at once; larger candidate sets are
+ *                  sorted and deduplicated in chunks (4096..2^31, default 2^30)
  * LOB_E_ARG for an unknown key or a value out of range. */
 int lob_set_option(lob_engine* e, const char* key, int64_t value);
 

@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(256) k_bwd_emit(const __grid_constant__ StepPa
   __shared__ u32 row_of[kEmitTile];
   __shared__ u32 sm[256 / 32 + 1];
   __shared__ u32 th_inc[256];
-  const u64 j0 = (u64)blockIdx.x * kEmitTile;
+  const u64 j0 = P.j_begin + (u64)blockIdx.x * kEmitTile;
+  const u64 j_end = P.j_begin + P.total;
   const u64 r0 = part[blockIdx.x];
   const u64 r_end = part[blockIdx.x + 1];
   for (int i = threadIdx.x; i < kEmitTile; i += 256) row_of[i] = 0;
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(256) k_bwd_emit(const __grid_constant__ StepPa
 #pragma unroll 1
   for (int i = 0; i < kItems; i++) {
     const u64 j = j0 + (u64)i * 256 + threadIdx.x;
-    if (j >= P.total) break;
+    if (j >= j_end) break;
     const u64 r = r0 + row_of[j - j0];
     const u64 v = P.lo[r] + (j - P.off[r]);
     u32 val[kMaxSlots];
@@ -138,10 +139,11 @@ __global__ void __launch_bounds__(256) k_bwd_emit(const __grid_constant__ StepPa
     tags[nf++] = reinterpret_cast<const float*>(P.v_tags)[v];
     tag = Sem::mul(tag, (double)tags[nf - 1]);
     if (!B.last) {
-      write_output<Sem>(P, P.out_base + j, ok, val, sample, tag);
+      const u64 o = j - P.j_begin;
+      write_output<Sem>(P, P.out_base + o, ok, val, sample, tag);
       for (int q = 0; q < nf; q++) {
-        B.out_fact_row[q][j] = rows[q];
-        B.out_fact_tag[q][j] = tags[q];
+        B.out_fact_row[q][o] = rows[q];
+        B.out_fact_tag[q][o] = tags[q];
       }
     } else if (ok) {
       const double a = head_adjoint(B, head_key(P, val, sample));
@@ -355,9 +357,10 @@ void replay_arm(lob_engine& e, BwdState& S, const RulePlan& rp, const ArmPlan& A
     }
     const u64 ntiles = (total + kEmitTile - 1) / kEmitTile;
     e.ensure(e.part, (ntiles + 1) * 8);
-    lbs_partition(e.off.as<u64>(), P.n_in, total, e.part.as<u64>(), e.stream);
+    lbs_partition(e.off.as<u64>(), P.n_in, 0, total, e.part.as<u64>(), e.stream);
     P.off = e.off.as<u64>();
     P.total = total;
+    P.j_begin = 0;
     k_bwd_emit<<<(unsigned)ntiles, 256, 0, e.stream>>>(P, B, e.part.as<u64>());
     e.after_launch("backward emit");
     e.launches += 2;

@@ -115,8 +115,11 @@ struct MergeTile {
   u64 d0, a0, b0, na_t, nb_t;
 };
 
+// Stage one merge-path tile of A and B in shared memory.  A partition that is
+// not monotone (which only unsorted input can produce) sets *err and yields an
+// empty tile instead of an out-of-range read.
 template <class K>
-LOB_DEV MergeTile<K> load_merge_tile(const K* A, u64 na, const K* B, u64 nb, const u64* apart, K* sk) {
+LOB_DEV MergeTile<K> load_merge_tile(const K* A, u64 na, const K* B, u64 nb, const u64* apart, K* sk, u64* err) {
   MergeTile<K> t;
   t.d0 = (u64)blockIdx.x * kMTile;
   const u64 d1 = min(t.d0 + kMTile, na + nb);
@@ -124,6 +127,14 @@ LOB_DEV MergeTile<K> load_merge_tile(const K* A, u64 na, const K* B, u64 nb, con
   const u64 a1 = apart[blockIdx.x + 1];
   t.b0 = t.d0 - t.a0;
   const u64 b1 = d1 - a1;
+  if (a1 < t.a0 || b1 < t.b0 || a1 > na || b1 > nb || (a1 - t.a0) + (b1 - t.b0) > (u64)kMTile) {
+    if (threadIdx.x == 0 && err) atomicExch(err, 1ull);
+    t.a0 = min(t.a0, na);
+    t.b0 = min(t.b0, nb);
+    t.na_t = t.nb_t = 0;
+    __syncthreads();
+    return t;
+  }
   t.na_t = a1 - t.a0;
   t.nb_t = b1 - t.b0;
   K v[kMItems];
@@ -160,6 +171,7 @@ struct MergeCtx {
   K* ok; typename Sem::Stored* ot; u32* os;
   K* rk; typename Sem::Stored* rt;
   u32 stamp;
+  u64* err;
 };
 
 template <class Sem>
@@ -213,7 +225,7 @@ __global__ void __launch_bounds__(kMThreads) k_diffmerge_count(MergeCtx<K, Sem> 
                                                                u64* __restrict__ tile_dup, u64* __restrict__ tile_r) {
   __shared__ K sk[kMTile];
   __shared__ u64 sm[kMThreads / 32 + 1];
-  MergeTile<K> t = load_merge_tile(c.fk, c.nf, c.uk, c.nu, apart, sk);
+  MergeTile<K> t = load_merge_tile(c.fk, c.nf, c.uk, c.nu, apart, sk, c.err);
   u64 ndup = 0, nr = 0;
   walk_items(c, t, sk, [&](bool isA, u64, u64, bool dup, bool improved) {
     if (!isA) {
@@ -233,7 +245,7 @@ __global__ void __launch_bounds__(kMThreads) k_diffmerge_write(MergeCtx<K, Sem> 
                                                                const u64* __restrict__ dup_off, const u64* __restrict__ r_off) {
   __shared__ K sk[kMTile];
   __shared__ u64 sm[kMThreads / 32 + 1];
-  MergeTile<K> t = load_merge_tile(c.fk, c.nf, c.uk, c.nu, apart, sk);
+  MergeTile<K> t = load_merge_tile(c.fk, c.nf, c.uk, c.nu, apart, sk, (u64*)nullptr);
   u64 ndup = 0, nr = 0;
   walk_items(c, t, sk, [&](bool isA, u64, u64, bool dup, bool improved) {
     if (!isA) {
@@ -290,6 +302,107 @@ __global__ void __launch_bounds__(kMThreads) k_diffmerge_write(MergeCtx<K, Sem> 
       }
     }
   });
+}
+
+// ---------------------------------------------------------------------------
+// combine: merge two sorted distinct-key lists, (+)-combining shared keys
+// (accumulates the unique candidates of several chunks of one iteration)
+// ---------------------------------------------------------------------------
+template <class K, class F>
+LOB_DEV void walk_merge(const K* A, const MergeTile<K>& t, const K* sk, F&& f) {
+  const K* sA = sk;
+  const K* sB = sk + t.na_t;
+  const u64 nt = t.na_t + t.nb_t;
+  const u64 diag = min((u64)threadIdx.x * kMItems, nt);
+  u64 ai = local_path(sA, t.na_t, sB, t.nb_t, diag);
+  u64 bi = diag - ai;
+  bool have_last = false;
+  K last = K(0);
+  if (ai > 0) { have_last = true; last = sA[ai - 1]; }
+  else if (t.a0 > 0) { have_last = true; last = A[t.a0 - 1]; }
+  for (int s = 0; s < kMItems && ai + bi < nt; s++) {
+    if (ai < t.na_t && (bi >= t.nb_t || sA[ai] <= sB[bi])) {
+      last = sA[ai];
+      have_last = true;
+      f(true, ai, bi, false);
+      ai++;
+    } else {
+      f(false, ai, bi, have_last && last == sB[bi]);
+      bi++;
+    }
+  }
+}
+
+template <class K>
+__global__ void __launch_bounds__(kMThreads) k_combine_count(const K* __restrict__ A, u64 na, const K* __restrict__ B, u64 nb,
+                                                             const u64* __restrict__ apart, u64* __restrict__ tile_dup,
+                                                             u64* err) {
+  __shared__ K sk[kMTile];
+  __shared__ u64 sm[kMThreads / 32 + 1];
+  MergeTile<K> t = load_merge_tile(A, na, B, nb, apart, sk, err);
+  u64 ndup = 0;
+  walk_merge(A, t, sk, [&](bool isA, u64, u64, bool dup) { ndup += (!isA) && dup; });
+  u64 tot;
+  block_exclusive_sum<u64>(ndup, sm, &tot);
+  if (threadIdx.x == 0) tile_dup[blockIdx.x] = tot;
+}
+
+template <class K, class Sem>
+__global__ void __launch_bounds__(kMThreads) k_combine_write(const K* __restrict__ A, const typename Sem::Cand* __restrict__ at,
+                                                             u64 na, const K* __restrict__ B,
+                                                             const typename Sem::Cand* __restrict__ bt, u64 nb,
+                                                             const u64* __restrict__ apart, const u64* __restrict__ dup_off,
+                                                             K* __restrict__ ok, typename Sem::Cand* __restrict__ ot) {
+  __shared__ K sk[kMTile];
+  __shared__ u64 sm[kMThreads / 32 + 1];
+  MergeTile<K> t = load_merge_tile(A, na, B, nb, apart, sk, (u64*)nullptr);
+  u64 ndup = 0;
+  walk_merge(A, t, sk, [&](bool isA, u64, u64, bool dup) { ndup += (!isA) && dup; });
+  u64 tot;
+  u64 dups_before = dup_off[blockIdx.x] + block_exclusive_sum<u64>(ndup, sm, &tot);
+  const K* sA = sk;
+  const K* sB = sk + t.na_t;
+  walk_merge(A, t, sk, [&](bool isA, u64 ai, u64 bi, bool dup) {
+    const u64 d = t.d0 + ai + bi;
+    if (isA) {
+      const u64 pos = d - dups_before;
+      const K k = sA[ai];
+      ok[pos] = k;
+      if constexpr (Sem::kTags) {
+        typename Sem::Cand tag = at[t.a0 + ai];
+        const u64 gb = t.b0 + bi;
+        const bool next_eq = bi < t.nb_t ? (sB[bi] == k) : (gb < nb && B[gb] == k);
+        if (next_eq) tag = Sem::add(tag, bt[gb]);
+        ot[pos] = tag;
+      }
+    } else if (dup) {
+      dups_before++;
+    } else {
+      const u64 pos = d - dups_before;
+      ok[pos] = sB[bi];
+      if constexpr (Sem::kTags) ot[pos] = bt[t.b0 + bi];
+    }
+  });
+}
+
+template <class K, class Sem>
+void combine_impl(const void* a, const void* at, u64 na, const void* b, const void* bt, u64 nb, void* o, void* ot,
+                  u64* count_dev, void* scratch, cudaStream_t st) {
+  typedef typename Sem::Cand C;
+  const u64 tiles = (na + nb + kMTile - 1) / kMTile;
+  u64* apart = reinterpret_cast<u64*>(scratch);
+  u64* tdup = apart + tiles + 1;
+  u64* ws = tdup + tiles + 1;
+  cudaMemsetAsync(count_dev + 1, 0, sizeof(u64), st);
+  const double kb = sizeof(K), cb = Sem::kTags ? sizeof(C) : 0;
+  { ProfScope ps("merge_path", (tiles + 1) * 8.0, st);
+    k_merge_path<K><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, st>>>((const K*)a, na, (const K*)b, nb, tiles + 1, apart); }
+  { ProfScope ps("combine_count", (na + nb) * kb, st);
+    k_combine_count<K><<<(unsigned)tiles, kMThreads, 0, st>>>((const K*)a, na, (const K*)b, nb, apart, tdup, count_dev + 1); }
+  exclusive_scan<u64, u64>(tdup, tdup, tiles, count_dev, ws, st);
+  { ProfScope ps("combine_write", 2.0 * (na + nb) * (kb + cb), st);
+    k_combine_write<K, Sem><<<(unsigned)tiles, kMThreads, 0, st>>>((const K*)a, (const C*)at, na, (const K*)b, (const C*)bt,
+                                                                   nb, apart, tdup, (K*)o, (C*)ot); }
 }
 
 // ---------------------------------------------------------------------------
@@ -447,6 +560,25 @@ void diff_merge(const MergeArgs& a, void* scratch, cudaStream_t st) {
   }
   if (a.key64) { LOB_MERGE(u64) } else { LOB_MERGE(u32) }
 #undef LOB_MERGE
+}
+
+size_t combine_scratch_bytes(u64 na, u64 nb) {
+  const u64 tiles = (na + nb + kMTile - 1) / kMTile;
+  return (2 * (tiles + 1) + scan_scratch_elems(tiles) + 8) * sizeof(u64);
+}
+
+// count_dev[0] = number of distinct keys written (na + nb - shared keys)
+void combine_merge(int sem, int key64, const void* akeys, const void* atags, u64 na, const void* bkeys,
+                   const void* btags, u64 nb, void* okeys, void* otags, u64* count_dev, void* scratch, cudaStream_t st) {
+#define LOB_COMB(K)                                                                                                   \
+  switch (sem) {                                                                                                      \
+    case SR_UNIT: combine_impl<K, SemUnit>(akeys, atags, na, bkeys, btags, nb, okeys, otags, count_dev, scratch, st); break; \
+    case SR_MAX_MIN: combine_impl<K, SemMaxMin>(akeys, atags, na, bkeys, btags, nb, okeys, otags, count_dev, scratch, st); break; \
+    case SR_DIFF_MAX_MIN: combine_impl<K, SemDiffMaxMin>(akeys, atags, na, bkeys, btags, nb, okeys, otags, count_dev, scratch, st); break; \
+    default: combine_impl<K, SemAddMult>(akeys, atags, na, bkeys, btags, nb, okeys, otags, count_dev, scratch, st); break; \
+  }
+  if (key64) { LOB_COMB(u64) } else { LOB_COMB(u32) }
+#undef LOB_COMB
 }
 
 void load_unique(const LoadUniqueArgs& a, void* scratch, cudaStream_t st) {

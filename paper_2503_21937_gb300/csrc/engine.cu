@@ -146,9 +146,10 @@ static void release_derived(lob_engine& e) {
     for (auto& v : r.views) release_view(e, v);
     r.views.clear();
     for (DevBuf* b : {&r.rkeys, &r.rtags, &r.nkeys, &r.ntags, &r.ckeys, &r.ctags, &r.ckeys2, &r.ctags2, &r.row_factor,
-                      &r.row_keys})
+                      &r.row_keys, &r.akeys, &r.atags, &r.akeys2, &r.atags2})
       e.release(*b);
-    r.n_recent = r.n_next = r.n_cand = 0;
+    r.n_recent = r.n_next = r.n_cand = r.n_acc = 0;
+    r.flushed = false;
   }
   e.plans.clear();
 }
@@ -242,13 +243,21 @@ static ArmPlan plan_arm(lob_engine& e, const RuleAst& R, int delta, bool idempot
     A.steps.push_back(s);
     bound_after.push_back(bound);
   }
+  // Greedy join order: next the atom with the most bound columns; on a tie an
+  // input relation (fixed size, static index) before a derived one, then the
+  // smaller input relation, then body order.
   for (size_t n_used = 1; n_used < R.body.size(); n_used++) {
-    int best = -1, best_b = -1;
+    int best = -1, best_b = -1, best_edb = -1;
+    u64 best_n = 0;
     for (size_t i = 0; i < R.body.size(); i++) {
       if (used[i]) continue;
       int b = 0;
       for (auto& t : R.body[i].args) b += (!t.var || bound[t.v]);
-      if (b > best_b) { best_b = b; best = (int)i; }
+      const RelSt& cand = e.rels[R.body[i].rel];
+      const int edb = cand.idb ? 0 : 1;
+      const u64 n = cand.n_in;
+      const bool better = b > best_b || (b == best_b && (edb > best_edb || (edb == best_edb && edb && n < best_n)));
+      if (better) { best_b = b; best = (int)i; best_edb = edb; best_n = n; }
     }
     const AtomAst& a = R.body[best];
     RelSt& rel = e.rels[a.rel];
@@ -576,6 +585,58 @@ static void ensure_cand(lob_engine& e, RelSt& H, u64 extra) {
   if (cb) e.ensure(H.ctags, (H.n_cand + extra) * cb, true);
 }
 
+// Sort + unique the candidates gathered so far and (+)-combine them into the
+// iteration's accumulator, so that no sort ever sees more than opt_max_cand keys.
+static void flush_candidates(lob_engine& e, RelSt& H) {
+  const u64 n = H.n_cand;
+  H.flushed = true;
+  if (!n) return;
+  const int ks = sem_kernel(e.semiring);
+  const Layout& L = H.views[0].lay;
+  const int kb = L.key64 ? 8 : 4, cb = cand_bytes(e.semiring);
+  if (n > e.opt_max_cand || n >= (1ull << 32)) throw LobError(LOB_E_CUDA, "internal error: candidate chunk too large");
+  e.ensure(H.ckeys2, n * kb);
+  if (cb) e.ensure(H.ctags2, n * cb);
+  void* keys = H.ckeys.p;
+  void* tags = H.ctags.p;
+  scratch_at_least(e, sort_scratch_bytes(n, e.opt_radix_bits));
+  sort_pairs(L.key64, cb, &keys, &tags, H.ckeys2.p, H.ctags2.p, n, L.bits, e.opt_radix_bits, e.scratch.p, e.stream);
+  e.after_launch("chunk sort");
+  e.launches += sort_kernel_launches(n, L.bits, e.opt_radix_bits);
+  void* ukeys = keys == H.ckeys.p ? H.ckeys2.p : H.ckeys.p;
+  void* utags = tags == H.ctags.p ? H.ctags2.p : H.ctags.p;
+  scratch_at_least(e, unique_scratch_bytes(n));
+  unique_run(ks, L.key64, keys, tags, n, ukeys, utags, e.counts.as<u64>() + 1, e.scratch.p, e.stream);
+  e.after_launch("chunk unique");
+  e.launches += 2 + scan_launches((n + 4095) / 4096);
+  const u64 nu = e.read_u64(e.counts.as<u64>() + 1);
+  H.n_cand = 0;
+  if (!nu) return;
+  if (!H.n_acc) {
+    e.ensure(H.akeys, nu * kb);
+    e.check(cudaMemcpyAsync(H.akeys.p, ukeys, nu * kb, cudaMemcpyDeviceToDevice, e.stream), "accumulate");
+    if (cb) {
+      e.ensure(H.atags, nu * cb);
+      e.check(cudaMemcpyAsync(H.atags.p, utags, nu * cb, cudaMemcpyDeviceToDevice, e.stream), "accumulate");
+    }
+    H.n_acc = nu;
+    return;
+  }
+  e.ensure(H.akeys2, (H.n_acc + nu) * kb);
+  if (cb) e.ensure(H.atags2, (H.n_acc + nu) * cb);
+  scratch_at_least(e, combine_scratch_bytes(H.n_acc, nu));
+  combine_merge(ks, L.key64, H.akeys.p, H.atags.p, H.n_acc, ukeys, utags, nu, H.akeys2.p, H.atags2.p,
+                e.counts.as<u64>() + 6, e.scratch.p, e.stream);
+  e.after_launch("accumulate");
+  e.launches += 3 + scan_launches((H.n_acc + nu + 2047) / 2048);
+  e.check(cudaMemcpyAsync(e.pinned, e.counts.as<u64>() + 6, 16, cudaMemcpyDeviceToHost, e.stream), "counts");
+  e.sync();
+  if (e.pinned[1]) throw LobError(LOB_E_CUDA, "internal error: unsorted input to the candidate accumulator");
+  H.n_acc = H.n_acc + nu - e.pinned[0];  // keys present in both lists collapse to one
+  std::swap(H.akeys, H.akeys2);
+  std::swap(H.atags, H.atags2);
+}
+
 // Run one semi-naive arm of a rule for iteration k.  Δ-atom rows are the
 // recent facts of the delta relation (or, with `src_stamp`, the rows of its
 // primary view carrying that stamp).
@@ -595,13 +656,23 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
   P.in_tags = D.rtags.p;
   P.n_in = D.n_recent;
   fill_filters(R, A.steps[0].filters, P.in_filters, P.n_in_filters);
-  if (A.steps.size() == 1) {
-    ensure_cand(e, H, P.n_in);
-    set_head_output(e, R, P, H);
-    project_rows(sem, P, e.stream);
-    e.after_launch("project");
-    e.launches++;
-    H.n_cand += P.n_in;
+  if (A.steps.size() == 1) {  // one output row per delta row, in chunks of at most opt_max_cand
+    const u64 n = P.n_in;
+    const int kb = P.in_lay.key64 ? 8 : 4, sb = stored_bytes(e.semiring);
+    for (u64 rb = 0; rb < n; rb += e.opt_max_cand) {
+      const u64 sub = std::min(e.opt_max_cand, n - rb);
+      if (H.n_cand + sub > e.opt_max_cand) flush_candidates(e, H);
+      ensure_cand(e, H, sub);
+      set_head_output(e, R, P, H);
+      P.in_keys = static_cast<const char*>(D.rkeys.p) + rb * kb;
+      P.in_tags = sb ? static_cast<const char*>(D.rtags.p) + rb * sb : nullptr;
+      P.n_in = sub;
+      project_rows(sem, P, e.stream);
+      e.after_launch("project");
+      e.launches++;
+      H.n_cand += sub;
+      e.cand_emitted += sub;
+    }
     return;
   }
   int side = 0;
@@ -649,9 +720,25 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
     if (!total) return;
     // outputs
     const int out_side = side ^ 1;
-    if (last) {
-      ensure_cand(e, H, total);
-      set_head_output(e, R, P, H);
+    if (last) {  // candidates, emitted in sub-ranges of at most opt_max_cand outputs
+      P.off = e.off.as<u64>();
+      for (u64 jb = 0; jb < total; jb += e.opt_max_cand) {
+        const u64 sub = std::min(e.opt_max_cand, total - jb);
+        if (H.n_cand + sub > e.opt_max_cand) flush_candidates(e, H);
+        ensure_cand(e, H, sub);
+        set_head_output(e, R, P, H);
+        const u64 nt = (sub + kEmitTile - 1) / kEmitTile;
+        e.ensure(e.part, (nt + 1) * 8);
+        lbs_partition(e.off.as<u64>(), P.n_in, jb, sub, e.part.as<u64>(), e.stream);
+        P.total = sub;
+        P.j_begin = jb;
+        join_emit(sem, P, e.part.as<u64>(), e.stream);
+        e.after_launch("join emit");
+        e.launches += 2;
+        H.n_cand += sub;
+        e.cand_emitted += sub;
+      }
+      return;
     } else {
       P.out_packed = 0;
       P.n_out_cols = (int)S.live.size();
@@ -668,16 +755,13 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
     }
     const u64 ntiles = (total + kEmitTile - 1) / kEmitTile;
     e.ensure(e.part, (ntiles + 1) * 8);
-    lbs_partition(e.off.as<u64>(), P.n_in, total, e.part.as<u64>(), e.stream);
+    lbs_partition(e.off.as<u64>(), P.n_in, 0, total, e.part.as<u64>(), e.stream);
     P.off = e.off.as<u64>();
     P.total = total;
+    P.j_begin = 0;
     join_emit(sem, P, e.part.as<u64>(), e.stream);
     e.after_launch("join emit");
     e.launches += 2;
-    if (last) {
-      H.n_cand += total;
-      return;
-    }
     // the binding table becomes the next step's input
     side = out_side;
     P.in_packed = 0;
@@ -697,28 +781,41 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
 static void dedup_relation(lob_engine& e, RelSt& H, u32 k) {
   H.n_next = 0;
   const u64 n = H.n_cand;
-  if (!n) return;
+  if (!n && !H.flushed) return;
   const int sem = e.semiring;
   const int ks = sem_kernel(sem);
   ViewSt& V = H.views[0];
   const Layout& L = V.lay;
   const int kb = L.key64 ? 8 : 4, cb = cand_bytes(sem), sb = stored_bytes(sem);
   const bool stamps = sem_stamps(sem);
-  e.ensure(H.ckeys2, n * kb);
-  if (cb) e.ensure(H.ctags2, n * cb);
-  void* keys = H.ckeys.p;
-  void* tags = H.ctags.p;
-  scratch_at_least(e, sort_scratch_bytes(n, e.opt_radix_bits));
-  sort_pairs(L.key64, cb, &keys, &tags, H.ckeys2.p, H.ctags2.p, n, L.bits, e.opt_radix_bits, e.scratch.p, e.stream);
-  e.after_launch("candidate sort");
-  e.launches += sort_kernel_launches(n, L.bits, e.opt_radix_bits);
-  void* ukeys = keys == H.ckeys.p ? H.ckeys2.p : H.ckeys.p;
-  void* utags = tags == H.ctags.p ? H.ctags2.p : H.ctags.p;
-  scratch_at_least(e, unique_scratch_bytes(n));
-  unique_run(ks, L.key64, keys, tags, n, ukeys, utags, e.counts.as<u64>() + 1, e.scratch.p, e.stream);
-  e.after_launch("unique");
-  e.launches += 2 + scan_launches((n + 4095) / 4096);
-  const u64 nu = e.read_u64(e.counts.as<u64>() + 1);
+  void* ukeys;
+  void* utags;
+  u64 nu;
+  if (H.flushed) {  // earlier chunks of this iteration were accumulated: add the rest
+    flush_candidates(e, H);
+    ukeys = H.akeys.p;
+    utags = H.atags.p;
+    nu = H.n_acc;
+    H.n_acc = 0;
+    H.flushed = false;
+  } else {
+    if (n > e.opt_max_cand || n >= (1ull << 32)) throw LobError(LOB_E_CUDA, "internal error: candidate set too large");
+    e.ensure(H.ckeys2, n * kb);
+    if (cb) e.ensure(H.ctags2, n * cb);
+    void* keys = H.ckeys.p;
+    void* tags = H.ctags.p;
+    scratch_at_least(e, sort_scratch_bytes(n, e.opt_radix_bits));
+    sort_pairs(L.key64, cb, &keys, &tags, H.ckeys2.p, H.ctags2.p, n, L.bits, e.opt_radix_bits, e.scratch.p, e.stream);
+    e.after_launch("candidate sort");
+    e.launches += sort_kernel_launches(n, L.bits, e.opt_radix_bits);
+    ukeys = keys == H.ckeys.p ? H.ckeys2.p : H.ckeys.p;
+    utags = tags == H.ctags.p ? H.ctags2.p : H.ctags.p;
+    scratch_at_least(e, unique_scratch_bytes(n));
+    unique_run(ks, L.key64, keys, tags, n, ukeys, utags, e.counts.as<u64>() + 1, e.scratch.p, e.stream);
+    e.after_launch("unique");
+    e.launches += 2 + scan_launches((n + 4095) / 4096);
+    nu = e.read_u64(e.counts.as<u64>() + 1);
+  }
   if (!nu) return;
   // difference against F fused with the merge into F
   e.ensure(V.keys2, (V.n + nu) * kb);
@@ -740,8 +837,9 @@ static void dedup_relation(lob_engine& e, RelSt& H, u32 k) {
   e.after_launch("difference+merge");
   const u64 mt = (V.n + nu + 2047) / 2048;
   e.launches += 3 + 2 * scan_launches(mt);
-  e.check(cudaMemcpyAsync(e.pinned, e.counts.as<u64>() + 2, 16, cudaMemcpyDeviceToHost, e.stream), "counts");
+  e.check(cudaMemcpyAsync(e.pinned, e.counts.as<u64>() + 2, 24, cudaMemcpyDeviceToHost, e.stream), "counts");
   e.sync();
+  if (e.pinned[2]) throw LobError(LOB_E_CUDA, "internal error: unsorted input to the difference/merge");
   const u64 dups = e.pinned[0], nr = e.pinned[1];
   V.n = V.n + nu - dups;
   std::swap(V.keys, V.keys2);
@@ -769,12 +867,15 @@ static void dedup_relation(lob_engine& e, RelSt& H, u32 k) {
     M2.okeys = W.keys2.p; M2.otags = W.tags2.p; M2.ostamp = stamps ? W.stamps2.as<u32>() : nullptr;
     M2.rkeys = nullptr; M2.rtags = nullptr;
     M2.stamp = k;
-    M2.counts_dev = e.counts.as<u64>() + 4;
+    M2.counts_dev = e.counts.as<u64>() + 9;
     scratch_at_least(e, merge_scratch_bytes(W.n, nr));
     diff_merge(M2, e.scratch.p, e.stream);
     e.after_launch("view merge");
     e.launches += 3 + 2 * scan_launches((W.n + nr + 2047) / 2048);
-    const u64 d2 = e.read_u64(e.counts.as<u64>() + 4);
+    e.check(cudaMemcpyAsync(e.pinned, e.counts.as<u64>() + 9, 24, cudaMemcpyDeviceToHost, e.stream), "counts");
+    e.sync();
+    if (e.pinned[2]) throw LobError(LOB_E_CUDA, "internal error: unsorted input to a view merge");
+    const u64 d2 = e.pinned[0];
     W.n = W.n + nr - d2;
     std::swap(W.keys, W.keys2);
     std::swap(W.tags, W.tags2);
@@ -799,6 +900,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   int rc = LOB_OK;
   u32 k = 0;
   e.iter_counts.clear();
+  e.cand_emitted = 0;
   for (;;) {
     if (k >= max_iters) { rc = LOB_E_MAXITER; break; }
     k++;
@@ -819,7 +921,6 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
     }
     u64 total_new = 0;
     for (auto& r : e.rels) {
-      s.candidates += r.n_cand;
       dedup_relation(e, r, k);
       total_new += r.n_next;
     }
@@ -841,6 +942,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   cudaEventDestroy(ev1);
   s.iterations = k;
   s.ms = ms;
+  s.candidates = e.cand_emitted;
   for (auto& r : e.rels)
     if (r.idb) s.derived += r.views[0].n;
   s.peak_bytes = e.peak_bytes;
@@ -1237,8 +1339,9 @@ int lob_prim_diff_merge(lob_engine* e, int semiring, const void* f_keys, const v
     scratch_at_least(*e, merge_scratch_bytes(nf, nu));
     diff_merge(M, e->scratch.p, e->stream);
     e->after_launch("merge");
-    e->check(cudaMemcpyAsync(e->pinned, e->counts.as<u64>() + 2, 16, cudaMemcpyDeviceToHost, e->stream), "counts");
+    e->check(cudaMemcpyAsync(e->pinned, e->counts.as<u64>() + 2, 24, cudaMemcpyDeviceToHost, e->stream), "counts");
     e->sync();
+    if (e->pinned[2]) throw LobError(LOB_E_ARG, "inputs are not sorted distinct keys");
     *n_out = nf + nu - e->pinned[0];
     *n_r = e->pinned[1];
     return LOB_OK;
@@ -1272,6 +1375,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "radix_bits" && value >= 4 && value <= 11) e->opt_radix_bits = sort_supported_radix_bits((int)value);
     else if (k == "sync_check" && (value == 0 || value == 1)) e->opt_sync_check = (int)value;
     else if (k == "profile" && (value == 0 || value == 1)) e->opt_profile = (int)value;
+    else if (k == "max_candidates" && value >= 4096 && value <= (int64_t)1 << 31) e->opt_max_cand = (u64)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

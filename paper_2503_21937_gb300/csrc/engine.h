@@ -83,6 +83,9 @@ struct RelSt {
   u64 n_next = 0;
   DevBuf ckeys, ctags, ckeys2, ctags2;  // candidates + sort ping-pong
   u64 n_cand = 0;
+  DevBuf akeys, atags, akeys2, atags2;  // unique candidates of the flushed chunks of this iteration
+  u64 n_acc = 0;
+  bool flushed = false;
   // gradient routing of loaded rows
   DevBuf row_factor, row_keys;
   u32 id_base = 0;
@@ -114,6 +117,7 @@ struct RulePlan {
 
 struct ProfAgg {
   u64 launches = 0;
+  u64 cand_emitted = 0;  // candidates emitted by the joins of the current run
   double ms = 0, bytes = 0;
 };
 struct EngineProfiler : KernelProfiler {
@@ -151,6 +155,7 @@ struct lob_engine {
   std::vector<RulePlan> plans;
   // options
   int opt_join_index = 0, opt_dense_bits = 24, opt_radix_bits = 8, opt_sync_check = 0, opt_profile = 0;
+  u64 opt_max_cand = 1ull << 30;  // candidates sorted at once (bounds every sort below 2^32 keys)
   EngineProfiler prof;
   // run state
   int state = 0;  // 0 loading, 1 ran
@@ -166,6 +171,7 @@ struct lob_engine {
   std::vector<std::vector<std::pair<u64, u64>>> iter_counts;  // per iteration: (|F|, |recent|) per relation
   u64* pinned = nullptr;           // host readback slots
   u64 launches = 0;
+  u64 cand_emitted = 0;  // candidates emitted by the joins of the current run
 
   // memory
   void* dalloc(size_t bytes);

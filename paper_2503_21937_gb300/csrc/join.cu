@@ -31,14 +31,11 @@ __global__ void __launch_bounds__(256) k_join_count(const __grid_constant__ Step
   }
 }
 
-__global__ void k_lbs_partition(const u64* __restrict__ off, u64 n_in, u64 ntiles, u64* __restrict__ part) {
+__global__ void k_lbs_partition(const u64* __restrict__ off, u64 n_in, u64 j_begin, u64 total, u64 ntiles,
+                                u64* __restrict__ part) {
   const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t > ntiles) return;
-  if (t == ntiles) {
-    part[t] = n_in - 1;
-    return;
-  }
-  const u64 j = t * (u64)kEmitTile;
+  const u64 j = t == ntiles ? j_begin + total - 1 : j_begin + t * (u64)kEmitTile;
   part[t] = upper_bound_dev<u64>(off, 0, n_in, j) - 1;
 }
 
@@ -48,7 +45,8 @@ __global__ void __launch_bounds__(256) k_join_emit(const __grid_constant__ StepP
   constexpr int kItems = kEmitTile / 256;
   __shared__ u32 row_of[kEmitTile];
   __shared__ u32 sm[256 / 32 + 1];
-  const u64 j0 = (u64)blockIdx.x * kEmitTile;
+  const u64 j0 = P.j_begin + (u64)blockIdx.x * kEmitTile;
+  const u64 j_end = P.j_begin + P.total;
   const u64 r0 = part[blockIdx.x];
   const u64 r_end = part[blockIdx.x + 1];
   for (int i = threadIdx.x; i < kEmitTile; i += 256) row_of[i] = 0;
@@ -79,7 +77,7 @@ __global__ void __launch_bounds__(256) k_join_emit(const __grid_constant__ StepP
 #pragma unroll 1
   for (int i = 0; i < kItems; i++) {
     const u64 j = j0 + (u64)i * 256 + threadIdx.x;
-    if (j >= P.total) break;
+    if (j >= j_end) break;
     const u64 r = r0 + row_of[j - j0];
     const u64 v = P.lo[r] + (j - P.off[r]);
     u32 val[kMaxSlots];
@@ -95,7 +93,7 @@ __global__ void __launch_bounds__(256) k_join_emit(const __grid_constant__ StepP
     }
     for (int f = 0; f < P.n_filters && ok; f++) ok = eval_filter(P.filters[f], val);
     if constexpr (Sem::kTags) tag = Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v]));
-    write_output<Sem>(P, P.out_base + j, ok, val, sample, tag);
+    write_output<Sem>(P, P.out_base + (j - P.j_begin), ok, val, sample, tag);
   }
 }
 
@@ -225,10 +223,10 @@ void join_count(int sem, const StepParams& P, cudaStream_t st) {
   if (P.n_in) by_sem<CountL>(sem, P, st);
 }
 
-void lbs_partition(const u64* off, u64 n_in, u64 total, u64* part, cudaStream_t st) {
+void lbs_partition(const u64* off, u64 n_in, u64 j_begin, u64 total, u64* part, cudaStream_t st) {
   const u64 ntiles = (total + kEmitTile - 1) / kEmitTile;
   ProfScope ps("join_partition", (ntiles + 1) * 8.0, st);
-  k_lbs_partition<<<(unsigned)((ntiles + 1 + 255) / 256), 256, 0, st>>>(off, n_in, ntiles, part);
+  k_lbs_partition<<<(unsigned)((ntiles + 1 + 255) / 256), 256, 0, st>>>(off, n_in, j_begin, total, ntiles, part);
 }
 
 void join_emit(int sem, const StepParams& P, const u64* part, cudaStream_t st) {

@@ -54,10 +54,18 @@ struct MergeArgs {
   void* okeys; void* otags; u32* ostamp;                            // F' (room for nf + nu)
   void* rkeys; void* rtags;                                         // R: new or improved facts (nullable)
   u32 stamp;                                                        // stamp of new / improved facts
-  u64* counts_dev;                                                  // [0] = #dups of U in F, [1] = |R|
+  u64* counts_dev;                                                  // [0] = #dups of U in F, [1] = |R|, [2] = error flag
 };
 size_t merge_scratch_bytes(u64 nf, u64 nu);
 void diff_merge(const MergeArgs& a, void* scratch, cudaStream_t st);
+
+// Merge two sorted lists of distinct keys with candidate tags into one,
+// combining the tags of a key present in both with (+).  count_dev[0] = number
+// of keys present in both (result size = na + nb - that), count_dev[1] = error
+// flag (non-zero: the inputs were not sorted; the output is not trustworthy).
+size_t combine_scratch_bytes(u64 na, u64 nb);
+void combine_merge(int sem, int key64, const void* akeys, const void* atags, u64 na, const void* bkeys,
+                   const void* btags, u64 nb, void* okeys, void* otags, u64* count_dev, void* scratch, cudaStream_t st);
 
 struct LoadUniqueArgs {
   int sem, key64;
@@ -113,14 +121,15 @@ struct StepParams {
   u32* out_sample;
   void* out_tags;
   u64 out_base;
-  // count / scan products
-  u32* cnt; u64* lo; const u64* off; u64 total;
+  // count / scan products; an emission launch covers outputs [j_begin, j_begin + total)
+  u32* cnt; u64* lo; const u64* off; u64 total; u64 j_begin;
 };
 
 void join_count(int sem, const StepParams& P, cudaStream_t st);
 constexpr int kEmitTile = 2048;
-// part[t] = last input row whose output range starts at or before t * kEmitTile
-void lbs_partition(const u64* off, u64 n_in, u64 total, u64* part, cudaStream_t st);
+// part[t] = last input row whose output range starts at or before j_begin + t * kEmitTile;
+// part[ntiles] = the row owning output j_begin + total - 1
+void lbs_partition(const u64* off, u64 n_in, u64 j_begin, u64 total, u64* part, cudaStream_t st);
 void join_emit(int sem, const StepParams& P, const u64* part, cudaStream_t st);
 void project_rows(int sem, const StepParams& P, cudaStream_t st);
 

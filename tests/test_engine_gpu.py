@@ -115,6 +115,34 @@ def test_batched_kinship_matches_oracle():
 
 
 # ---------------------------------------------------------------------------
+# candidate sets larger than one sort: chunked sort + unique + (+)-accumulation
+# ---------------------------------------------------------------------------
+
+CHUNK = {"max_candidates": 4096}
+
+
+def test_chunked_tc_unit():
+    a, b = W.erdos_renyi(300, 1500, seed_index=140)
+    st, _ = compare(W.TC_PROGRAM, {"edge": ((a, b),)}, options=CHUNK)
+    assert st["candidates"] > 10 * 4096
+
+
+@pytest.mark.parametrize("semiring", ["max_min", "add_mult", "diff_max_min"])
+def test_chunked_grid(semiring):
+    g = W.grid_reach_instance(40, sub=141)
+    src, dst, p = g["edge"]
+    compare(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, semiring, options=CHUNK)
+
+
+def test_chunked_batched_kinship_add_mult():
+    B = W.batched_instance(4)
+    f, c = B["fact"], B["comp"]
+    inputs = {"fact": ((f[0], f[1], f[2]), f[3], f[4]), "comp": ((c[0], c[1], c[2]), None, c[4])}
+    st, _ = compare(W.KIN_PROGRAM, inputs, "add_mult", rels=["kin"], options=CHUNK)
+    assert st["candidates"] > 10 * 4096
+
+
+# ---------------------------------------------------------------------------
 # errors
 # ---------------------------------------------------------------------------
 
