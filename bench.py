@@ -252,6 +252,29 @@ def batched_fwd_bwd(n_samples=512, loop_samples=32, reps=3):
 
 
 # ---------------------------------------------------------------------------
+# small cases for ncu captures (a few GB on the device at most)
+# ---------------------------------------------------------------------------
+def profile_case(name):
+    import torch
+    from paper_2503_21937_gb300 import Engine, build
+    build.build()
+    e = Engine()
+    if name == "sort_u32_2e26":  # one sort of 2^26 random 30-bit keys (4 LSD passes)
+        keys = W.stream(7001).below(1 << 26, 1 << 30)
+        k = torch.from_numpy(keys.view(np.int32)).cuda()
+        e.prim_sort(k, None, key_bits=30)
+        torch.cuda.synchronize()
+        ok = bool(torch.all(k[1:].to(torch.int64) >= k[:-1].to(torch.int64)).item())
+        print(json.dumps({"case": name, "n": 1 << 26, "sorted": ok}))
+    else:  # transitive closure of an 8,000-node / 40,000-edge power-law graph
+        s, d = W.chung_lu_power_law(8000, 40000, seed_index=3)
+        e.program(W.TC_PROGRAM)
+        e.load("edge", torch.from_numpy(np.stack([s, d]).astype(np.int32)).cuda())
+        print(json.dumps({"case": name, **e.run("unit")}))
+    e.close()
+
+
+# ---------------------------------------------------------------------------
 # the engine arm
 # ---------------------------------------------------------------------------
 def main():
@@ -264,7 +287,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=1, help="extra steps with per-kernel CUDA-event timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched fwd+bwd measurement")
+    ap.add_argument("--profile-case", choices=["sort_u32_2e26", "tc_8k"],
+                    help="run one small case once (for ncu captures) and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return reference_arm(args)
