@@ -155,6 +155,10 @@ int lob_reset(lob_engine* e);
  *   "profile"      1: time every kernel launch with CUDA events      (default 0)
  *   "max_candidates" candidates sorted at once; larger candidate sets are
  *                  sorted and deduplicated in chunks (4096..2^31, default 2^30)
+ *   "emit_filter"  1: under LOB_UNIT, once most candidates of a relation are
+ *                  duplicates, test them against a membership bitmap of the
+ *                  relation when they are emitted (key <= 34 bits); 2: from
+ *                  the first iteration on; 0: never                  (default 1)
  * LOB_E_ARG for an unknown key or a value out of range. */
 int lob_set_option(lob_engine* e, const char* key, int64_t value);
 

@@ -406,6 +406,28 @@ void combine_impl(const void* a, const void* at, u64 na, const void* b, const vo
 }
 
 // ---------------------------------------------------------------------------
+// merge of two sorted key lists that share no key: output position = a + b
+// ---------------------------------------------------------------------------
+template <class K>
+__global__ void __launch_bounds__(kMThreads) k_merge_nodup(const K* __restrict__ A, u64 na, const K* __restrict__ B, u64 nb,
+                                                           const u64* __restrict__ apart, K* __restrict__ out) {
+  __shared__ K sk[kMTile];
+  MergeTile<K> t = load_merge_tile(A, na, B, nb, apart, sk, (u64*)nullptr);
+  const K* sA = sk;
+  const K* sB = sk + t.na_t;
+  const u64 nt = t.na_t + t.nb_t;
+  const u64 diag = min((u64)threadIdx.x * kMItems, nt);
+  u64 ai = local_path(sA, t.na_t, sB, t.nb_t, diag);
+  u64 bi = diag - ai;
+  // each thread writes its run of at most kMItems consecutive outputs
+  for (int s = 0; s < kMItems && ai + bi < nt; s++) {
+    const u64 d = t.d0 + ai + bi;
+    if (ai < t.na_t && (bi >= t.nb_t || sA[ai] <= sB[bi])) out[d] = sA[ai++];
+    else out[d] = sB[bi++];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // load: sorted (key, row) pairs -> unique facts, tags (+)-merged over the rows
 // ---------------------------------------------------------------------------
 template <class Sem>
@@ -560,6 +582,23 @@ void diff_merge(const MergeArgs& a, void* scratch, cudaStream_t st) {
   }
   if (a.key64) { LOB_MERGE(u64) } else { LOB_MERGE(u32) }
 #undef LOB_MERGE
+}
+
+size_t merge_nodup_scratch_bytes(u64 na, u64 nb) { return ((na + nb) / kMTile + 8) * sizeof(u64); }
+
+void merge_nodup(int key64, const void* a, u64 na, const void* b, u64 nb, void* out, void* scratch, cudaStream_t st) {
+  const u64 tiles = (na + nb + kMTile - 1) / kMTile;
+  if (!tiles) return;
+  u64* apart = reinterpret_cast<u64*>(scratch);
+  const double kb = key64 ? 8 : 4;
+  ProfScope ps("merge_nodup", 2.0 * (na + nb) * kb, st);
+  if (key64) {
+    k_merge_path<u64><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, st>>>((const u64*)a, na, (const u64*)b, nb, tiles + 1, apart);
+    k_merge_nodup<u64><<<(unsigned)tiles, kMThreads, 0, st>>>((const u64*)a, na, (const u64*)b, nb, apart, (u64*)out);
+  } else {
+    k_merge_path<u32><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, st>>>((const u32*)a, na, (const u32*)b, nb, tiles + 1, apart);
+    k_merge_nodup<u32><<<(unsigned)tiles, kMThreads, 0, st>>>((const u32*)a, na, (const u32*)b, nb, apart, (u32*)out);
+  }
 }
 
 size_t combine_scratch_bytes(u64 na, u64 nb) {

@@ -146,10 +146,12 @@ static void release_derived(lob_engine& e) {
     for (auto& v : r.views) release_view(e, v);
     r.views.clear();
     for (DevBuf* b : {&r.rkeys, &r.rtags, &r.nkeys, &r.ntags, &r.ckeys, &r.ctags, &r.ckeys2, &r.ctags2, &r.row_factor,
-                      &r.row_keys, &r.akeys, &r.atags, &r.akeys2, &r.atags2})
+                      &r.row_keys, &r.akeys, &r.atags, &r.akeys2, &r.atags2, &r.bitmap})
       e.release(*b);
     r.n_recent = r.n_next = r.n_cand = r.n_acc = 0;
     r.flushed = false;
+    r.filter_on = false;
+    r.last_cand = r.last_new = r.cand_iter = 0;
   }
   e.plans.clear();
 }
@@ -671,6 +673,8 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
       e.after_launch("project");
       e.launches++;
       H.n_cand += sub;
+      H.cand_iter += sub;
+      H.unfiltered = true;
       e.cand_emitted += sub;
     }
     return;
@@ -732,10 +736,19 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
         lbs_partition(e.off.as<u64>(), P.n_in, jb, sub, e.part.as<u64>(), e.stream);
         P.total = sub;
         P.j_begin = jb;
+        if (H.filter_on) {
+          P.bitmap = H.bitmap.as<u32>();
+          P.out_count = e.counts.as<u64>() + 14;
+          e.check(cudaMemsetAsync(P.out_count, 0, sizeof(u64), e.stream), "filter count");
+        }
         join_emit(sem, P, e.part.as<u64>(), e.stream);
         e.after_launch("join emit");
         e.launches += 2;
-        H.n_cand += sub;
+        const u64 written = H.filter_on ? e.read_u64(e.counts.as<u64>() + 14) : sub;
+        P.bitmap = nullptr;
+        P.out_count = nullptr;
+        H.n_cand += written;
+        H.cand_iter += sub;
         e.cand_emitted += sub;
       }
       return;
@@ -777,17 +790,93 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
   }
 }
 
+// Secondary views of H receive the nr new / improved facts now in H.nkeys.
+static void update_secondary_views(lob_engine& e, RelSt& H, u32 k, u64 nr) {
+  if (!nr) return;
+  const int sem = e.semiring;
+  const int ks = sem_kernel(sem);
+  const int sb = stored_bytes(sem);
+  const bool stamps = sem_stamps(sem);
+  for (size_t vi = 1; vi < H.views.size(); vi++) {
+    ViewSt& W = H.views[vi];
+    if (!W.maintained) {
+      W.stale = true;
+      continue;
+    }
+    const int kb = W.lay.key64 ? 8 : 4;
+    auto kt = sort_view_rows(e, H, W, H.nkeys.p, H.ntags.p, nr);
+    e.ensure(W.keys2, (W.n + nr) * kb);
+    if (sb) e.ensure(W.tags2, (W.n + nr) * sb);
+    if (stamps) e.ensure(W.stamps2, (W.n + nr) * 4);
+    MergeArgs M2{};
+    M2.sem = ks;
+    M2.key64 = W.lay.key64;
+    M2.fkeys = W.keys.p; M2.ftags = W.tags.p; M2.fstamp = stamps ? W.stamps.as<u32>() : nullptr; M2.nf = W.n;
+    M2.ukeys = kt.first; M2.utags = kt.second; M2.nu = nr; M2.u_stored = 1;
+    M2.okeys = W.keys2.p; M2.otags = W.tags2.p; M2.ostamp = stamps ? W.stamps2.as<u32>() : nullptr;
+    M2.rkeys = nullptr; M2.rtags = nullptr;
+    M2.stamp = k;
+    M2.counts_dev = e.counts.as<u64>() + 9;
+    scratch_at_least(e, merge_scratch_bytes(W.n, nr));
+    diff_merge(M2, e.scratch.p, e.stream);
+    e.after_launch("view merge");
+    e.launches += 3 + 2 * scan_launches((W.n + nr + 2047) / 2048);
+    e.check(cudaMemcpyAsync(e.pinned, e.counts.as<u64>() + 9, 24, cudaMemcpyDeviceToHost, e.stream), "counts");
+    e.sync();
+    if (e.pinned[2]) throw LobError(LOB_E_CUDA, "internal error: unsorted input to a view merge");
+    const u64 d2 = e.pinned[0];
+    W.n = W.n + nr - d2;
+    std::swap(W.keys, W.keys2);
+    std::swap(W.tags, W.tags2);
+    std::swap(W.stamps, W.stamps2);
+    for (auto& kv : W.index) kv.second.valid = false;
+  }
+}
+
 // sort + unique + difference/merge of one head relation's candidates
 static void dedup_relation(lob_engine& e, RelSt& H, u32 k) {
   H.n_next = 0;
+  H.last_cand = H.cand_iter;
+  H.cand_iter = 0;
   const u64 n = H.n_cand;
-  if (!n && !H.flushed) return;
+  if (!n && !H.flushed) {
+    H.last_new = 0;
+    H.unfiltered = false;
+    return;
+  }
   const int sem = e.semiring;
   const int ks = sem_kernel(sem);
   ViewSt& V = H.views[0];
   const Layout& L = V.lay;
   const int kb = L.key64 ? 8 : 4, cb = cand_bytes(sem), sb = stored_bytes(sem);
   const bool stamps = sem_stamps(sem);
+  const bool fast = H.filter_on && !H.flushed && !H.unfiltered;
+  H.unfiltered = false;
+  if (fast) {
+    // every candidate is distinct and absent from F (membership filter at
+    // emission): sort them, merge into F, and they are the next recent set
+    e.ensure(H.ckeys2, n * kb);
+    void* keys = H.ckeys.p;
+    void* none = nullptr;
+    scratch_at_least(e, sort_scratch_bytes(n, e.opt_radix_bits));
+    sort_pairs(L.key64, 0, &keys, &none, H.ckeys2.p, nullptr, n, L.bits, e.opt_radix_bits, e.scratch.p, e.stream);
+    e.after_launch("candidate sort");
+    e.launches += sort_kernel_launches(n, L.bits, e.opt_radix_bits);
+    e.ensure(V.keys2, (V.n + n) * kb);
+    scratch_at_least(e, merge_nodup_scratch_bytes(V.n, n));
+    merge_nodup(L.key64, V.keys.p, V.n, keys, n, V.keys2.p, e.scratch.p, e.stream);
+    e.after_launch("merge");
+    e.launches += 2;
+    V.n += n;
+    std::swap(V.keys, V.keys2);
+    for (auto& kv : V.index) kv.second.valid = false;
+    if (keys == H.ckeys.p) std::swap(H.nkeys, H.ckeys);
+    else std::swap(H.nkeys, H.ckeys2);
+    H.n_next = n;
+    H.last_new = n;
+    update_secondary_views(e, H, k, n);
+    return;
+  }
   void* ukeys;
   void* utags;
   u64 nu;
@@ -847,41 +936,30 @@ static void dedup_relation(lob_engine& e, RelSt& H, u32 k) {
   std::swap(V.stamps, V.stamps2);
   for (auto& kv : V.index) kv.second.valid = false;
   H.n_next = nr;
-  if (!nr) return;
-  // secondary views receive the same new / improved facts
-  for (size_t vi = 1; vi < H.views.size(); vi++) {
-    ViewSt& W = H.views[vi];
-    if (!W.maintained) {
-      W.stale = true;
-      continue;
-    }
-    auto kt = sort_view_rows(e, H, W, H.nkeys.p, H.ntags.p, nr);
-    e.ensure(W.keys2, (W.n + nr) * kb);
-    if (sb) e.ensure(W.tags2, (W.n + nr) * sb);
-    if (stamps) e.ensure(W.stamps2, (W.n + nr) * 4);
-    MergeArgs M2{};
-    M2.sem = ks;
-    M2.key64 = W.lay.key64;
-    M2.fkeys = W.keys.p; M2.ftags = W.tags.p; M2.fstamp = stamps ? W.stamps.as<u32>() : nullptr; M2.nf = W.n;
-    M2.ukeys = kt.first; M2.utags = kt.second; M2.nu = nr; M2.u_stored = 1;
-    M2.okeys = W.keys2.p; M2.otags = W.tags2.p; M2.ostamp = stamps ? W.stamps2.as<u32>() : nullptr;
-    M2.rkeys = nullptr; M2.rtags = nullptr;
-    M2.stamp = k;
-    M2.counts_dev = e.counts.as<u64>() + 9;
-    scratch_at_least(e, merge_scratch_bytes(W.n, nr));
-    diff_merge(M2, e.scratch.p, e.stream);
-    e.after_launch("view merge");
-    e.launches += 3 + 2 * scan_launches((W.n + nr + 2047) / 2048);
-    e.check(cudaMemcpyAsync(e.pinned, e.counts.as<u64>() + 9, 24, cudaMemcpyDeviceToHost, e.stream), "counts");
-    e.sync();
-    if (e.pinned[2]) throw LobError(LOB_E_CUDA, "internal error: unsorted input to a view merge");
-    const u64 d2 = e.pinned[0];
-    W.n = W.n + nr - d2;
-    std::swap(W.keys, W.keys2);
-    std::swap(W.tags, W.tags2);
-    std::swap(W.stamps, W.stamps2);
-    for (auto& kv : W.index) kv.second.valid = false;
+  H.last_new = nr;
+  if (H.filter_on && nr) {  // keep the membership bitmap equal to F
+    bitmap_set_keys(H.nkeys.p, L.key64, nr, H.bitmap.as<u32>(), e.stream);
+    e.after_launch("bitmap");
+    e.launches++;
   }
+  update_secondary_views(e, H, k, nr);
+}
+
+// Unit semiring: when most of a relation's candidates were duplicates in the
+// previous iteration, keep a membership bitmap of the relation (key bits <= 34,
+// at most 2 GB) and drop known facts and repeated candidates at emission.
+static void maybe_enable_filter(lob_engine& e, RelSt& r) {
+  if (r.filter_on || e.semiring != SR_UNIT || !e.opt_emit_filter || !r.idb) return;
+  const Layout& L = r.views[0].lay;
+  if (L.bits > 34) return;
+  if (e.opt_emit_filter == 1 && (r.last_cand < (1ull << 20) || r.last_new * 2 > r.last_cand)) return;
+  const u64 words = ((1ull << L.bits) + 31) / 32;
+  e.ensure(r.bitmap, words * 4);
+  e.check(cudaMemsetAsync(r.bitmap.p, 0, words * 4, e.stream), "bitmap");
+  bitmap_set_keys(r.views[0].keys.p, L.key64, r.views[0].n, r.bitmap.as<u32>(), e.stream);
+  e.after_launch("bitmap");
+  e.launches++;
+  r.filter_on = true;
 }
 
 static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
@@ -906,6 +984,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
     k++;
     e.iter_counts.emplace_back();
     for (auto& r : e.rels) e.iter_counts.back().emplace_back(r.views[0].n, r.n_recent);
+    for (auto& r : e.rels) maybe_enable_filter(e, r);
     for (auto& r : e.rels) r.n_cand = 0;
     for (auto& p : e.plans) {
       for (auto& A : p.arms) {
@@ -1376,6 +1455,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "sync_check" && (value == 0 || value == 1)) e->opt_sync_check = (int)value;
     else if (k == "profile" && (value == 0 || value == 1)) e->opt_profile = (int)value;
     else if (k == "max_candidates" && value >= 4096 && value <= (int64_t)1 << 31) e->opt_max_cand = (u64)value;
+    else if (k == "emit_filter" && value >= 0 && value <= 2) e->opt_emit_filter = (int)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

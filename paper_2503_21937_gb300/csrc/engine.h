@@ -86,6 +86,11 @@ struct RelSt {
   DevBuf akeys, atags, akeys2, atags2;  // unique candidates of the flushed chunks of this iteration
   u64 n_acc = 0;
   bool flushed = false;
+  // membership filter at emission (unit semiring): bitmap over the key space
+  DevBuf bitmap;
+  bool filter_on = false;
+  bool unfiltered = false;  // this iteration appended candidates that bypassed the filter
+  u64 last_cand = 0, last_new = 0, cand_iter = 0;
   // gradient routing of loaded rows
   DevBuf row_factor, row_keys;
   u32 id_base = 0;
@@ -156,6 +161,7 @@ struct lob_engine {
   // options
   int opt_join_index = 0, opt_dense_bits = 24, opt_radix_bits = 8, opt_sync_check = 0, opt_profile = 0;
   u64 opt_max_cand = 1ull << 30;  // candidates sorted at once (bounds every sort below 2^32 keys)
+  int opt_emit_filter = 1;        // unit semiring: membership bitmap at emission when duplicates dominate
   EngineProfiler prof;
   // run state
   int state = 0;  // 0 loading, 1 ran

@@ -97,6 +97,87 @@ __global__ void __launch_bounds__(256) k_join_emit(const __grid_constant__ StepP
   }
 }
 
+// Emission with the membership filter (unit semiring): candidates whose bit was
+// already set (a known fact, or a candidate emitted earlier) are dropped; the
+// survivors of a tile are written contiguously at a block-reserved offset.
+__global__ void __launch_bounds__(256) k_join_emit_filtered(const __grid_constant__ StepParams P,
+                                                           const u64* __restrict__ part) {
+  typedef SemUnit Sem;
+  constexpr int kItems = kEmitTile / 256;
+  __shared__ u32 row_of[kEmitTile];
+  __shared__ u32 sm[256 / 32 + 1];
+  __shared__ u32 th_inc[256];
+  __shared__ u64 block_base;
+  const u64 j0 = P.j_begin + (u64)blockIdx.x * kEmitTile;
+  const u64 j_end = P.j_begin + P.total;
+  const u64 r0 = part[blockIdx.x];
+  const u64 r_end = part[blockIdx.x + 1];
+  for (int i = threadIdx.x; i < kEmitTile; i += 256) row_of[i] = 0;
+  __syncthreads();
+  for (u64 r = r0 + 1 + threadIdx.x; r <= r_end; r += 256) {
+    const u64 o = P.off[r];
+    if (o < j0 + kEmitTile) atomicMax(&row_of[o - j0], (u32)(r - r0));
+  }
+  __syncthreads();
+  u32 loc[kItems];
+  u32 m = 0;
+#pragma unroll
+  for (int i = 0; i < kItems; i++) {
+    const u32 x = row_of[threadIdx.x * kItems + i];
+    m = x > m ? x : m;
+    loc[i] = m;
+  }
+  const u32 inc = block_inclusive_max<u32>(m, sm);
+  th_inc[threadIdx.x] = inc;
+  __syncthreads();
+  const u32 ex = threadIdx.x ? th_inc[threadIdx.x - 1] : 0u;
+#pragma unroll
+  for (int i = 0; i < kItems; i++) row_of[threadIdx.x * kItems + i] = loc[i] > ex ? loc[i] : ex;
+  __syncthreads();
+  u64 kept[kItems];
+  u32 nkeep = 0;
+  const Layout& L = P.out_lay;
+#pragma unroll 1
+  for (int i = 0; i < kItems; i++) {
+    const u64 j = j0 + (u64)i * 256 + threadIdx.x;
+    if (j >= j_end) break;
+    const u64 r = r0 + row_of[j - j0];
+    const u64 v = P.lo[r] + (j - P.off[r]);
+    u32 val[kMaxSlots];
+    u32 sample;
+    typename Sem::Cand tag;
+    read_input<Sem>(P, r, val, sample, tag);
+    bool ok = P.v_stamp_mode == STAMP_NONE || stamp_ok(P.v_stamp[v], P.v_stamp_mode, P.v_stamp_val);
+    const u64 vk = load_key(P.v_keys, P.v_lay.key64, v);
+    for (int c = 0; c < P.v_lay.arity; c++)
+      if (c >= P.prefix_len && ok) ok = apply_act(P.v_act[c], (u32)field_of(vk, P.v_lay.shift[c], P.v_lay.width[c]), val);
+    for (int f = 0; f < P.n_filters && ok; f++) ok = eval_filter(P.filters[f], val);
+    if (!ok) continue;
+    u64 key = L.swidth ? (u64)sample << L.sshift : 0ull;
+    for (int c = 0; c < L.arity; c++) {
+      const u32 x = P.head_slot[c] >= 0 ? val[P.head_slot[c]] : P.head_const[c];
+      key |= (u64)x << L.shift[c];
+    }
+    const u32 bit = 1u << (u32)(key & 31u);
+    if (atomicOr(P.bitmap + (key >> 5), bit) & bit) continue;
+    kept[nkeep++] = key;
+  }
+  u32 tot;
+  const u32 mine = block_exclusive_sum<u32>(nkeep, sm, &tot);
+  if (threadIdx.x == 0) block_base = tot ? atomicAdd(reinterpret_cast<unsigned long long*>(P.out_count), (u64)tot) : 0ull;
+  __syncthreads();
+  const u64 base = P.out_base + block_base + mine;
+  for (u32 q = 0; q < nkeep; q++) store_key(P.out_keys, L.key64, base + q, kept[q]);
+}
+
+__global__ void k_bitmap_set(const void* __restrict__ keys, int key64, u64 n, u32* __restrict__ bm) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const u64 k = load_key(keys, key64, i);
+    atomicOr(bm + (k >> 5), 1u << (u32)(k & 31u));
+  }
+}
+
 template <class Sem>
 __global__ void __launch_bounds__(256) k_project(const __grid_constant__ StepParams P) {
   const u64 stride = (u64)gridDim.x * blockDim.x;
@@ -191,7 +272,10 @@ template <class Sem> struct CountL {
 template <class Sem> struct EmitL {
   static void go(const StepParams& P, const u64* part, cudaStream_t st) {
     const u64 tiles = (P.total + kEmitTile - 1) / kEmitTile;
-    k_join_emit<Sem><<<(unsigned)tiles, 256, 0, st>>>(P, part);
+    if (std::is_same<Sem, SemUnit>::value && P.bitmap && P.out_packed)
+      k_join_emit_filtered<<<(unsigned)tiles, 256, 0, st>>>(P, part);
+    else
+      k_join_emit<Sem><<<(unsigned)tiles, 256, 0, st>>>(P, part);
   }
 };
 template <class Sem> struct ProjL {
@@ -271,6 +355,11 @@ void read_rows(int sem, const Layout& L, const int* perm, const void* keys, cons
   Perm p;
   for (int j = 0; j < kMaxArity; j++) p.p[j] = j < L.arity ? perm[j] : 0;
   by_sem<ReadL>(sem, L, p, keys, tags, n, cols, stride, otags, samples, st);
+}
+
+void bitmap_set_keys(const void* keys, int key64, u64 n, u32* bitmap, cudaStream_t st) {
+  ProfScope ps("bitmap_build", n * (key64 ? 8.0 : 4.0), st);
+  if (n) k_bitmap_set<<<grid_for(n), 256, 0, st>>>(keys, key64, n, bitmap);
 }
 
 void reduce_max_u32(const u32* a, u64 n, u32* out_dev, cudaStream_t st) {

@@ -123,6 +123,10 @@ struct StepParams {
   u64 out_base;
   // count / scan products; an emission launch covers outputs [j_begin, j_begin + total)
   u32* cnt; u64* lo; const u64* off; u64 total; u64 j_begin;
+  // membership filter (unit semiring): bit `key` of `bitmap` is set for every
+  // fact of the head relation and every candidate emitted so far; only
+  // candidates that set their bit are written, compacted at out_base + *out_count
+  u32* bitmap; u64* out_count;
 };
 
 void join_count(int sem, const StepParams& P, cudaStream_t st);
@@ -132,6 +136,11 @@ constexpr int kEmitTile = 2048;
 void lbs_partition(const u64* off, u64 n_in, u64 j_begin, u64 total, u64* part, cudaStream_t st);
 void join_emit(int sem, const StepParams& P, const u64* part, cudaStream_t st);
 void project_rows(int sem, const StepParams& P, cudaStream_t st);
+// set the bit of every key of a sorted view in a membership bitmap
+void bitmap_set_keys(const void* keys, int key64, u64 n, u32* bitmap, cudaStream_t st);
+// merge two sorted key lists known to share no key (keys only)
+size_t merge_nodup_scratch_bytes(u64 na, u64 nb);
+void merge_nodup(int key64, const void* a, u64 na, const void* b, u64 nb, void* out, void* scratch, cudaStream_t st);
 
 void build_dense_index(const Layout& L, int prefix_len, const void* keys, u64 n, u64* offs, u64 domain, cudaStream_t st);
 // re-encode keys of layout `from` into layout `to`; view column j of `to` is

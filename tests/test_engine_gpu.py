@@ -143,6 +143,30 @@ def test_chunked_batched_kinship_add_mult():
 
 
 # ---------------------------------------------------------------------------
+# membership filter at emission (unit semiring), forced on from iteration 1
+# ---------------------------------------------------------------------------
+
+FILTER = {"emit_filter": 2}
+
+
+def test_filter_tc_and_sg():
+    a, b = W.erdos_renyi(300, 1500, seed_index=150)
+    compare(W.TC_PROGRAM, {"edge": ((a, b),)}, options=FILTER)
+    parent, child, _ = W.random_tree(2000, seed_index=151)
+    compare(W.SG_PROGRAM, {"parent": ((parent, child),)}, options=FILTER)
+
+
+def test_filter_andersen_with_secondary_views():
+    A = W.andersen_program(4000, 12000, seed_index=152)
+    compare(W.ANDERSEN_PROGRAM, {k: ((v[0], v[1]),) for k, v in A.items()}, rels=["pt"], options=FILTER)
+
+
+def test_filter_with_chunking():
+    a, b = W.erdos_renyi(300, 1500, seed_index=153)
+    compare(W.TC_PROGRAM, {"edge": ((a, b),)}, options={"emit_filter": 2, "max_candidates": 4096})
+
+
+# ---------------------------------------------------------------------------
 # errors
 # ---------------------------------------------------------------------------
 
