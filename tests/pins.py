@@ -199,3 +199,34 @@ def layered_reach_dp(src, dst, p, source):
             if dist[w] == dist[v] + 1:
                 acc[w] += t[v] * pw
     return t, dist
+
+
+def andersen_sparse(addr, assign, load, store, n_vars):
+    """Andersen points-to as the least fixpoint of boolean sparse-matrix
+    equations (pt as a vars x vars matrix P):
+        P = Addr + Assign.P + Load.P.P + P^T.Store.P   (boolean),
+    iterated from P = Addr until no entry changes."""
+    import scipy.sparse as sp
+
+    def mat(pq):
+        p, q = pq
+        m = sp.csr_matrix((np.ones(len(p), np.int64), (p.astype(np.int64), q.astype(np.int64))),
+                          shape=(n_vars, n_vars))
+        m.data[:] = 1
+        m.sum_duplicates()
+        m.data[:] = 1
+        return m
+
+    def boolify(m):
+        m = m.tocsr()
+        m.data = (m.data > 0).astype(np.int64)
+        m.eliminate_zeros()
+        return m
+
+    Ad, As, Ld, St = mat(addr), mat(assign), mat(load), mat(store)
+    P = boolify(Ad)
+    while True:
+        nxt = boolify(Ad + As @ P + Ld @ (P @ P) + P.T @ (St @ P))
+        if nxt.nnz == P.nnz:
+            return nxt
+        P = nxt
