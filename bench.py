@@ -287,6 +287,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=1, help="extra steps with per-kernel CUDA-event timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched fwd+bwd measurement")
+    ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
+                    help="engine option applied to every engine (repeatable)")
     ap.add_argument("--profile-case", choices=["sort_u32_2e26", "tc_8k"],
                     help="run one small case once (for ncu captures) and exit")
     args = ap.parse_args()
@@ -316,6 +318,9 @@ def main():
         for name, (prog, rels) in inputs.items():
             e = Engine(stream=stream.cuda_stream)
             e.program(prog)
+            for kv in args.option:
+                k, v = kv.split("=")
+                e.set_option(k, int(v))
             engines[name] = e
     heads = {"sg": "sg", "tc": "path"}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
@@ -434,7 +439,8 @@ def main():
                 "config": {"workload": WORKLOAD, "sg_tree_nodes": SG_NODES, "tc_nodes": TC_NODES,
                            "tc_edges": TC_EDGES, "semiring": "unit", "parallelism": "replicas" if world > 1 else "1 GPU",
                            "l2": "flushed between timed steps (256 MiB write)",
-                           "derived_per_step": derived[0], "iterations": iters},
+                           "derived_per_step": derived[0], "iterations": iters,
+                           "engine_options": args.option},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "kernels": kernels, "batched": batched}
         print(json.dumps(line))

@@ -155,10 +155,14 @@ int lob_reset(lob_engine* e);
  *   "profile"      1: time every kernel launch with CUDA events      (default 0)
  *   "max_candidates" candidates sorted at once; larger candidate sets are
  *                  sorted and deduplicated in chunks (4096..2^31, default 2^30)
- *   "emit_filter"  1: under LOB_UNIT, once most candidates of a relation are
- *                  duplicates, test them against a membership bitmap of the
- *                  relation when they are emitted (key <= 34 bits); 2: from
- *                  the first iteration on; 0: never                  (default 1)
+ *   "emit_filter"  1: under LOB_UNIT, test candidates against a membership
+ *                  bitmap of the relation when they are emitted -- from the
+ *                  first iteration for keys of <= 32 bits, and for keys of
+ *                  <= 34 bits once most candidates are duplicates; 2: from
+ *                  the first iteration for keys of <= 34 bits; 0: never (default 1)
+ *   "sort_algo"    0: three kernels per radix pass, no inter-block waiting;
+ *                  1: one kernel per pass with decoupled look-back (bounded
+ *                  waits; LOB_E_TIMEOUT if one gives up)            (default 0)
  * LOB_E_ARG for an unknown key or a value out of range. */
 int lob_set_option(lob_engine* e, const char* key, int64_t value);
 

@@ -394,6 +394,26 @@ static void prepare(lob_engine& e, int sem) {
 // ---------------------------------------------------------------------------
 static void scratch_at_least(lob_engine& e, size_t bytes) { e.ensure(e.scratch, bytes); }
 
+// error word of the look-back sort (set by a kernel whose bounded wait gave up)
+static u32* sort_err(lob_engine& e) { return reinterpret_cast<u32*>(e.counts.as<u64>() + 15); }
+
+// Radix sort with the engine's chosen algorithm: reduce-then-scan passes by
+// default, or one kernel per pass with decoupled look-back (option sort_algo=1).
+static void engine_sort(lob_engine& e, int key64, int pay_bytes, void** keys, void** pay, void* ktmp, void* ptmp, u64 n,
+                        int bits) {
+  const int rb = sort_supported_radix_bits(e.opt_radix_bits);
+  const bool onesweep = e.opt_sort_algo == 1 && (bits + rb - 1) / rb <= 8;
+  if (onesweep) {
+    scratch_at_least(e, sort_onesweep_scratch_bytes(n, rb));
+    sort_pairs_onesweep(key64, pay_bytes, keys, pay, ktmp, ptmp, n, bits, rb, e.scratch.p, sort_err(e), e.stream);
+    e.launches += sort_onesweep_launches(n, bits, rb);
+  } else {
+    scratch_at_least(e, sort_scratch_bytes(n, rb));
+    sort_pairs(key64, pay_bytes, keys, pay, ktmp, ptmp, n, bits, rb, e.scratch.p, e.stream);
+    e.launches += sort_kernel_launches(n, bits, rb);
+  }
+}
+
 // Re-encode n primary-layout facts into view `v`'s layout and sort them.
 // Returns pointers (into the engine's tmp buffers) to the sorted keys and tags.
 static std::pair<void*, void*> sort_view_rows(lob_engine& e, RelSt& r, ViewSt& v, const void* pkeys, const void* ptags,
@@ -411,10 +431,9 @@ static std::pair<void*, void*> sort_view_rows(lob_engine& e, RelSt& r, ViewSt& v
   e.after_launch("repack");
   void* k = e.tmp_keys.p;
   void* t = e.tmp_tags.p;
-  scratch_at_least(e, sort_scratch_bytes(n, e.opt_radix_bits));
-  sort_pairs(v.lay.key64, sb, &k, &t, e.tmp_keys2.p, e.tmp_tags2.p, n, v.lay.bits, e.opt_radix_bits, e.scratch.p, e.stream);
+  engine_sort(e, v.lay.key64, sb, &k, &t, e.tmp_keys2.p, e.tmp_tags2.p, n, v.lay.bits);
   e.after_launch("view sort");
-  e.launches += 1 + sort_kernel_launches(n, v.lay.bits, e.opt_radix_bits);
+  e.launches += 1;
   return {k, t};
 }
 
@@ -449,11 +468,8 @@ static void load_facts(lob_engine& e) {
     }
     void* k = e.tmp_keys.p;
     void* rows = e.tmp_tags.p;
-    scratch_at_least(e, sort_scratch_bytes(n, e.opt_radix_bits));
-    sort_pairs(V.lay.key64, 4, &k, &rows, e.tmp_keys2.p, e.tmp_tags2.p, n, V.lay.bits, e.opt_radix_bits, e.scratch.p,
-               e.stream);
+    engine_sort(e, V.lay.key64, 4, &k, &rows, e.tmp_keys2.p, e.tmp_tags2.p, n, V.lay.bits);
     e.after_launch("load sort");
-    e.launches += sort_kernel_launches(n, V.lay.bits, e.opt_radix_bits);
     e.ensure(V.keys, n * kb);
     if (sb) e.ensure(V.tags, n * sb);
     if (stamps) e.ensure(V.stamps, n * 4);
@@ -601,10 +617,8 @@ static void flush_candidates(lob_engine& e, RelSt& H) {
   if (cb) e.ensure(H.ctags2, n * cb);
   void* keys = H.ckeys.p;
   void* tags = H.ctags.p;
-  scratch_at_least(e, sort_scratch_bytes(n, e.opt_radix_bits));
-  sort_pairs(L.key64, cb, &keys, &tags, H.ckeys2.p, H.ctags2.p, n, L.bits, e.opt_radix_bits, e.scratch.p, e.stream);
+  engine_sort(e, L.key64, cb, &keys, &tags, H.ckeys2.p, H.ctags2.p, n, L.bits);
   e.after_launch("chunk sort");
-  e.launches += sort_kernel_launches(n, L.bits, e.opt_radix_bits);
   void* ukeys = keys == H.ckeys.p ? H.ckeys2.p : H.ckeys.p;
   void* utags = tags == H.ctags.p ? H.ctags2.p : H.ctags.p;
   scratch_at_least(e, unique_scratch_bytes(n));
@@ -858,11 +872,9 @@ static void dedup_relation(lob_engine& e, RelSt& H, u32 k) {
     e.ensure(H.ckeys2, n * kb);
     void* keys = H.ckeys.p;
     void* none = nullptr;
-    scratch_at_least(e, sort_scratch_bytes(n, e.opt_radix_bits));
-    sort_pairs(L.key64, 0, &keys, &none, H.ckeys2.p, nullptr, n, L.bits, e.opt_radix_bits, e.scratch.p, e.stream);
+    engine_sort(e, L.key64, 0, &keys, &none, H.ckeys2.p, nullptr, n, L.bits);
     e.after_launch("candidate sort");
-    e.launches += sort_kernel_launches(n, L.bits, e.opt_radix_bits);
-    e.ensure(V.keys2, (V.n + n) * kb);
+      e.ensure(V.keys2, (V.n + n) * kb);
     scratch_at_least(e, merge_nodup_scratch_bytes(V.n, n));
     merge_nodup(L.key64, V.keys.p, V.n, keys, n, V.keys2.p, e.scratch.p, e.stream);
     e.after_launch("merge");
@@ -893,11 +905,9 @@ static void dedup_relation(lob_engine& e, RelSt& H, u32 k) {
     if (cb) e.ensure(H.ctags2, n * cb);
     void* keys = H.ckeys.p;
     void* tags = H.ctags.p;
-    scratch_at_least(e, sort_scratch_bytes(n, e.opt_radix_bits));
-    sort_pairs(L.key64, cb, &keys, &tags, H.ckeys2.p, H.ctags2.p, n, L.bits, e.opt_radix_bits, e.scratch.p, e.stream);
+    engine_sort(e, L.key64, cb, &keys, &tags, H.ckeys2.p, H.ctags2.p, n, L.bits);
     e.after_launch("candidate sort");
-    e.launches += sort_kernel_launches(n, L.bits, e.opt_radix_bits);
-    ukeys = keys == H.ckeys.p ? H.ckeys2.p : H.ckeys.p;
+      ukeys = keys == H.ckeys.p ? H.ckeys2.p : H.ckeys.p;
     utags = tags == H.ctags.p ? H.ctags2.p : H.ctags.p;
     scratch_at_least(e, unique_scratch_bytes(n));
     unique_run(ks, L.key64, keys, tags, n, ukeys, utags, e.counts.as<u64>() + 1, e.scratch.p, e.stream);
@@ -945,14 +955,15 @@ static void dedup_relation(lob_engine& e, RelSt& H, u32 k) {
   update_secondary_views(e, H, k, nr);
 }
 
-// Unit semiring: when most of a relation's candidates were duplicates in the
-// previous iteration, keep a membership bitmap of the relation (key bits <= 34,
-// at most 2 GB) and drop known facts and repeated candidates at emission.
+// Unit semiring: keep a membership bitmap of the relation and drop known facts
+// and repeated candidates at emission -- from the first iteration when the key
+// has at most 32 bits (bitmap <= 512 MB), and for keys of up to 34 bits (2 GB)
+// once most of the previous iteration's candidates were duplicates.
 static void maybe_enable_filter(lob_engine& e, RelSt& r) {
   if (r.filter_on || e.semiring != SR_UNIT || !e.opt_emit_filter || !r.idb) return;
   const Layout& L = r.views[0].lay;
   if (L.bits > 34) return;
-  if (e.opt_emit_filter == 1 && (r.last_cand < (1ull << 20) || r.last_new * 2 > r.last_cand)) return;
+  if (e.opt_emit_filter == 1 && L.bits > 32 && (r.last_cand < (1ull << 20) || r.last_new * 2 > r.last_cand)) return;
   const u64 words = ((1ull << L.bits) + 31) / 32;
   e.ensure(r.bitmap, words * 4);
   e.check(cudaMemsetAsync(r.bitmap.p, 0, words * 4, e.stream), "bitmap");
@@ -979,6 +990,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   u32 k = 0;
   e.iter_counts.clear();
   e.cand_emitted = 0;
+  e.check(cudaMemsetAsync(sort_err(e), 0, sizeof(u32), e.stream), "sort error word");
   for (;;) {
     if (k >= max_iters) { rc = LOB_E_MAXITER; break; }
     k++;
@@ -1015,6 +1027,8 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   e.check(cudaEventRecord(ev1, e.stream), "event");
   e.sync();
   e.prof.flush();
+  if (e.read_u64(e.counts.as<u64>() + 15) & 0xFFFFFFFFull)
+    throw LobError(LOB_E_TIMEOUT, "a bounded device wait of the sort gave up; the run's results are invalid");
   float ms = 0;
   cudaEventElapsedTime(&ms, ev0, ev1);
   cudaEventDestroy(ev0);
@@ -1349,16 +1363,16 @@ int lob_prim_sort(lob_engine* e, void* keys, void* payload, uint64_t n, uint32_t
     if (n < 2) return LOB_OK;
     e->ensure(e->tmp_keys, n * key_bytes);
     if (payload_bytes) e->ensure(e->tmp_tags, n * payload_bytes);
-    scratch_at_least(*e, sort_scratch_bytes(n, e->opt_radix_bits));
     void* k = keys;
     void* p = payload;
-    sort_pairs(key_bytes == 8, payload_bytes, &k, &p, e->tmp_keys.p, e->tmp_tags.p, n, (int)key_bits, e->opt_radix_bits,
-               e->scratch.p, e->stream);
+    e->check(cudaMemsetAsync(sort_err(*e), 0, sizeof(u32), e->stream), "sort error word");
+    engine_sort(*e, key_bytes == 8, payload_bytes, &k, &p, e->tmp_keys.p, e->tmp_tags.p, n, (int)key_bits);
     e->after_launch("sort");
     if (k != keys) e->check(cudaMemcpyAsync(keys, k, n * key_bytes, cudaMemcpyDeviceToDevice, e->stream), "copy back");
     if (payload_bytes && p != payload)
       e->check(cudaMemcpyAsync(payload, p, n * payload_bytes, cudaMemcpyDeviceToDevice, e->stream), "copy back");
     e->sync();
+    if (e->read_u64(e->counts.as<u64>() + 15) & 0xFFFFFFFFull) throw LobError(LOB_E_TIMEOUT, "sort look-back wait gave up");
     return LOB_OK;
   });
 }
@@ -1456,6 +1470,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "profile" && (value == 0 || value == 1)) e->opt_profile = (int)value;
     else if (k == "max_candidates" && value >= 4096 && value <= (int64_t)1 << 31) e->opt_max_cand = (u64)value;
     else if (k == "emit_filter" && value >= 0 && value <= 2) e->opt_emit_filter = (int)value;
+    else if (k == "sort_algo" && (value == 0 || value == 1)) e->opt_sort_algo = (int)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

@@ -162,6 +162,7 @@ struct lob_engine {
   int opt_join_index = 0, opt_dense_bits = 24, opt_radix_bits = 8, opt_sync_check = 0, opt_profile = 0;
   u64 opt_max_cand = 1ull << 30;  // candidates sorted at once (bounds every sort below 2^32 keys)
   int opt_emit_filter = 1;        // unit semiring: membership bitmap at emission when duplicates dominate
+  int opt_sort_algo = 0;          // 0: reduce-then-scan passes, 1: one kernel per pass with look-back
   EngineProfiler prof;
   // run state
   int state = 0;  // 0 loading, 1 ran

@@ -37,6 +37,12 @@ size_t sort_scratch_bytes(u64 n, int rb);
 void sort_pairs(int key64, int pay_bytes, void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits, int rb,
                 void* scratch, cudaStream_t st);
 int sort_kernel_launches(u64 n, int bits, int rb);
+// Same result with one kernel per digit pass (decoupled look-back); *err is set
+// (never cleared) if a bounded wait gave up, in which case the output is invalid.
+size_t sort_onesweep_scratch_bytes(u64 n, int rb);
+void sort_pairs_onesweep(int key64, int pay_bytes, void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits,
+                         int rb, void* scratch, u32* err, cudaStream_t st);
+int sort_onesweep_launches(u64 n, int bits, int rb);
 
 // ---------------------------------------------------------------------------
 // unique, difference + merge, load normalisation (dedup.cu)

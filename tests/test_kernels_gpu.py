@@ -86,6 +86,28 @@ def test_sort_adversarial(eng, pattern):
     assert np.array_equal(_host(p, np.uint32), pay[order])
 
 
+@pytest.mark.parametrize("n,bits,pay", [(1, 30, 4), (4097, 30, 4), (1_000_003, 30, 0), (300_001, 36, 8), (70_000, 32, 4)])
+def test_sort_lookback_variant(eng, n, bits, pay):
+    eng.set_option("sort_algo", 1)
+    try:
+        s = W.stream(520 + n % 11)
+        mask = np.uint64((1 << bits) - 1)
+        keys = s.take(n) & mask
+        keys = keys.astype(np.uint32) if bits <= 32 else keys
+        if n > 100:
+            keys[:50] = keys[0]  # a run of equal keys
+        p = np.arange(n, dtype=np.uint32) if pay == 4 else (s.take(n) if pay == 8 else None)
+        k = _dev(keys)
+        pd = _dev(p) if p is not None else None
+        eng.prim_sort(k, pd, key_bits=bits)
+        order = np.argsort(keys, kind="stable")
+        assert np.array_equal(_host(k, keys.dtype), keys[order])
+        if p is not None:
+            assert np.array_equal(_host(pd, p.dtype), p[order])
+    finally:
+        eng.set_option("sort_algo", 0)
+
+
 def test_sort_keys_only(eng):
     n = 500_000
     keys = W.stream(501).below(n, 1 << 30)
