@@ -266,10 +266,15 @@ def profile_case(name):
         torch.cuda.synchronize()
         ok = bool(torch.all(k[1:].to(torch.int64) >= k[:-1].to(torch.int64)).item())
         print(json.dumps({"case": name, "n": 1 << 26, "sorted": ok}))
-    else:  # transitive closure of an 8,000-node / 40,000-edge power-law graph
+    elif name == "tc_8k":  # transitive closure of an 8,000-node / 40,000-edge power-law graph
         s, d = W.chung_lu_power_law(8000, 40000, seed_index=3)
         e.program(W.TC_PROGRAM)
         e.load("edge", torch.from_numpy(np.stack([s, d]).astype(np.int32)).cuda())
+        print(json.dumps({"case": name, **e.run("unit")}))
+    else:  # same generation on a 20,000-node random tree
+        parent, child, _ = W.random_tree(20000, seed_index=2)
+        e.program(W.SG_PROGRAM)
+        e.load("parent", torch.from_numpy(np.stack([parent, child]).astype(np.int32)).cuda())
         print(json.dumps({"case": name, **e.run("unit")}))
     e.close()
 
@@ -289,7 +294,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched fwd+bwd measurement")
     ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
                     help="engine option applied to every engine (repeatable)")
-    ap.add_argument("--profile-case", choices=["sort_u32_2e26", "tc_8k"],
+    ap.add_argument("--profile-case", choices=["sort_u32_2e26", "tc_8k", "sg_20k"],
                     help="run one small case once (for ncu captures) and exit")
     args = ap.parse_args()
     if args.profile_case:

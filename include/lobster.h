@@ -163,6 +163,8 @@ int lob_reset(lob_engine* e);
  *   "sort_algo"    0: three kernels per radix pass, no inter-block waiting;
  *                  1: one kernel per pass with decoupled look-back (bounded
  *                  waits; LOB_E_TIMEOUT if one gives up)            (default 0)
+ *   "packed_join"  1: join kernels on packed words when an arm's bindings
+ *                  fit 64 bits; 0: the general kernels               (default 1)
  * LOB_E_ARG for an unknown key or a value out of range. */
 int lob_set_option(lob_engine* e, const char* key, int64_t value);
 

@@ -419,12 +419,18 @@ __global__ void __launch_bounds__(kMThreads) k_merge_nodup(const K* __restrict__
   const u64 diag = min((u64)threadIdx.x * kMItems, nt);
   u64 ai = local_path(sA, t.na_t, sB, t.nb_t, diag);
   u64 bi = diag - ai;
-  // each thread writes its run of at most kMItems consecutive outputs
+  // each thread merges its run of at most kMItems outputs into registers; the
+  // tile is then written back through shared memory with coalesced stores
+  K v[kMItems];
+  int m = 0;
   for (int s = 0; s < kMItems && ai + bi < nt; s++) {
-    const u64 d = t.d0 + ai + bi;
-    if (ai < t.na_t && (bi >= t.nb_t || sA[ai] <= sB[bi])) out[d] = sA[ai++];
-    else out[d] = sB[bi++];
+    if (ai < t.na_t && (bi >= t.nb_t || sA[ai] <= sB[bi])) v[m++] = sA[ai++];
+    else v[m++] = sB[bi++];
   }
+  __syncthreads();
+  for (int s = 0; s < m; s++) sk[diag + s] = v[s];
+  __syncthreads();
+  for (u64 i = threadIdx.x; i < nt; i += kMThreads) out[t.d0 + i] = sk[i];
 }
 
 // ---------------------------------------------------------------------------

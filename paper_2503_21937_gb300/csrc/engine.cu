@@ -321,6 +321,160 @@ static ArmPlan plan_arm(lob_engine& e, const RuleAst& R, int delta, bool idempot
   return A;
 }
 
+// ---------------------------------------------------------------------------
+// packed-word compilation of an arm (see pjoin.cu)
+// ---------------------------------------------------------------------------
+static POperand op_field(int word, int shift, int width) {
+  POperand o{};
+  o.word = (uint8_t)word;
+  o.shift = (uint8_t)shift;
+  o.width = (uint8_t)width;
+  return o;
+}
+static POperand op_const(u32 c) {
+  POperand o{};
+  o.word = 2;
+  o.cval = c;
+  return o;
+}
+
+static PackedArm compile_packed(lob_engine& e, const RuleAst& R, const ArmPlan& A) {
+  PackedArm out;
+  const int nv = (int)R.var_names.size();
+  std::vector<POperand> loc(nv, op_const(0));
+  auto term_op = [&](const Term& t) { return t.var ? loc[t.v] : op_const(t.v); };
+  auto add_check = [&](PCheck* arr, int& n, POperand a, POperand b, bool eq) {
+    if (n >= kMaxPChecks) return false;
+    PCheck c{};
+    c.a = a;
+    c.b = b;
+    c.eq = eq ? 1 : 0;
+    arr[n++] = c;
+    return true;
+  };
+  PStep cur;
+  std::memset(&cur, 0, sizeof(cur));
+  // source atom: the delta relation's primary layout
+  const RelSt& D = e.rels[R.body[A.delta].rel];
+  const Layout& L0 = D.views[0].lay;
+  cur.in_packed = 1;
+  cur.in_w64 = L0.key64;
+  std::vector<char> bound(nv, 0);
+  for (size_t c = 0; c < R.body[A.delta].args.size(); c++) {
+    const Term& t = R.body[A.delta].args[c];
+    const POperand f = op_field(0, L0.shift[c], L0.width[c]);
+    if (!t.var) { if (!add_check(cur.in_checks, cur.n_in_checks, f, op_const(t.v), true)) return out; }
+    else if (bound[t.v]) { if (!add_check(cur.in_checks, cur.n_in_checks, f, loc[t.v], true)) return out; }
+    else { loc[t.v] = f; bound[t.v] = 1; }
+  }
+  for (int f : A.steps[0].filters) {
+    const FilterAst& F = R.filters[f];
+    if (!add_check(cur.in_checks, cur.n_in_checks, term_op(F.a), term_op(F.b), F.eq)) return out;
+  }
+  POperand sample = L0.swidth ? op_field(0, L0.sshift, L0.swidth) : op_const(0);
+  const Layout& HL = e.rels[R.head.rel].views[0].lay;
+  auto head_fields = [&](PStep& P) {
+    P.n_out = 0;
+    for (size_t c = 0; c < R.head.args.size(); c++) {
+      PField f{};
+      f.op = term_op(R.head.args[c]);
+      f.shift = (uint8_t)HL.shift[c];
+      P.out[P.n_out++] = f;
+    }
+    if (HL.swidth) {
+      PField f{};
+      f.op = sample;
+      f.shift = (uint8_t)HL.sshift;
+      P.out[P.n_out++] = f;
+    }
+    P.out_w64 = HL.key64;
+  };
+  if (A.steps.size() == 1) {
+    head_fields(cur);
+    out.steps.push_back(cur);
+    out.ok = true;
+    return out;
+  }
+  for (size_t s = 1; s < A.steps.size(); s++) {
+    const StepPlan& S = A.steps[s];
+    const AtomAst& atom = R.body[S.atom];
+    const ViewSt& W = e.rels[atom.rel].views[S.view];
+    const Layout& WL = W.lay;
+    const int rs = rest_shift(WL, S.prefix_len);
+    cur.n_prefix = 0;
+    if (WL.swidth) {
+      PField f{};
+      f.op = sample;
+      f.shift = (uint8_t)(WL.sshift - rs);
+      f.limit_bits = (uint8_t)WL.swidth;
+      cur.prefix[cur.n_prefix++] = f;
+    }
+    for (int j = 0; j < S.prefix_len; j++) {
+      PField f{};
+      f.op = term_op(atom.args[W.perm[j]]);
+      f.shift = (uint8_t)(WL.shift[j] - rs);
+      f.limit_bits = (uint8_t)WL.width[j];
+      cur.prefix[cur.n_prefix++] = f;
+    }
+    cur.rest_shift = rs >= 64 ? 0 : rs;
+    cur.whole_view = S.prefix_len == 0 && WL.swidth == 0;
+    cur.n_checks = 0;
+    for (int j = S.prefix_len; j < (int)atom.args.size(); j++) {
+      const Term& t = atom.args[W.perm[j]];
+      const POperand f = op_field(1, WL.shift[j], WL.width[j]);
+      const ColAct& act = S.act[j];
+      if (act.op == OP_BIND) loc[t.v] = f;
+      else if (!add_check(cur.checks, cur.n_checks, f, act.op == OP_CHECK_CONST ? op_const(act.cnst) : loc[t.v], true))
+        return out;
+    }
+    for (int f : S.filters) {
+      const FilterAst& F = R.filters[f];
+      if (!add_check(cur.checks, cur.n_checks, term_op(F.a), term_op(F.b), F.eq)) return out;
+    }
+    const bool last = s + 1 == A.steps.size();
+    if (last) {
+      head_fields(cur);
+      out.steps.push_back(cur);
+      break;
+    }
+    // binding word of the live variables (and the sample id) for the next step
+    int acc = 0;
+    cur.n_out = 0;
+    std::vector<POperand> next(nv, op_const(0));
+    for (int v : S.live) {
+      PField f{};
+      f.op = loc[v];
+      f.shift = (uint8_t)acc;
+      cur.out[cur.n_out++] = f;
+      next[v] = op_field(0, acc, loc[v].width);
+      acc += loc[v].width;
+      if (cur.n_out >= kMaxPFields) return out;
+    }
+    POperand next_sample = op_const(0);
+    if (WL.swidth) {
+      PField f{};
+      f.op = sample;
+      f.shift = (uint8_t)acc;
+      cur.out[cur.n_out++] = f;
+      next_sample = op_field(0, acc, WL.swidth);
+      acc += WL.swidth;
+    }
+    if (acc > 64 || acc == 0) return out;
+    cur.out_w64 = acc > 32;
+    out.steps.push_back(cur);
+    // the next step reads this binding word
+    PStep nxt;
+    std::memset(&nxt, 0, sizeof(nxt));
+    nxt.in_packed = 0;
+    nxt.in_w64 = cur.out_w64;
+    loc = next;
+    sample = next_sample;
+    cur = nxt;
+  }
+  out.ok = true;
+  return out;
+}
+
 static void prepare(lob_engine& e, int sem) {
   release_derived(e);
   e.semiring = sem;
@@ -387,6 +541,8 @@ static void prepare(lob_engine& e, int sem) {
       for (size_t s = 1; s < A.steps.size(); s++)
         if (late) e.rels[p.ast.body[A.steps[s].atom].rel].views[A.steps[s].view].maintained = true;
     }
+  for (auto& p : e.plans)
+    for (auto& A : p.arms) A.packed = e.opt_packed_join ? compile_packed(e, p.ast, A) : PackedArm{};
 }
 
 // ---------------------------------------------------------------------------
@@ -731,7 +887,10 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
     join_count(sem, P, e.stream);
     e.after_launch("join count");
     scratch_at_least(e, scan_scratch_elems(P.n_in) * 8 + 64);
-    exclusive_scan<u32, u64>(e.cnt.as<u32>(), e.off.as<u64>(), P.n_in, e.counts.as<u64>(), e.scratch.as<u64>(), e.stream);
+    {
+      ProfScope ps("join_scan", P.n_in * 12.0, e.stream);
+      exclusive_scan<u32, u64>(e.cnt.as<u32>(), e.off.as<u64>(), P.n_in, e.counts.as<u64>(), e.scratch.as<u64>(), e.stream);
+    }
     e.after_launch("join scan");
     e.launches += 1 + scan_launches(P.n_in);
     const u64 total = e.read_u64(e.counts.as<u64>());
@@ -844,6 +1003,133 @@ static void update_secondary_views(lob_engine& e, RelSt& H, u32 k, u64 nr) {
     std::swap(W.tags, W.tags2);
     std::swap(W.stamps, W.stamps2);
     for (auto& kv : W.index) kv.second.valid = false;
+  }
+}
+
+// The same arm on the packed-word kernels (compile_packed).
+static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) {
+  const RuleAst& R = rp.ast;
+  RelSt& D = e.rels[R.body[A.delta].rel];
+  RelSt& H = e.rels[R.head.rel];
+  const int sem = sem_kernel(e.semiring);
+  const int cb = cand_bytes(e.semiring), sb = stored_bytes(e.semiring);
+  if (!D.n_recent) return;
+  if (A.steps.size() == 1) {  // projection, in chunks of at most opt_max_cand rows
+    PStep P = A.packed.steps[0];
+    const int kb = D.views[0].lay.key64 ? 8 : 4;
+    for (u64 rb = 0; rb < D.n_recent; rb += e.opt_max_cand) {
+      const u64 sub = std::min(e.opt_max_cand, D.n_recent - rb);
+      if (H.n_cand + sub > e.opt_max_cand) flush_candidates(e, H);
+      ensure_cand(e, H, sub);
+      P.in_words = static_cast<const char*>(D.rkeys.p) + rb * kb;
+      P.in_tags = sb ? static_cast<const char*>(D.rtags.p) + rb * sb : nullptr;
+      P.n_in = sub;
+      P.out_words = H.ckeys.p;
+      P.out_tags = H.ctags.p;
+      P.out_base = H.n_cand;
+      pjoin_project(sem, P, e.stream);
+      e.after_launch("project");
+      e.launches++;
+      H.n_cand += sub;
+      H.cand_iter += sub;
+      H.unfiltered = true;
+      e.cand_emitted += sub;
+    }
+    return;
+  }
+  const void* in_words = D.rkeys.p;
+  const void* in_tags = D.rtags.p;
+  u64 n_in = D.n_recent;
+  int side = 0;
+  for (size_t s = 1; s < A.steps.size(); s++) {
+    const StepPlan& S = A.steps[s];
+    const bool last = s + 1 == A.steps.size();
+    RelSt& V = e.rels[R.body[S.atom].rel];
+    ViewSt& W = V.views[S.view];
+    if (W.stale) rebuild_view(e, V, W);
+    if (!W.n) return;
+    ensure_index(e, W, S.prefix_len);
+    PStep P = A.packed.steps[s - 1];
+    P.in_words = in_words;
+    P.in_tags = in_tags;
+    P.n_in = n_in;
+    P.v_keys = W.keys.p;
+    P.v_key64 = W.lay.key64;
+    P.v_tags = W.tags.p;
+    P.v_stamp = W.stamps.as<u32>();
+    P.v_n = W.n;
+    P.v_stamp_mode = S.probe_old ? STAMP_LT : STAMP_NONE;
+    P.v_stamp_val = k - 1;
+    const IndexSt& I = W.index[S.prefix_len];
+    P.index_mode = I.mode;
+    P.dense_offs = I.offs.as<u64>();
+    e.ensure(e.cnt, n_in * 4);
+    e.ensure(e.lo, n_in * 8);
+    e.ensure(e.off, (n_in + 1) * 8);
+    P.cnt = e.cnt.as<u32>();
+    P.lo32 = e.lo.as<u32>();
+    if (W.n > 0xFFFFFFFFull) throw LobError(LOB_E_ARG, "packed join needs views below 2^32 rows");
+    pjoin_count(sem, P, e.stream);
+    e.after_launch("join count");
+    scratch_at_least(e, scan_scratch_elems(n_in) * 8 + 64);
+    {
+      ProfScope ps("join_scan", n_in * 12.0, e.stream);
+      exclusive_scan<u32, u64>(e.cnt.as<u32>(), e.off.as<u64>(), n_in, e.counts.as<u64>(), e.scratch.as<u64>(), e.stream);
+    }
+    e.after_launch("join scan");
+    e.launches += 1 + scan_launches(n_in);
+    const u64 total = e.read_u64(e.counts.as<u64>());
+    if (!total) return;
+    P.off = e.off.as<u64>();
+    if (last) {  // candidates, in sub-ranges of at most opt_max_cand outputs
+      for (u64 jb = 0; jb < total; jb += e.opt_max_cand) {
+        const u64 sub = std::min(e.opt_max_cand, total - jb);
+        if (H.n_cand + sub > e.opt_max_cand) flush_candidates(e, H);
+        ensure_cand(e, H, sub);
+        P.out_words = H.ckeys.p;
+        P.out_tags = H.ctags.p;
+        P.out_base = H.n_cand;
+        const u64 nt = (sub + kEmitTile - 1) / kEmitTile;
+        e.ensure(e.part, (nt + 1) * 8);
+        lbs_partition(e.off.as<u64>(), n_in, jb, sub, e.part.as<u64>(), e.stream);
+        P.total = sub;
+        P.j_begin = jb;
+        P.bitmap = nullptr;
+        P.out_count = nullptr;
+        if (H.filter_on) {
+          P.bitmap = H.bitmap.as<u32>();
+          P.out_count = e.counts.as<u64>() + 14;
+          e.check(cudaMemsetAsync(P.out_count, 0, sizeof(u64), e.stream), "filter count");
+        }
+        pjoin_emit(sem, P, e.part.as<u64>(), e.stream);
+        e.after_launch("join emit");
+        e.launches += 2;
+        const u64 written = H.filter_on ? e.read_u64(e.counts.as<u64>() + 14) : sub;
+        H.n_cand += written;
+        H.cand_iter += sub;
+        e.cand_emitted += sub;
+      }
+      return;
+    }
+    const int out_side = side ^ 1;
+    const int wb = P.out_w64 ? 8 : 4;
+    e.ensure(e.bind[out_side][0], total * wb);
+    if (cb) e.ensure(e.bind[out_side][kMaxSlots + 1], total * cb);
+    P.out_words = e.bind[out_side][0].p;
+    P.out_tags = e.bind[out_side][kMaxSlots + 1].p;
+    P.out_base = 0;
+    const u64 ntiles = (total + kEmitTile - 1) / kEmitTile;
+    e.ensure(e.part, (ntiles + 1) * 8);
+    lbs_partition(e.off.as<u64>(), n_in, 0, total, e.part.as<u64>(), e.stream);
+    P.total = total;
+    P.j_begin = 0;
+    pjoin_emit(sem, P, e.part.as<u64>(), e.stream);
+    e.after_launch("join emit");
+    e.launches += 2;
+    side = out_side;
+    in_words = e.bind[side][0].p;
+    in_tags = e.bind[side][kMaxSlots + 1].p;
+    n_in = total;
   }
 }
 
@@ -1007,7 +1293,8 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
           if (br.views[0].n == br.n_recent) { skip = true; break; }
         }
         if (skip) continue;
-        run_arm(e, p, A, k);
+        if (A.packed.ok) run_arm_packed(e, p, A, k);
+        else run_arm(e, p, A, k);
       }
     }
     u64 total_new = 0;
@@ -1471,6 +1758,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "max_candidates" && value >= 4096 && value <= (int64_t)1 << 31) e->opt_max_cand = (u64)value;
     else if (k == "emit_filter" && value >= 0 && value <= 2) e->opt_emit_filter = (int)value;
     else if (k == "sort_algo" && (value == 0 || value == 1)) e->opt_sort_algo = (int)value;
+    else if (k == "packed_join" && (value == 0 || value == 1)) e->opt_packed_join = (int)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

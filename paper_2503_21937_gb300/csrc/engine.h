@@ -8,6 +8,7 @@
 
 #include "../../include/lobster.h"
 #include "kernels.h"
+#include "pjoin.h"
 
 struct LobError : std::runtime_error {
   int code;
@@ -110,10 +111,17 @@ struct StepPlan {
   std::vector<int> filters;
   std::vector<int> live;  // slots materialised after this step
 };
+// The same arm compiled for the packed kernels (pjoin.cu): per probe step (or
+// the single projection) a PStep template whose pointers are filled per launch.
+struct PackedArm {
+  bool ok = false;
+  std::vector<PStep> steps;
+};
 struct ArmPlan {
   int delta = 0;
   std::vector<StepPlan> steps;
   std::vector<u32> before_rels;  // relations of body atoms before the delta atom
+  PackedArm packed;
 };
 struct RulePlan {
   RuleAst ast;
@@ -163,6 +171,7 @@ struct lob_engine {
   u64 opt_max_cand = 1ull << 30;  // candidates sorted at once (bounds every sort below 2^32 keys)
   int opt_emit_filter = 1;        // unit semiring: membership bitmap at emission when duplicates dominate
   int opt_sort_algo = 0;          // 0: reduce-then-scan passes, 1: one kernel per pass with look-back
+  int opt_packed_join = 1;        // packed-word join kernels when an arm's bindings fit 64 bits
   EngineProfiler prof;
   // run state
   int state = 0;  // 0 loading, 1 ran

@@ -1,0 +1,502 @@
+// Packed join pipeline: the same count / emit steps as join.cu, specialised
+// for rules whose intermediate bindings fit one 64-bit word.
+//
+// Every rule variable lives in a bit field of either the input word (a packed
+// relation key, or a packed binding row of the previous step) or the matched
+// view key.  The plan compiles each step into operand lists -- (word, shift,
+// width) or a constant -- for the probe prefix, the equality / inequality
+// checks and the output word, so the kernels only shift, mask, compare and OR
+// values held in registers.  A dropped binding row is the all-ones word (no
+// field is ever all ones, so no valid row is).
+#include "pjoin.h"
+
+namespace {
+
+LOB_DEV u64 pick(const POperand& o, u64 wi, u64 wv) {
+  if (o.word == 2) return o.cval;
+  const u64 w = o.word ? wv : wi;
+  return (w >> o.shift) & (o.width >= 64 ? ~0ull : ((1ull << o.width) - 1ull));
+}
+
+LOB_DEV u64 load_word(const void* p, int w64, u64 i) {
+  return w64 ? reinterpret_cast<const u64*>(p)[i] : (u64)reinterpret_cast<const u32*>(p)[i];
+}
+
+LOB_DEV bool checks_ok(const PCheck* c, int n, u64 wi, u64 wv) {
+  bool ok = true;
+#pragma unroll 4
+  for (int q = 0; q < n; q++) ok = ok && ((pick(c[q].a, wi, wv) == pick(c[q].b, wi, wv)) == (c[q].eq != 0));
+  return ok;
+}
+
+LOB_DEV u64 compose(const PField* f, int n, u64 wi, u64 wv) {
+  u64 o = 0;
+#pragma unroll 4
+  for (int q = 0; q < n; q++) o |= pick(f[q].op, wi, wv) << f[q].shift;
+  return o;
+}
+
+// input row r: its word, or false when the row is dropped / filtered
+template <class Sem>
+LOB_DEV bool input_row(const PStep& P, u64 r, u64& wi, typename Sem::Cand& tag) {
+  if (P.in_stamp_mode != STAMP_NONE) {
+    u32 s = P.in_stamp[r] & 0x7FFFFFFFu;
+    if (P.in_stamp_mode == STAMP_LT ? !(s < P.in_stamp_val) : s != P.in_stamp_val) return false;
+  }
+  wi = load_word(P.in_words, P.in_w64, r);
+  if (wi == (P.in_w64 ? ~0ull : 0xFFFFFFFFull)) return false;
+  if (!checks_ok(P.in_checks, P.n_in_checks, wi, 0)) return false;
+  if constexpr (Sem::kTags) {
+    if (P.in_packed) tag = Sem::from_stored(reinterpret_cast<const typename Sem::Stored*>(P.in_tags)[r]);
+    else tag = reinterpret_cast<const typename Sem::Cand*>(P.in_tags)[r];
+  } else {
+    tag = Sem::one();
+  }
+  return true;
+}
+
+LOB_DEV u64 lower_bound_w(const void* keys, int key64, u64 n, u64 x) {
+  u64 lo = 0, hi = n;
+  if (key64) {
+    const u64* a = reinterpret_cast<const u64*>(keys);
+    while (lo < hi) { const u64 m = (lo + hi) >> 1; if (a[m] < x) lo = m + 1; else hi = m; }
+  } else {
+    if (x > 0xFFFFFFFFull) return n;
+    const u32* a = reinterpret_cast<const u32*>(keys);
+    const u32 y = (u32)x;
+    while (lo < hi) { const u64 m = (lo + hi) >> 1; if (a[m] < y) lo = m + 1; else hi = m; }
+  }
+  return lo;
+}
+
+template <class Sem>
+__global__ void __launch_bounds__(256) k_pcount(const __grid_constant__ PStep P) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < P.n_in; r += stride) {
+    u64 wi;
+    typename Sem::Cand tag;
+    u64 lo = 0, hi = 0;
+    if (input_row<Sem>(P, r, wi, tag)) {
+      bool ok = true;
+      u64 pv = 0;
+#pragma unroll 4
+      for (int q = 0; q < P.n_prefix; q++) {
+        const u64 x = pick(P.prefix[q].op, wi, 0);
+        ok = ok && !(P.prefix[q].limit_bits < 64 && (x >> P.prefix[q].limit_bits));
+        pv |= x << P.prefix[q].shift;
+      }
+      if (ok) {
+        if (P.index_mode == INDEX_DENSE) {
+          lo = P.dense_offs[pv];
+          hi = P.dense_offs[pv + 1];
+        } else if (P.whole_view) {
+          lo = 0;
+          hi = P.v_n;
+        } else {
+          const u64 klo = pv << P.rest_shift;
+          const u64 khi = klo + (1ull << P.rest_shift);
+          lo = lower_bound_w(P.v_keys, P.v_key64, P.v_n, klo);
+          hi = khi < klo ? P.v_n : lower_bound_w(P.v_keys, P.v_key64, P.v_n, khi);
+        }
+      }
+    }
+    P.cnt[r] = (u32)(hi - lo);
+    P.lo32[r] = (u32)lo;
+  }
+}
+
+template <class Sem, bool kFilter>
+__global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, const u64* __restrict__ part) {
+  typedef typename Sem::Stored S;
+  typedef typename Sem::Cand C;
+  constexpr int kItems = kEmitTile / 256;
+  __shared__ __align__(16) u32 row_of[kEmitTile];
+  __shared__ u32 sm[256 / 32 + 1];
+  __shared__ u32 th_inc[256];
+  __shared__ u64 block_base;
+  const u64 j0 = P.j_begin + (u64)blockIdx.x * kEmitTile;
+  const u64 j_end = P.j_begin + P.total;
+  const u64 r0 = part[blockIdx.x];
+  const u64 r_end = part[blockIdx.x + 1];
+  for (int i = threadIdx.x; i < kEmitTile; i += 256) row_of[i] = 0;
+  __syncthreads();
+  for (u64 r = r0 + 1 + threadIdx.x; r <= r_end; r += 256) {
+    const u64 o = P.off[r];
+    if (o < j0 + kEmitTile) atomicMax(&row_of[o - j0], (u32)(r - r0));
+  }
+  __syncthreads();
+  u32 loc[kItems];
+  u32 m = 0;
+#pragma unroll
+  for (int i = 0; i < kItems; i++) {
+    const u32 x = row_of[threadIdx.x * kItems + i];
+    m = x > m ? x : m;
+    loc[i] = m;
+  }
+  const u32 inc = block_inclusive_max<u32>(m, sm);
+  th_inc[threadIdx.x] = inc;
+  __syncthreads();
+  const u32 ex = threadIdx.x ? th_inc[threadIdx.x - 1] : 0u;
+#pragma unroll
+  for (int i = 0; i < kItems; i++) row_of[threadIdx.x * kItems + i] = loc[i] > ex ? loc[i] : ex;
+  __syncthreads();
+  const u64 invalid_out = P.out_w64 ? ~0ull : 0xFFFFFFFFull;
+  u64 kept[kFilter ? kItems : 1];
+  u32 nkeep = 0;
+#pragma unroll 2
+  for (int i = 0; i < kItems; i++) {
+    const u64 j = j0 + (u64)i * 256 + threadIdx.x;
+    if (j >= j_end) break;
+    const u64 r = r0 + row_of[j - j0];
+    const u64 v = (u64)P.lo32[r] + (j - P.off[r]);
+    u64 wi;
+    C tag;
+    input_row<Sem>(P, r, wi, tag);
+    const u64 wv = load_word(P.v_keys, P.v_key64, v);
+    bool ok = P.v_stamp_mode == STAMP_NONE ||
+              (P.v_stamp_mode == STAMP_LT ? (P.v_stamp[v] & 0x7FFFFFFFu) < P.v_stamp_val
+                                          : (P.v_stamp[v] & 0x7FFFFFFFu) == P.v_stamp_val);
+    ok = ok && checks_ok(P.checks, P.n_checks, wi, wv);
+    const u64 w = ok ? compose(P.out, P.n_out, wi, wv) : invalid_out;
+    if constexpr (kFilter) {
+      if (!ok) continue;
+      const u32 bit = 1u << (u32)(w & 31u);
+      u32* word = P.bitmap + (w >> 5);
+      if (*reinterpret_cast<volatile u32*>(word) & bit) continue;  // a known fact: no atomic needed
+      if (atomicOr(word, bit) & bit) continue;
+      kept[nkeep++] = w;
+    } else {
+      const u64 o = P.out_base + (j - P.j_begin);
+      if (P.out_w64) reinterpret_cast<u64*>(P.out_words)[o] = w;
+      else reinterpret_cast<u32*>(P.out_words)[o] = (u32)w;
+      if constexpr (Sem::kTags) reinterpret_cast<C*>(P.out_tags)[o] = Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v]));
+    }
+  }
+  if constexpr (kFilter) {
+    // compact the tile's survivors in shared memory (reusing row_of), then
+    // store them with consecutive threads writing consecutive words
+    u32 tot;
+    const u32 mine = block_exclusive_sum<u32>(nkeep, sm, &tot);
+    if (threadIdx.x == 0) block_base = tot ? atomicAdd(reinterpret_cast<unsigned long long*>(P.out_count), (u64)tot) : 0ull;
+    __syncthreads();
+    const u64 base = P.out_base + block_base;
+    if (P.out_w64) {
+      u64* stage = reinterpret_cast<u64*>(row_of);  // kEmitTile u32 = kEmitTile / 2 u64 slots
+      for (u32 c0 = 0; c0 < tot; c0 += kEmitTile / 2) {
+        for (u32 q = 0; q < nkeep; q++) {
+          const u32 pos = mine + q;
+          if (pos >= c0 && pos < c0 + kEmitTile / 2) stage[pos - c0] = kept[q];
+        }
+        __syncthreads();
+        const u32 lim = min(tot - c0, (u32)(kEmitTile / 2));
+        for (u32 i = threadIdx.x; i < lim; i += 256) reinterpret_cast<u64*>(P.out_words)[base + c0 + i] = stage[i];
+        __syncthreads();
+      }
+    } else {
+      for (u32 q = 0; q < nkeep; q++) row_of[mine + q] = (u32)kept[q];
+      __syncthreads();
+      for (u32 i = threadIdx.x; i < tot; i += 256) reinterpret_cast<u32*>(P.out_words)[base + i] = row_of[i];
+    }
+  }
+}
+
+template <class Sem>
+__global__ void __launch_bounds__(256) k_pproject(const __grid_constant__ PStep P) {
+  typedef typename Sem::Cand C;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  const u64 invalid_out = P.out_w64 ? ~0ull : 0xFFFFFFFFull;
+  for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < P.n_in; r += stride) {
+    u64 wi;
+    C tag = Sem::one();
+    const bool ok = input_row<Sem>(P, r, wi, tag);
+    const u64 w = ok ? compose(P.out, P.n_out, wi, 0) : invalid_out;
+    const u64 o = P.out_base + r;
+    if (P.out_w64) reinterpret_cast<u64*>(P.out_words)[o] = w;
+    else reinterpret_cast<u32*>(P.out_words)[o] = (u32)w;
+    if constexpr (Sem::kTags) reinterpret_cast<C*>(P.out_tags)[o] = tag;
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Specialised emission: the numbers of output fields (NOUT) and of checks
+// (NCHK) are compile-time, so operand descriptors live in registers and every
+// field costs a select, two shifts, a mask and an OR.  Each thread's outputs are
+// processed in phases -- all row lookups, then all row-offset / match-start /
+// input-word loads, then all matched-key loads, then the arithmetic -- so a
+// thread keeps many independent loads in flight instead of one dependent chain.
+// ---------------------------------------------------------------------------
+struct RegOp {
+  u64 mask;
+  u32 cval;
+  uint8_t shift, word;
+};
+
+LOB_DEV RegOp reg_op(const POperand& o) {
+  RegOp r;
+  r.mask = o.width >= 64 ? ~0ull : ((1ull << o.width) - 1ull);
+  r.shift = o.shift;
+  r.word = o.word;
+  r.cval = o.cval;
+  return r;
+}
+LOB_DEV u64 reg_pick(const RegOp& o, u64 wi, u64 wv) {
+  return o.word == 2 ? (u64)o.cval : (((o.word ? wv : wi) >> o.shift) & o.mask);
+}
+
+template <class Sem, bool kFilter, int NOUT, int NCHK>
+__global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PStep P, const u64* __restrict__ part) {
+  typedef typename Sem::Stored S;
+  typedef typename Sem::Cand C;
+  constexpr int kItems = kEmitTile / 256;
+  __shared__ __align__(16) u32 row_of[kEmitTile];
+  __shared__ u32 sm[256 / 32 + 1];
+  __shared__ u32 th_inc[256];
+  __shared__ u64 block_base;
+  const u64 j0 = P.j_begin + (u64)blockIdx.x * kEmitTile;
+  const u64 j_end = P.j_begin + P.total;
+  const u64 r0 = part[blockIdx.x];
+  const u64 r_end = part[blockIdx.x + 1];
+  for (int i = threadIdx.x; i < kEmitTile; i += 256) row_of[i] = 0;
+  __syncthreads();
+  for (u64 r = r0 + 1 + threadIdx.x; r <= r_end; r += 256) {
+    const u64 o = P.off[r];
+    if (o < j0 + kEmitTile) atomicMax(&row_of[o - j0], (u32)(r - r0));
+  }
+  __syncthreads();
+  {
+    u32 loc[kItems];
+    u32 m = 0;
+#pragma unroll
+    for (int i = 0; i < kItems; i++) {
+      const u32 x = row_of[threadIdx.x * kItems + i];
+      m = x > m ? x : m;
+      loc[i] = m;
+    }
+    const u32 inc = block_inclusive_max<u32>(m, sm);
+    th_inc[threadIdx.x] = inc;
+    __syncthreads();
+    const u32 ex = threadIdx.x ? th_inc[threadIdx.x - 1] : 0u;
+#pragma unroll
+    for (int i = 0; i < kItems; i++) row_of[threadIdx.x * kItems + i] = loc[i] > ex ? loc[i] : ex;
+  }
+  __syncthreads();
+  RegOp out_op[NOUT];
+  u32 out_sh[NOUT];
+#pragma unroll
+  for (int q = 0; q < NOUT; q++) {
+    out_op[q] = reg_op(P.out[q].op);
+    out_sh[q] = P.out[q].shift;
+  }
+  RegOp ca[NCHK > 0 ? NCHK : 1], cb[NCHK > 0 ? NCHK : 1];
+  bool ceq[NCHK > 0 ? NCHK : 1];
+#pragma unroll
+  for (int q = 0; q < NCHK; q++) {
+    ca[q] = reg_op(P.checks[q].a);
+    cb[q] = reg_op(P.checks[q].b);
+    ceq[q] = P.checks[q].eq != 0;
+  }
+  const u64 invalid_out = P.out_w64 ? ~0ull : 0xFFFFFFFFull;
+  const u64 invalid_in = P.in_w64 ? ~0ull : 0xFFFFFFFFull;
+  u64 kept[kFilter ? kItems : 1];
+  u32 nkeep = 0;
+  constexpr int B = 2;  // outputs whose loads are issued together (keeps registers, and occupancy, up)
+#pragma unroll 1
+  for (int i0 = 0; i0 < kItems; i0 += B) {
+    u32 rr[B];
+    u64 offv[B], wi[B], wv[B];
+    u32 lov[B];
+#pragma unroll
+    for (int b = 0; b < B; b++) {
+      const u64 j = j0 + (u64)(i0 + b) * 256 + threadIdx.x;
+      rr[b] = j < j_end ? row_of[j - j0] : 0u;
+    }
+#pragma unroll
+    for (int b = 0; b < B; b++) {
+      const u64 r = r0 + rr[b];
+      offv[b] = P.off[r];
+      lov[b] = P.lo32[r];
+      wi[b] = load_word(P.in_words, P.in_w64, r);
+    }
+#pragma unroll
+    for (int b = 0; b < B; b++) {
+      const u64 j = j0 + (u64)(i0 + b) * 256 + threadIdx.x;
+      wv[b] = j < j_end ? load_word(P.v_keys, P.v_key64, (u64)lov[b] + (j - offv[b])) : 0ull;
+    }
+#pragma unroll
+    for (int b = 0; b < B; b++) {
+      const u64 j = j0 + (u64)(i0 + b) * 256 + threadIdx.x;
+      if (j >= j_end) continue;
+      bool ok = wi[b] != invalid_in;
+      if (P.n_in_checks) ok = ok && checks_ok(P.in_checks, P.n_in_checks, wi[b], 0);
+      const u64 v = (u64)lov[b] + (j - offv[b]);
+      if (P.v_stamp_mode != STAMP_NONE) {
+        const u32 st = P.v_stamp[v] & 0x7FFFFFFFu;
+        ok = ok && (P.v_stamp_mode == STAMP_LT ? st < P.v_stamp_val : st == P.v_stamp_val);
+      }
+#pragma unroll
+      for (int q = 0; q < NCHK; q++) ok = ok && ((reg_pick(ca[q], wi[b], wv[b]) == reg_pick(cb[q], wi[b], wv[b])) == ceq[q]);
+      u64 w = 0;
+#pragma unroll
+      for (int q = 0; q < NOUT; q++) w |= reg_pick(out_op[q], wi[b], wv[b]) << out_sh[q];
+      if constexpr (kFilter) {
+        if (!ok) continue;
+        const u32 bit = 1u << (u32)(w & 31u);
+        u32* word = P.bitmap + (w >> 5);
+        if (*reinterpret_cast<volatile u32*>(word) & bit) continue;
+        if (atomicOr(word, bit) & bit) continue;
+        kept[nkeep++] = w;
+      } else {
+        const u64 o = P.out_base + (j - P.j_begin);
+        if (!ok) w = invalid_out;
+        if (P.out_w64) reinterpret_cast<u64*>(P.out_words)[o] = w;
+        else reinterpret_cast<u32*>(P.out_words)[o] = (u32)w;
+        if constexpr (Sem::kTags) {
+          const u64 r = r0 + rr[b];
+          C tag = P.in_packed ? Sem::from_stored(reinterpret_cast<const S*>(P.in_tags)[r])
+                              : reinterpret_cast<const C*>(P.in_tags)[r];
+          reinterpret_cast<C*>(P.out_tags)[o] = Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v]));
+        }
+      }
+    }
+  }
+  if constexpr (kFilter) {
+    u32 tot;
+    const u32 mine = block_exclusive_sum<u32>(nkeep, sm, &tot);
+    if (threadIdx.x == 0) block_base = tot ? atomicAdd(reinterpret_cast<unsigned long long*>(P.out_count), (u64)tot) : 0ull;
+    __syncthreads();
+    const u64 base = P.out_base + block_base;
+    if (P.out_w64) {
+      u64* stage = reinterpret_cast<u64*>(row_of);
+      for (u32 c0 = 0; c0 < tot; c0 += kEmitTile / 2) {
+        for (u32 q = 0; q < nkeep; q++) {
+          const u32 pos = mine + q;
+          if (pos >= c0 && pos < c0 + kEmitTile / 2) stage[pos - c0] = kept[q];
+        }
+        __syncthreads();
+        const u32 lim = min(tot - c0, (u32)(kEmitTile / 2));
+        for (u32 i = threadIdx.x; i < lim; i += 256) reinterpret_cast<u64*>(P.out_words)[base + c0 + i] = stage[i];
+        __syncthreads();
+      }
+    } else {
+      for (u32 q = 0; q < nkeep; q++) row_of[mine + q] = (u32)kept[q];
+      __syncthreads();
+      for (u32 i = threadIdx.x; i < tot; i += 256) reinterpret_cast<u32*>(P.out_words)[base + i] = row_of[i];
+    }
+  }
+}
+
+// count with a compile-time number of prefix fields
+template <class Sem, int NPRE>
+__global__ void __launch_bounds__(256) k_pcount_fast(const __grid_constant__ PStep P) {
+  RegOp pre[NPRE];
+  u32 psh[NPRE];
+  u32 plim[NPRE];
+#pragma unroll
+  for (int q = 0; q < NPRE; q++) {
+    pre[q] = reg_op(P.prefix[q].op);
+    psh[q] = P.prefix[q].shift;
+    plim[q] = P.prefix[q].limit_bits;
+  }
+  const u64 invalid_in = P.in_w64 ? ~0ull : 0xFFFFFFFFull;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < P.n_in; r += stride) {
+    const u64 wi = load_word(P.in_words, P.in_w64, r);
+    bool ok = wi != invalid_in;
+    if (P.in_stamp_mode != STAMP_NONE) {
+      const u32 st = P.in_stamp[r] & 0x7FFFFFFFu;
+      ok = ok && (P.in_stamp_mode == STAMP_LT ? st < P.in_stamp_val : st == P.in_stamp_val);
+    }
+    if (P.n_in_checks) ok = ok && checks_ok(P.in_checks, P.n_in_checks, wi, 0);
+    u64 pv = 0;
+#pragma unroll
+    for (int q = 0; q < NPRE; q++) {
+      const u64 x = reg_pick(pre[q], wi, 0);
+      ok = ok && !(plim[q] < 64 && (x >> plim[q]));
+      pv |= x << psh[q];
+    }
+    u64 lo = 0, hi = 0;
+    if (ok) {
+      lo = P.dense_offs[pv];
+      hi = P.dense_offs[pv + 1];
+    }
+    P.cnt[r] = (u32)(hi - lo);
+    P.lo32[r] = (u32)lo;
+  }
+}
+
+unsigned grid_n(u64 n) {
+  u64 b = (n + 255) / 256;
+  if (b > 152ull * 16) b = 152ull * 16;
+  return (unsigned)(b ? b : 1);
+}
+
+double row_bytes(int sem, int w64, bool packed_in) {
+  const double t = sem == SR_UNIT ? 0 : (packed_in ? (sem == SR_DIFF_MAX_MIN ? 8 : 4) : (sem == SR_MAX_MIN ? 4 : 8));
+  return (w64 ? 8 : 4) + t;
+}
+
+template <template <class> class L, class... A>
+void by_sem_p(int sem, A&&... a) {
+  switch (sem) {
+    case SR_UNIT: L<SemUnit>::go(a...); break;
+    case SR_MAX_MIN: L<SemMaxMin>::go(a...); break;
+    case SR_DIFF_MAX_MIN: L<SemDiffMaxMin>::go(a...); break;
+    default: L<SemAddMult>::go(a...); break;
+  }
+}
+template <class Sem> struct PCountL {
+  static void go(const PStep& P, cudaStream_t st) {
+    const unsigned g = grid_n(P.n_in);
+    if (P.index_mode == INDEX_DENSE && P.n_prefix == 1) k_pcount_fast<Sem, 1><<<g, 256, 0, st>>>(P);
+    else if (P.index_mode == INDEX_DENSE && P.n_prefix == 2) k_pcount_fast<Sem, 2><<<g, 256, 0, st>>>(P);
+    else if (P.index_mode == INDEX_DENSE && P.n_prefix == 3) k_pcount_fast<Sem, 3><<<g, 256, 0, st>>>(P);
+    else k_pcount<Sem><<<g, 256, 0, st>>>(P);
+  }
+};
+template <class Sem, bool F, int NO, int NC>
+void launch_fast(const PStep& P, const u64* part, unsigned tiles, cudaStream_t st) {
+  k_pemit_fast<Sem, F, NO, NC><<<tiles, 256, 0, st>>>(P, part);
+}
+template <class Sem, bool F>
+bool try_fast(const PStep& P, const u64* part, unsigned tiles, cudaStream_t st) {
+  const int no = P.n_out, nc = P.n_checks;
+#define LOB_FAST(NO, NC) if (no == NO && nc == NC) { launch_fast<Sem, F, NO, NC>(P, part, tiles, st); return true; }
+  LOB_FAST(1, 0) LOB_FAST(2, 0) LOB_FAST(3, 0) LOB_FAST(4, 0)
+  LOB_FAST(1, 1) LOB_FAST(2, 1) LOB_FAST(3, 1) LOB_FAST(4, 1)
+#undef LOB_FAST
+  return false;
+}
+template <class Sem> struct PEmitL {
+  static void go(const PStep& P, const u64* part, cudaStream_t st) {
+    const u64 tiles = (P.total + kEmitTile - 1) / kEmitTile;
+    if (std::is_same<Sem, SemUnit>::value && P.bitmap) {
+      if (!try_fast<SemUnit, true>(P, part, (unsigned)tiles, st))
+        k_pemit<SemUnit, true><<<(unsigned)tiles, 256, 0, st>>>(P, part);
+    } else if (!try_fast<Sem, false>(P, part, (unsigned)tiles, st)) {
+      k_pemit<Sem, false><<<(unsigned)tiles, 256, 0, st>>>(P, part);
+    }
+  }
+};
+template <class Sem> struct PProjL {
+  static void go(const PStep& P, cudaStream_t st) { k_pproject<Sem><<<grid_n(P.n_in), 256, 0, st>>>(P); }
+};
+
+}  // namespace
+
+void pjoin_count(int sem, const PStep& P, cudaStream_t st) {
+  ProfScope ps("join_count", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + 16.0 + 12.0), st);
+  if (P.n_in) by_sem_p<PCountL>(sem, P, st);
+}
+
+void pjoin_emit(int sem, const PStep& P, const u64* part, cudaStream_t st) {
+  const double vb = (P.v_key64 ? 8 : 4) + (sem == SR_UNIT ? 0 : (sem == SR_DIFF_MAX_MIN ? 8 : 4));
+  ProfScope ps("join_emit", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + 16.0) +
+                                P.total * (vb + row_bytes(sem, P.out_w64, false)), st);
+  if (P.total) by_sem_p<PEmitL>(sem, P, part, st);
+}
+
+void pjoin_project(int sem, const PStep& P, cudaStream_t st) {
+  ProfScope ps("project", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + row_bytes(sem, P.out_w64, false)), st);
+  if (P.n_in) by_sem_p<PProjL>(sem, P, st);
+}

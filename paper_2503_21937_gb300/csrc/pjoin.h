@@ -1,0 +1,49 @@
+// Packed join steps (pjoin.cu): rule variables as bit fields of packed words.
+#pragma once
+#include "kernels.h"
+
+struct POperand {
+  uint8_t word;   // 0: input word, 1: matched view key, 2: constant
+  uint8_t shift;
+  uint8_t width;
+  uint8_t pad;
+  u32 cval;
+};
+struct PField {   // operand placed at `shift` of a composed word
+  POperand op;
+  uint8_t shift;
+  uint8_t limit_bits;  // probe prefix: the value must fit this many bits (64: no limit)
+};
+struct PCheck {
+  POperand a, b;
+  int8_t eq;
+};
+
+constexpr int kMaxPChecks = 16;
+constexpr int kMaxPFields = kMaxArity + 1;
+
+struct PStep {
+  // input rows: packed relation keys (in_packed, tags are stored tags) or
+  // packed binding words (tags are candidate tags)
+  int in_packed;
+  const void* in_words; int in_w64; const void* in_tags;
+  const u32* in_stamp; int in_stamp_mode; u32 in_stamp_val;
+  u64 n_in;
+  int n_in_checks; PCheck in_checks[kMaxPChecks];
+  // probe
+  const void* v_keys; int v_key64; const void* v_tags; const u32* v_stamp; u64 v_n;
+  int v_stamp_mode; u32 v_stamp_val;
+  int n_prefix; PField prefix[kMaxPFields];
+  int index_mode; const u64* dense_offs; int rest_shift; int whole_view;
+  int n_checks; PCheck checks[kMaxPChecks];
+  // output word: a head key or a binding word
+  void* out_words; int out_w64; void* out_tags; u64 out_base;
+  int n_out; PField out[kMaxPFields];
+  // count / scan / emission range / membership filter
+  u32* cnt; u32* lo32; const u64* off; u64 total; u64 j_begin;  // view rows < 2^32
+  u32* bitmap; u64* out_count;
+};
+
+void pjoin_count(int sem, const PStep& P, cudaStream_t st);
+void pjoin_emit(int sem, const PStep& P, const u64* part, cudaStream_t st);
+void pjoin_project(int sem, const PStep& P, cudaStream_t st);
