@@ -254,11 +254,22 @@ def batched_fwd_bwd(n_samples=512, loop_samples=32, reps=3):
 # ---------------------------------------------------------------------------
 # small cases for ncu captures (a few GB on the device at most)
 # ---------------------------------------------------------------------------
-def profile_case(name):
+def parse_options(pairs):
+    """--option KEY=VALUE strings as (key, int value) pairs."""
+    out = []
+    for kv in pairs:
+        k, v = kv.split("=")
+        out.append((k, int(v)))
+    return out
+
+
+def profile_case(name, options=()):
     import torch
     from paper_2503_21937_gb300 import Engine, build
     build.build()
     e = Engine()
+    for k, v in options:
+        e.set_option(k, v)
     if name == "sort_u32_2e26":  # one sort of 2^26 random 30-bit keys (4 LSD passes)
         keys = W.stream(7001).below(1 << 26, 1 << 30)
         k = torch.from_numpy(keys.view(np.int32)).cuda()
@@ -298,7 +309,7 @@ def main():
                     help="run one small case once (for ncu captures) and exit")
     args = ap.parse_args()
     if args.profile_case:
-        return profile_case(args.profile_case)
+        return profile_case(args.profile_case, parse_options(args.option))
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return reference_arm(args)
@@ -323,9 +334,8 @@ def main():
         for name, (prog, rels) in inputs.items():
             e = Engine(stream=stream.cuda_stream)
             e.program(prog)
-            for kv in args.option:
-                k, v = kv.split("=")
-                e.set_option(k, int(v))
+            for k, v in parse_options(args.option):
+                e.set_option(k, v)
             engines[name] = e
     heads = {"sg": "sg", "tc": "path"}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
@@ -373,10 +383,13 @@ def main():
 
     # per-kernel CUDA-event timing on extra steps (not part of the timed value)
     prof = {}
+    by_workload = {}
     with torch.cuda.stream(stream):
         for _ in range(args.profile_steps):
             step(profile=True)
-    for e in engines.values():
+    for wname, e in engines.items():
+        by_workload[wname] = {k: round(v["ms"], 3) for k, v in sorted(e.profile().items(), key=lambda kv: -kv[1]["ms"])
+                              if v["ms"] >= 0.05}
         for k, v in e.profile().items():
             p = prof.setdefault(k, {"launches": 0, "ms": 0.0, "bytes": 0.0})
             for f in p:
@@ -447,7 +460,7 @@ def main():
                            "derived_per_step": derived[0], "iterations": iters,
                            "engine_options": args.option},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "kernels": kernels, "batched": batched}
+                "clocks": clk, "kernels": kernels, "kernels_by_workload": by_workload, "batched": batched}
         print(json.dumps(line))
     for e in engines.values():
         e.close()

@@ -1063,24 +1063,32 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
     const IndexSt& I = W.index[S.prefix_len];
     P.index_mode = I.mode;
     P.dense_offs = I.offs.as<u64>();
+    const u64 n_blk = pjoin_loc_blocks(n_in);
     e.ensure(e.cnt, n_in * 4);
-    e.ensure(e.lo, n_in * 8);
-    e.ensure(e.off, (n_in + 1) * 8);
-    P.cnt = e.cnt.as<u32>();
+    e.ensure(e.lo, n_in * 4);
+    e.ensure(e.off, n_blk * 16);
+    P.loc = e.cnt.as<u32>();
     P.lo32 = e.lo.as<u32>();
+    P.blk_cnt = e.off.as<u64>() + n_blk;
+    P.blk_off = e.off.as<u64>();
+    P.err = reinterpret_cast<u32*>(e.counts.as<u64>() + 1);
     if (W.n > 0xFFFFFFFFull) throw LobError(LOB_E_ARG, "packed join needs views below 2^32 rows");
+    e.check(cudaMemsetAsync(P.err, 0, sizeof(u64), e.stream), "join error word");
     pjoin_count(sem, P, e.stream);
     e.after_launch("join count");
-    scratch_at_least(e, scan_scratch_elems(n_in) * 8 + 64);
+    scratch_at_least(e, scan_scratch_elems(n_blk) * 8 + 64);
     {
-      ProfScope ps("join_scan", n_in * 12.0, e.stream);
-      exclusive_scan<u32, u64>(e.cnt.as<u32>(), e.off.as<u64>(), n_in, e.counts.as<u64>(), e.scratch.as<u64>(), e.stream);
+      ProfScope ps("join_scan", n_blk * 16.0, e.stream);
+      exclusive_scan<u64, u64>(P.blk_cnt, e.off.as<u64>(), n_blk, e.counts.as<u64>(), e.scratch.as<u64>(), e.stream);
     }
     e.after_launch("join scan");
-    e.launches += 1 + scan_launches(n_in);
-    const u64 total = e.read_u64(e.counts.as<u64>());
+    e.launches += 1 + scan_launches(n_blk);
+    e.check(cudaMemcpyAsync(e.pinned, e.counts.as<u64>(), 16, cudaMemcpyDeviceToHost, e.stream), "join total");
+    e.sync();
+    if (e.pinned[1] & kErrLocOverflow)
+      throw LobError(LOB_E_ARG, "join step: 1024 consecutive input rows have 2^32 or more matches");
+    const u64 total = e.pinned[0];
     if (!total) return;
-    P.off = e.off.as<u64>();
     if (last) {  // candidates, in sub-ranges of at most opt_max_cand outputs
       for (u64 jb = 0; jb < total; jb += e.opt_max_cand) {
         const u64 sub = std::min(e.opt_max_cand, total - jb);
@@ -1091,9 +1099,9 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
         P.out_base = H.n_cand;
         const u64 nt = (sub + kEmitTile - 1) / kEmitTile;
         e.ensure(e.part, (nt + 1) * 8);
-        lbs_partition(e.off.as<u64>(), n_in, jb, sub, e.part.as<u64>(), e.stream);
         P.total = sub;
         P.j_begin = jb;
+        pjoin_partition(P, nt, e.part.as<u64>(), e.stream);
         P.bitmap = nullptr;
         P.out_count = nullptr;
         if (H.filter_on) {
@@ -1120,9 +1128,9 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
     P.out_base = 0;
     const u64 ntiles = (total + kEmitTile - 1) / kEmitTile;
     e.ensure(e.part, (ntiles + 1) * 8);
-    lbs_partition(e.off.as<u64>(), n_in, 0, total, e.part.as<u64>(), e.stream);
     P.total = total;
     P.j_begin = 0;
+    pjoin_partition(P, ntiles, e.part.as<u64>(), e.stream);
     pjoin_emit(sem, P, e.part.as<u64>(), e.stream);
     e.after_launch("join emit");
     e.launches += 2;

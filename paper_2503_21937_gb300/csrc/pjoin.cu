@@ -69,41 +69,7 @@ LOB_DEV u64 lower_bound_w(const void* keys, int key64, u64 n, u64 x) {
   return lo;
 }
 
-template <class Sem>
-__global__ void __launch_bounds__(256) k_pcount(const __grid_constant__ PStep P) {
-  const u64 stride = (u64)gridDim.x * blockDim.x;
-  for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < P.n_in; r += stride) {
-    u64 wi;
-    typename Sem::Cand tag;
-    u64 lo = 0, hi = 0;
-    if (input_row<Sem>(P, r, wi, tag)) {
-      bool ok = true;
-      u64 pv = 0;
-#pragma unroll 4
-      for (int q = 0; q < P.n_prefix; q++) {
-        const u64 x = pick(P.prefix[q].op, wi, 0);
-        ok = ok && !(P.prefix[q].limit_bits < 64 && (x >> P.prefix[q].limit_bits));
-        pv |= x << P.prefix[q].shift;
-      }
-      if (ok) {
-        if (P.index_mode == INDEX_DENSE) {
-          lo = P.dense_offs[pv];
-          hi = P.dense_offs[pv + 1];
-        } else if (P.whole_view) {
-          lo = 0;
-          hi = P.v_n;
-        } else {
-          const u64 klo = pv << P.rest_shift;
-          const u64 khi = klo + (1ull << P.rest_shift);
-          lo = lower_bound_w(P.v_keys, P.v_key64, P.v_n, klo);
-          hi = khi < klo ? P.v_n : lower_bound_w(P.v_keys, P.v_key64, P.v_n, khi);
-        }
-      }
-    }
-    P.cnt[r] = (u32)(hi - lo);
-    P.lo32[r] = (u32)lo;
-  }
-}
+LOB_DEV u64 row_off(const PStep& P, u64 r) { return P.blk_off[r / kLocRows] + P.loc[r]; }
 
 template <class Sem, bool kFilter>
 __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, const u64* __restrict__ part) {
@@ -121,7 +87,7 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
   for (int i = threadIdx.x; i < kEmitTile; i += 256) row_of[i] = 0;
   __syncthreads();
   for (u64 r = r0 + 1 + threadIdx.x; r <= r_end; r += 256) {
-    const u64 o = P.off[r];
+    const u64 o = row_off(P, r);
     if (o < j0 + kEmitTile) atomicMax(&row_of[o - j0], (u32)(r - r0));
   }
   __syncthreads();
@@ -148,7 +114,7 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
     const u64 j = j0 + (u64)i * 256 + threadIdx.x;
     if (j >= j_end) break;
     const u64 r = r0 + row_of[j - j0];
-    const u64 v = (u64)P.lo32[r] + (j - P.off[r]);
+    const u64 v = (u64)P.lo32[r] + (j - row_off(P, r));
     u64 wi;
     C tag;
     input_row<Sem>(P, r, wi, tag);
@@ -260,7 +226,7 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
   for (int i = threadIdx.x; i < kEmitTile; i += 256) row_of[i] = 0;
   __syncthreads();
   for (u64 r = r0 + 1 + threadIdx.x; r <= r_end; r += 256) {
-    const u64 o = P.off[r];
+    const u64 o = row_off(P, r);
     if (o < j0 + kEmitTile) atomicMax(&row_of[o - j0], (u32)(r - r0));
   }
   __syncthreads();
@@ -314,7 +280,7 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
 #pragma unroll
     for (int b = 0; b < B; b++) {
       const u64 r = r0 + rr[b];
-      offv[b] = P.off[r];
+      offv[b] = row_off(P, r);
       lov[b] = P.lo32[r];
       wi[b] = load_word(P.in_words, P.in_w64, r);
     }
@@ -386,12 +352,18 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
   }
 }
 
-// count with a compile-time number of prefix fields
-template <class Sem, int NPRE>
-__global__ void __launch_bounds__(256) k_pcount_fast(const __grid_constant__ PStep P) {
-  RegOp pre[NPRE];
-  u32 psh[NPRE];
-  u32 plim[NPRE];
+// Count: the matches of every input row in the probed view (lo32: first matched
+// view row) and the row's output offset within its block of kLocRows rows
+// (loc), plus one total per block (blk_cnt).  Each thread takes four
+// consecutive rows, so the block's local offsets come from one block scan and
+// no pass over per-row counts is needed afterwards.  NPRE > 0: dense index
+// probed with NPRE prefix fields held in registers; NPRE == 0: any index.
+template <int NPRE>
+__global__ void __launch_bounds__(256) k_pcount_loc(const __grid_constant__ PStep P, u64 n_blk) {
+  __shared__ u64 sm64[256 / 32 + 1];
+  constexpr int NP = NPRE > 0 ? NPRE : 1;
+  RegOp pre[NP];
+  u32 psh[NP], plim[NP];
 #pragma unroll
   for (int q = 0; q < NPRE; q++) {
     pre[q] = reg_op(P.prefix[q].op);
@@ -399,30 +371,110 @@ __global__ void __launch_bounds__(256) k_pcount_fast(const __grid_constant__ PSt
     plim[q] = P.prefix[q].limit_bits;
   }
   const u64 invalid_in = P.in_w64 ? ~0ull : 0xFFFFFFFFull;
-  const u64 stride = (u64)gridDim.x * blockDim.x;
-  for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < P.n_in; r += stride) {
-    const u64 wi = load_word(P.in_words, P.in_w64, r);
-    bool ok = wi != invalid_in;
-    if (P.in_stamp_mode != STAMP_NONE) {
-      const u32 st = P.in_stamp[r] & 0x7FFFFFFFu;
-      ok = ok && (P.in_stamp_mode == STAMP_LT ? st < P.in_stamp_val : st == P.in_stamp_val);
-    }
-    if (P.n_in_checks) ok = ok && checks_ok(P.in_checks, P.n_in_checks, wi, 0);
-    u64 pv = 0;
+  const bool vec_in = (reinterpret_cast<uintptr_t>(P.in_words) & 15) == 0;
+  for (u64 b = blockIdx.x; b < n_blk; b += gridDim.x) {
+    const u64 r0 = b * kLocRows + (u64)threadIdx.x * 4;
+    const bool full = r0 + 4 <= P.n_in;
+    u64 w[4];
+    if (full && vec_in) {
+      if (P.in_w64) {
+        const ulonglong2 x = reinterpret_cast<const ulonglong2*>(P.in_words)[r0 / 2];
+        const ulonglong2 y = reinterpret_cast<const ulonglong2*>(P.in_words)[r0 / 2 + 1];
+        w[0] = x.x; w[1] = x.y; w[2] = y.x; w[3] = y.y;
+      } else {
+        const uint4 x = reinterpret_cast<const uint4*>(P.in_words)[r0 / 4];
+        w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+      }
+    } else {
 #pragma unroll
-    for (int q = 0; q < NPRE; q++) {
-      const u64 x = reg_pick(pre[q], wi, 0);
-      ok = ok && !(plim[q] < 64 && (x >> plim[q]));
-      pv |= x << psh[q];
+      for (int i = 0; i < 4; i++) w[i] = r0 + i < P.n_in ? load_word(P.in_words, P.in_w64, r0 + i) : invalid_in;
     }
-    u64 lo = 0, hi = 0;
-    if (ok) {
-      lo = P.dense_offs[pv];
-      hi = P.dense_offs[pv + 1];
+    u32 c[4], lo[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      c[i] = 0;
+      lo[i] = 0;
+      bool ok = w[i] != invalid_in;
+      if (ok && P.in_stamp_mode != STAMP_NONE) {
+        const u32 st = P.in_stamp[r0 + i] & 0x7FFFFFFFu;
+        ok = P.in_stamp_mode == STAMP_LT ? st < P.in_stamp_val : st == P.in_stamp_val;
+      }
+      if (ok && P.n_in_checks) ok = checks_ok(P.in_checks, P.n_in_checks, w[i], 0);
+      u64 pv = 0;
+      if constexpr (NPRE > 0) {
+#pragma unroll
+        for (int q = 0; q < NPRE; q++) {
+          const u64 x = reg_pick(pre[q], w[i], 0);
+          ok = ok && !(plim[q] < 64 && (x >> plim[q]));
+          pv |= x << psh[q];
+        }
+        if (ok) {
+          const u64 l = P.dense_offs[pv];
+          c[i] = (u32)(P.dense_offs[pv + 1] - l);
+          lo[i] = (u32)l;
+        }
+      } else {
+        for (int q = 0; q < P.n_prefix; q++) {
+          const u64 x = pick(P.prefix[q].op, w[i], 0);
+          ok = ok && !(P.prefix[q].limit_bits < 64 && (x >> P.prefix[q].limit_bits));
+          pv |= x << P.prefix[q].shift;
+        }
+        if (ok) {
+          u64 l, h;
+          if (P.index_mode == INDEX_DENSE) {
+            l = P.dense_offs[pv];
+            h = P.dense_offs[pv + 1];
+          } else if (P.whole_view) {
+            l = 0;
+            h = P.v_n;
+          } else {
+            const u64 klo = pv << P.rest_shift;
+            const u64 khi = klo + (1ull << P.rest_shift);
+            l = lower_bound_w(P.v_keys, P.v_key64, P.v_n, klo);
+            h = khi < klo ? P.v_n : lower_bound_w(P.v_keys, P.v_key64, P.v_n, khi);
+          }
+          c[i] = (u32)(h - l);
+          lo[i] = (u32)l;
+        }
+      }
     }
-    P.cnt[r] = (u32)(hi - lo);
-    P.lo32[r] = (u32)lo;
+    u64 tot;
+    const u64 ex = block_exclusive_sum<u64>((u64)c[0] + c[1] + c[2] + c[3], sm64, &tot);
+    u32 lc[4];
+    u32 run = (u32)ex;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      lc[i] = run;
+      run += c[i];
+    }
+    if (full) {
+      reinterpret_cast<uint4*>(P.loc)[r0 / 4] = make_uint4(lc[0], lc[1], lc[2], lc[3]);
+      reinterpret_cast<uint4*>(P.lo32)[r0 / 4] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        if (r0 + i < P.n_in) {
+          P.loc[r0 + i] = lc[i];
+          P.lo32[r0 + i] = lo[i];
+        }
+    }
+    if (threadIdx.x == 0) {
+      P.blk_cnt[b] = tot;
+      if (tot >> 32) atomicOr(P.err, kErrLocOverflow);
+    }
   }
+}
+
+// partition of outputs [j_begin, j_begin + total) into tiles of kEmitTile:
+// part[t] = the last row whose first output is at or before the tile's start
+__global__ void k_ppartition(const __grid_constant__ PStep P, u64 n_blk, u64 ntiles, u64* __restrict__ part) {
+  const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > ntiles) return;
+  const u64 j = t == ntiles ? P.j_begin + P.total - 1 : P.j_begin + t * (u64)kEmitTile;
+  const u64 b = upper_bound_dev<u64>(P.blk_off, 0, n_blk, j) - 1;
+  const u64 lo = b * kLocRows;
+  const u64 hi = lo + kLocRows < P.n_in ? lo + kLocRows : P.n_in;
+  part[t] = upper_bound_dev<u32>(P.loc, lo, hi, (u32)(j - P.blk_off[b])) - 1;
 }
 
 unsigned grid_n(u64 n) {
@@ -445,15 +497,6 @@ void by_sem_p(int sem, A&&... a) {
     default: L<SemAddMult>::go(a...); break;
   }
 }
-template <class Sem> struct PCountL {
-  static void go(const PStep& P, cudaStream_t st) {
-    const unsigned g = grid_n(P.n_in);
-    if (P.index_mode == INDEX_DENSE && P.n_prefix == 1) k_pcount_fast<Sem, 1><<<g, 256, 0, st>>>(P);
-    else if (P.index_mode == INDEX_DENSE && P.n_prefix == 2) k_pcount_fast<Sem, 2><<<g, 256, 0, st>>>(P);
-    else if (P.index_mode == INDEX_DENSE && P.n_prefix == 3) k_pcount_fast<Sem, 3><<<g, 256, 0, st>>>(P);
-    else k_pcount<Sem><<<g, 256, 0, st>>>(P);
-  }
-};
 template <class Sem, bool F, int NO, int NC>
 void launch_fast(const PStep& P, const u64* part, unsigned tiles, cudaStream_t st) {
   k_pemit_fast<Sem, F, NO, NC><<<tiles, 256, 0, st>>>(P, part);
@@ -485,8 +528,19 @@ template <class Sem> struct PProjL {
 }  // namespace
 
 void pjoin_count(int sem, const PStep& P, cudaStream_t st) {
-  ProfScope ps("join_count", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + 16.0 + 12.0), st);
-  if (P.n_in) by_sem_p<PCountL>(sem, P, st);
+  const u64 n_blk = pjoin_loc_blocks(P.n_in);
+  ProfScope ps("join_count", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + 16.0 + 8.0) + n_blk * 8.0, st);
+  if (!P.n_in) return;
+  const unsigned g = (unsigned)(n_blk < 152ull * 64 ? n_blk : 152ull * 64);
+  if (P.index_mode == INDEX_DENSE && P.n_prefix == 1) k_pcount_loc<1><<<g, 256, 0, st>>>(P, n_blk);
+  else if (P.index_mode == INDEX_DENSE && P.n_prefix == 2) k_pcount_loc<2><<<g, 256, 0, st>>>(P, n_blk);
+  else if (P.index_mode == INDEX_DENSE && P.n_prefix == 3) k_pcount_loc<3><<<g, 256, 0, st>>>(P, n_blk);
+  else k_pcount_loc<0><<<g, 256, 0, st>>>(P, n_blk);
+}
+
+void pjoin_partition(const PStep& P, u64 ntiles, u64* part, cudaStream_t st) {
+  ProfScope ps("join_partition", (ntiles + 1) * 8.0, st);
+  k_ppartition<<<(unsigned)((ntiles + 1 + 255) / 256), 256, 0, st>>>(P, pjoin_loc_blocks(P.n_in), ntiles, part);
 }
 
 void pjoin_emit(int sem, const PStep& P, const u64* part, cudaStream_t st) {

@@ -39,11 +39,21 @@ struct PStep {
   // output word: a head key or a binding word
   void* out_words; int out_w64; void* out_tags; u64 out_base;
   int n_out; PField out[kMaxPFields];
-  // count / scan / emission range / membership filter
-  u32* cnt; u32* lo32; const u64* off; u64 total; u64 j_begin;  // view rows < 2^32
+  // count / offsets / emission range / membership filter.  Row r's first output
+  // is blk_off[r / kLocRows] + loc[r]: loc is local to the row's block of
+  // kLocRows rows, blk_off the exclusive scan of the per-block totals.
+  u32* loc; u32* lo32; u64* blk_cnt; const u64* blk_off; u32* err;  // view rows < 2^32
+  u64 total; u64 j_begin;
   u32* bitmap; u64* out_count;
 };
 
+constexpr u64 kLocRows = 1024;  // rows per offset block: 256 threads x 4 consecutive rows
+constexpr u32 kErrLocOverflow = 1;  // a block's matches reached 2^32
+
+inline u64 pjoin_loc_blocks(u64 n_in) { return (n_in + kLocRows - 1) / kLocRows; }
+// count: loc, lo32 and blk_cnt for every input row / block; sets *err on overflow
 void pjoin_count(int sem, const PStep& P, cudaStream_t st);
+// tile partition of outputs [j_begin, j_begin + total) (needs blk_off): ntiles + 1 row indices
+void pjoin_partition(const PStep& P, u64 ntiles, u64* part, cudaStream_t st);
 void pjoin_emit(int sem, const PStep& P, const u64* part, cudaStream_t st);
 void pjoin_project(int sem, const PStep& P, cudaStream_t st);

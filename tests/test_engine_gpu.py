@@ -192,3 +192,27 @@ def test_parse_and_unknown_relation_errors():
     with pytest.raises(LobsterError, match="E_ARG"):
         e.add_rule("path(x,y) :- edge(x,y,z).")
     e.close()
+
+
+# ---------------------------------------------------------------------------
+# join steps: packed-word kernels (block-local offsets) vs the general kernels,
+# on skewed fan-out, ragged row counts, sub-range emission and the filter
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("packed_join", [0, 1])
+def test_emission_paths(packed_join):
+    opts = {"packed_join": packed_join}
+    parent, child, _ = W.random_tree(2500, seed_index=160)
+    compare(W.SG_PROGRAM, {"parent": ((parent, child),)}, options=opts)
+    compare(W.SG_PROGRAM, {"parent": ((parent, child),)}, options=dict(opts, emit_filter=2))
+    a, b = W.ktree_chain(300)
+    compare(W.TC_PROGRAM, {"edge": ((a, b),)}, options=dict(opts, max_candidates=4096))
+    s, d = W.chung_lu_power_law(3000, 15000, seed_index=162)  # skewed fan-out: rows with thousands of matches
+    compare(W.TC_PROGRAM, {"edge": ((s, d),)}, options=opts)
+    compare(W.TC_PROGRAM, {"edge": ((s, d),)}, options=dict(opts, emit_filter=2, max_candidates=50000))
+    A = W.andersen_program(3000, 9000, seed_index=163)
+    compare(W.ANDERSEN_PROGRAM, {k: ((v[0], v[1]),) for k, v in A.items()}, rels=["pt"], options=opts)
+    g = W.grid_reach_instance(20, sub=161)
+    src, dst, p = g["edge"]
+    for sr in ("max_min", "diff_add_mult"):
+        compare(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, sr, options=opts)
