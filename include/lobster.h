@@ -165,6 +165,12 @@ int lob_reset(lob_engine* e);
  *                  waits; LOB_E_TIMEOUT if one gives up)            (default 0)
  *   "packed_join"  1: join kernels on packed words when an arm's bindings
  *                  fit 64 bits; 0: the general kernels               (default 1)
+ *   "bitmap_delta" relations with a membership filter: 2 = the joins only
+ *                  set bits and each iteration's new facts are read, in key
+ *                  order, out of the bitmap and its start-of-iteration copy;
+ *                  1 = that whenever the last iteration's new facts
+ *                  outnumber bitmap bytes / 64; 0 = never (candidates are
+ *                  sorted and merged)                                (default 1)
  * LOB_E_ARG for an unknown key or a value out of range. */
 int lob_set_option(lob_engine* e, const char* key, int64_t value);
 

@@ -146,8 +146,9 @@ static void release_derived(lob_engine& e) {
     for (auto& v : r.views) release_view(e, v);
     r.views.clear();
     for (DevBuf* b : {&r.rkeys, &r.rtags, &r.nkeys, &r.ntags, &r.ckeys, &r.ctags, &r.ckeys2, &r.ctags2, &r.row_factor,
-                      &r.row_keys, &r.akeys, &r.atags, &r.akeys2, &r.atags2, &r.bitmap})
+                      &r.row_keys, &r.akeys, &r.atags, &r.akeys2, &r.atags2, &r.bitmap, &r.prev_bitmap})
       e.release(*b);
+    r.extract = r.touched = r.keys_stale = false;
     r.n_recent = r.n_next = r.n_cand = r.n_acc = 0;
     r.flushed = false;
     r.filter_on = false;
@@ -539,7 +540,11 @@ static void prepare(lob_engine& e, int sem) {
     for (auto& A : p.arms) {
       const bool late = e.rels[p.ast.body[A.delta].rel].idb || sem_stamps(sem);
       for (size_t s = 1; s < A.steps.size(); s++)
-        if (late) e.rels[p.ast.body[A.steps[s].atom].rel].views[A.steps[s].view].maintained = true;
+        if (late) {
+          ViewSt& W = e.rels[p.ast.body[A.steps[s].atom].rel].views[A.steps[s].view];
+          W.maintained = true;
+          W.probed_late = true;
+        }
     }
   for (auto& p : e.plans)
     for (auto& A : p.arms) A.packed = e.opt_packed_join ? compile_packed(e, p.ast, A) : PackedArm{};
@@ -763,6 +768,13 @@ static void ensure_cand(lob_engine& e, RelSt& H, u64 extra) {
 // iteration's accumulator, so that no sort ever sees more than opt_max_cand keys.
 static void flush_candidates(lob_engine& e, RelSt& H) {
   const u64 n = H.n_cand;
+  if (H.extract) {  // bitmap delta mode: candidates only need their bits set
+    bitmap_set_keys(H.ckeys.p, H.views[0].lay.key64, n, H.bitmap.as<u32>(), e.stream);
+    e.after_launch("bitmap");
+    e.launches += n ? 1 : 0;
+    H.n_cand = 0;
+    return;
+  }
   H.flushed = true;
   if (!n) return;
   const int ks = sem_kernel(e.semiring);
@@ -1089,6 +1101,28 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
       throw LobError(LOB_E_ARG, "join step: 1024 consecutive input rows have 2^32 or more matches");
     const u64 total = e.pinned[0];
     if (!total) return;
+    if (last && H.extract) {  // new facts only set their bits in the membership bitmap
+      H.touched = true;
+      P.out_words = nullptr;
+      P.out_tags = nullptr;
+      P.out_base = 0;
+      P.out_count = nullptr;
+      P.bitmap = H.bitmap.as<u32>();
+      for (u64 jb = 0; jb < total; jb += e.opt_max_cand) {
+        const u64 sub = std::min(e.opt_max_cand, total - jb);
+        const u64 nt = (sub + kEmitTile - 1) / kEmitTile;
+        e.ensure(e.part, (nt + 1) * 8);
+        P.total = sub;
+        P.j_begin = jb;
+        pjoin_partition(P, nt, e.part.as<u64>(), e.stream);
+        pjoin_emit(sem, P, e.part.as<u64>(), e.stream);
+        e.after_launch("join emit");
+        e.launches += 2;
+        H.cand_iter += sub;
+        e.cand_emitted += sub;
+      }
+      return;
+    }
     if (last) {  // candidates, in sub-ranges of at most opt_max_cand outputs
       for (u64 jb = 0; jb < total; jb += e.opt_max_cand) {
         const u64 sub = std::min(e.opt_max_cand, total - jb);
@@ -1142,10 +1176,101 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
 }
 
 // sort + unique + difference/merge of one head relation's candidates
+static void dedup_sorted(lob_engine& e, RelSt& H, u32 k);
+static u64 bitmap_bits(const RelSt& H) { return 1ull << H.views[0].lay.bits; }
+
+// The primary view's keys, read out of a membership bitmap (sorted).
+static void materialize_keys(lob_engine& e, RelSt& H, const u32* bits) {
+  ViewSt& V = H.views[0];
+  const int kb = V.lay.key64 ? 8 : 4;
+  scratch_at_least(e, bits_scratch_bytes(bitmap_bits(H)));
+  e.launches += bits_count(bits, nullptr, bitmap_bits(H), e.scratch.p, e.counts.as<u64>() + 1, e.stream);
+  e.after_launch("bitmap count");
+  const u64 n = e.read_u64(e.counts.as<u64>() + 1);
+  if (n != V.n) throw LobError(LOB_E_CUDA, "internal error: membership bitmap and relation size disagree");
+  e.ensure(V.keys, n * kb);
+  bits_extract(bits, nullptr, bitmap_bits(H), V.lay.key64, V.keys.p, n, e.scratch.p, e.stream);
+  e.after_launch("bitmap extract");
+  e.launches++;
+  H.keys_stale = false;
+  for (auto& kv : V.index) kv.second.valid = false;
+}
+
+// A relation that no arm probes after iteration 1 (arms whose delta is an
+// input relation run in iteration 1 only, before the first dedup).
+static bool probed_after_first(const RelSt& H) {
+  for (const ViewSt& W : H.views)
+    if (W.probed_late) return true;
+  return false;
+}
+
+// Bitmap delta mode: this iteration's new facts are the bits set in the
+// membership bitmap but not in its start-of-iteration copy, read out in key
+// order; candidates written by other kernels (projections, general joins) only
+// add their bits first.  The full relation's keys are merged only when some arm
+// probes it later; otherwise they stay in the bitmap until the fixpoint.
+static void dedup_bitmap_delta(lob_engine& e, RelSt& H, u32 k) {
+  ViewSt& V = H.views[0];
+  const Layout& L = V.lay;
+  const int kb = L.key64 ? 8 : 4;
+  const u64 n = H.n_cand;
+  H.unfiltered = false;
+  H.flushed = false;
+  if (n) bitmap_set_keys(H.ckeys.p, L.key64, n, H.bitmap.as<u32>(), e.stream);
+  e.launches += n ? 1 : 0;
+  H.n_cand = 0;
+  if (!n && !H.touched) {
+    H.last_new = 0;
+    return;
+  }
+  scratch_at_least(e, bits_scratch_bytes(bitmap_bits(H)));
+  e.launches += bits_count(H.bitmap.as<u32>(), H.prev_bitmap.as<u32>(), bitmap_bits(H), e.scratch.p,
+                           e.counts.as<u64>() + 1, e.stream);
+  e.after_launch("bitmap count");
+  const u64 nr = e.read_u64(e.counts.as<u64>() + 1);
+  H.last_new = nr;
+  if (!nr) return;
+  e.ensure(H.nkeys, nr * kb);
+  bits_extract(H.bitmap.as<u32>(), H.prev_bitmap.as<u32>(), bitmap_bits(H), L.key64, H.nkeys.p, nr, e.scratch.p,
+               e.stream);
+  e.after_launch("bitmap extract");
+  e.launches++;
+  H.n_next = nr;
+  if (probed_after_first(H)) {
+    e.ensure(V.keys2, (V.n + nr) * kb);
+    scratch_at_least(e, merge_nodup_scratch_bytes(V.n, nr));
+    merge_nodup(L.key64, V.keys.p, V.n, H.nkeys.p, nr, V.keys2.p, e.scratch.p, e.stream);
+    e.after_launch("merge");
+    e.launches++;
+    std::swap(V.keys, V.keys2);
+  } else {
+    H.keys_stale = true;
+  }
+  V.n += nr;
+  for (auto& kv : V.index) kv.second.valid = false;
+  update_secondary_views(e, H, k, nr);
+}
+
 static void dedup_relation(lob_engine& e, RelSt& H, u32 k) {
   H.n_next = 0;
   H.last_cand = H.cand_iter;
   H.cand_iter = 0;
+  if (H.extract) {
+    dedup_bitmap_delta(e, H, k);
+    return;
+  }
+  // sorted-candidate path: the keys must be materialised, and the start-of-
+  // iteration bitmap copy (when kept) follows the bitmap at the end
+  if (H.keys_stale) materialize_keys(e, H, H.prev_bitmap.as<u32>());
+  dedup_sorted(e, H, k);
+  if (H.prev_bitmap.p && H.n_next) {
+    bitmap_set_keys(H.nkeys.p, H.views[0].lay.key64, H.n_next, H.prev_bitmap.as<u32>(), e.stream);
+    e.after_launch("bitmap");
+    e.launches++;
+  }
+}
+
+static void dedup_sorted(lob_engine& e, RelSt& H, u32 k) {
   const u64 n = H.n_cand;
   if (!n && !H.flushed) {
     H.last_new = 0;
@@ -1265,6 +1390,21 @@ static void maybe_enable_filter(lob_engine& e, RelSt& r) {
   e.after_launch("bitmap");
   e.launches++;
   r.filter_on = true;
+  if (e.opt_bitmap_delta) {
+    e.ensure(r.prev_bitmap, words * 4);
+    e.check(cudaMemcpyAsync(r.prev_bitmap.p, r.bitmap.p, words * 4, cudaMemcpyDeviceToDevice, e.stream), "bitmap copy");
+  }
+}
+
+// Bitmap delta mode for this iteration when reading the two bitmaps (about
+// 2.5 bitmap sizes of traffic) is predicted to cost less than sorting and
+// merging the new facts (the last iteration's count as the prediction).
+static void choose_dedup_mode(lob_engine& e, RelSt& r) {
+  r.touched = false;
+  r.extract = false;
+  if (!r.filter_on || !r.prev_bitmap.p) return;
+  const u64 bitmap_bytes = bitmap_bits(r) / 8;
+  r.extract = e.opt_bitmap_delta == 2 || (e.opt_bitmap_delta == 1 && r.last_new * 64 >= bitmap_bytes);
 }
 
 static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
@@ -1291,6 +1431,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
     e.iter_counts.emplace_back();
     for (auto& r : e.rels) e.iter_counts.back().emplace_back(r.views[0].n, r.n_recent);
     for (auto& r : e.rels) maybe_enable_filter(e, r);
+    for (auto& r : e.rels) choose_dedup_mode(e, r);
     for (auto& r : e.rels) r.n_cand = 0;
     for (auto& p : e.plans) {
       for (auto& A : p.arms) {
@@ -1319,6 +1460,8 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
     s.new_facts += total_new;
     if (!total_new) break;
   }
+  for (auto& r : e.rels)
+    if (r.keys_stale) materialize_keys(e, r, r.bitmap.as<u32>());
   e.check(cudaEventRecord(ev1, e.stream), "event");
   e.sync();
   e.prof.flush();
@@ -1767,6 +1910,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "emit_filter" && value >= 0 && value <= 2) e->opt_emit_filter = (int)value;
     else if (k == "sort_algo" && (value == 0 || value == 1)) e->opt_sort_algo = (int)value;
     else if (k == "packed_join" && (value == 0 || value == 1)) e->opt_packed_join = (int)value;
+    else if (k == "bitmap_delta" && value >= 0 && value <= 2) e->opt_bitmap_delta = (int)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

@@ -61,6 +61,7 @@ struct ViewSt {
   DevBuf keys2, tags2, stamps2;  // merge target
   u64 n = 0;
   bool probed = false;
+  bool probed_late = false; // probed by an arm that can run after iteration 1
   bool maintained = false;  // merged with new facts every iteration
   bool stale = false;       // behind the primary view; rebuilt before its next probe
   std::map<int, IndexSt> index;  // by prefix length
@@ -89,6 +90,10 @@ struct RelSt {
   bool flushed = false;
   // membership filter at emission (unit semiring): bitmap over the key space
   DevBuf bitmap;
+  DevBuf prev_bitmap;       // the bitmap as the iteration started (bitmap delta mode)
+  bool extract = false;     // this iteration: new facts only set bits; read out of bitmap & ~prev_bitmap
+  bool touched = false;     // this iteration emitted into the bitmap
+  bool keys_stale = false;  // primary view keys not materialised (the bitmaps hold the relation)
   bool filter_on = false;
   bool unfiltered = false;  // this iteration appended candidates that bypassed the filter
   u64 last_cand = 0, last_new = 0, cand_iter = 0;
@@ -172,6 +177,7 @@ struct lob_engine {
   int opt_emit_filter = 1;        // unit semiring: membership bitmap at emission when duplicates dominate
   int opt_sort_algo = 0;          // 0: reduce-then-scan passes, 1: one kernel per pass with look-back
   int opt_packed_join = 1;        // packed-word join kernels when an arm's bindings fit 64 bits
+  int opt_bitmap_delta = 1;       // filtered relations: 0 never, 1 when predicted cheaper, 2 always read new facts from the bitmap
   EngineProfiler prof;
   // run state
   int state = 0;  // 0 loading, 1 ran

@@ -144,6 +144,15 @@ void join_emit(int sem, const StepParams& P, const u64* part, cudaStream_t st);
 void project_rows(int sem, const StepParams& P, cudaStream_t st);
 // set the bit of every key of a sorted view in a membership bitmap
 void bitmap_set_keys(const void* keys, int key64, u64 n, u32* bitmap, cudaStream_t st);
+
+// Sorted keys from membership bitmaps of nbits bits (bitset.cu).  bits_count
+// counts the bits of a (of a & ~b when b is given) into *total_dev and places
+// them per tile in scratch (bits_scratch_bytes); bits_extract, called next with
+// the same a, b and scratch, writes those bits' keys in increasing order to out
+// (n_out of them) and sets b |= a.  bits_count returns its kernel launches.
+size_t bits_scratch_bytes(u64 nbits);
+int bits_count(const u32* a, const u32* b, u64 nbits, void* scratch, u64* total_dev, cudaStream_t st);
+void bits_extract(const u32* a, u32* b, u64 nbits, int key64, void* out, u64 n_out, void* scratch, cudaStream_t st);
 // merge two sorted key lists known to share no key (keys only)
 size_t merge_nodup_scratch_bytes(u64 na, u64 nb);
 void merge_nodup(int key64, const void* a, u64 na, const void* b, u64 nb, void* out, void* scratch, cudaStream_t st);

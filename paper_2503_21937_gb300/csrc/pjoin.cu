@@ -71,7 +71,7 @@ LOB_DEV u64 lower_bound_w(const void* keys, int key64, u64 n, u64 x) {
 
 LOB_DEV u64 row_off(const PStep& P, u64 r) { return P.blk_off[r / kLocRows] + P.loc[r]; }
 
-template <class Sem, bool kFilter>
+template <class Sem, int kFilter>
 __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, const u64* __restrict__ part) {
   typedef typename Sem::Stored S;
   typedef typename Sem::Cand C;
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
   for (int i = 0; i < kItems; i++) row_of[threadIdx.x * kItems + i] = loc[i] > ex ? loc[i] : ex;
   __syncthreads();
   const u64 invalid_out = P.out_w64 ? ~0ull : 0xFFFFFFFFull;
-  u64 kept[kFilter ? kItems : 1];
+  u64 kept[kFilter == 1 ? kItems : 1];
   u32 nkeep = 0;
 #pragma unroll 2
   for (int i = 0; i < kItems; i++) {
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
       u32* word = P.bitmap + (w >> 5);
       if (*reinterpret_cast<volatile u32*>(word) & bit) continue;  // a known fact: no atomic needed
       if (atomicOr(word, bit) & bit) continue;
-      kept[nkeep++] = w;
+      if constexpr (kFilter == 1) kept[nkeep++] = w;
     } else {
       const u64 o = P.out_base + (j - P.j_begin);
       if (P.out_w64) reinterpret_cast<u64*>(P.out_words)[o] = w;
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
       if constexpr (Sem::kTags) reinterpret_cast<C*>(P.out_tags)[o] = Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v]));
     }
   }
-  if constexpr (kFilter) {
+  if constexpr (kFilter == 1) {
     // compact the tile's survivors in shared memory (reusing row_of), then
     // store them with consecutive threads writing consecutive words
     u32 tot;
@@ -210,7 +210,7 @@ LOB_DEV u64 reg_pick(const RegOp& o, u64 wi, u64 wv) {
   return o.word == 2 ? (u64)o.cval : (((o.word ? wv : wi) >> o.shift) & o.mask);
 }
 
-template <class Sem, bool kFilter, int NOUT, int NCHK>
+template <class Sem, int kFilter, int NOUT, int NCHK>
 __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PStep P, const u64* __restrict__ part) {
   typedef typename Sem::Stored S;
   typedef typename Sem::Cand C;
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
   }
   const u64 invalid_out = P.out_w64 ? ~0ull : 0xFFFFFFFFull;
   const u64 invalid_in = P.in_w64 ? ~0ull : 0xFFFFFFFFull;
-  u64 kept[kFilter ? kItems : 1];
+  u64 kept[kFilter == 1 ? kItems : 1];
   u32 nkeep = 0;
   constexpr int B = 2;  // outputs whose loads are issued together (keeps registers, and occupancy, up)
 #pragma unroll 1
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
         u32* word = P.bitmap + (w >> 5);
         if (*reinterpret_cast<volatile u32*>(word) & bit) continue;
         if (atomicOr(word, bit) & bit) continue;
-        kept[nkeep++] = w;
+        if constexpr (kFilter == 1) kept[nkeep++] = w;
       } else {
         const u64 o = P.out_base + (j - P.j_begin);
         if (!ok) w = invalid_out;
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
       }
     }
   }
-  if constexpr (kFilter) {
+  if constexpr (kFilter == 1) {
     u32 tot;
     const u32 mine = block_exclusive_sum<u32>(nkeep, sm, &tot);
     if (threadIdx.x == 0) block_base = tot ? atomicAdd(reinterpret_cast<unsigned long long*>(P.out_count), (u64)tot) : 0ull;
@@ -497,11 +497,11 @@ void by_sem_p(int sem, A&&... a) {
     default: L<SemAddMult>::go(a...); break;
   }
 }
-template <class Sem, bool F, int NO, int NC>
+template <class Sem, int F, int NO, int NC>
 void launch_fast(const PStep& P, const u64* part, unsigned tiles, cudaStream_t st) {
   k_pemit_fast<Sem, F, NO, NC><<<tiles, 256, 0, st>>>(P, part);
 }
-template <class Sem, bool F>
+template <class Sem, int F>
 bool try_fast(const PStep& P, const u64* part, unsigned tiles, cudaStream_t st) {
   const int no = P.n_out, nc = P.n_checks;
 #define LOB_FAST(NO, NC) if (no == NO && nc == NC) { launch_fast<Sem, F, NO, NC>(P, part, tiles, st); return true; }
@@ -513,11 +513,15 @@ bool try_fast(const PStep& P, const u64* part, unsigned tiles, cudaStream_t st) 
 template <class Sem> struct PEmitL {
   static void go(const PStep& P, const u64* part, cudaStream_t st) {
     const u64 tiles = (P.total + kEmitTile - 1) / kEmitTile;
-    if (std::is_same<Sem, SemUnit>::value && P.bitmap) {
-      if (!try_fast<SemUnit, true>(P, part, (unsigned)tiles, st))
-        k_pemit<SemUnit, true><<<(unsigned)tiles, 256, 0, st>>>(P, part);
-    } else if (!try_fast<Sem, false>(P, part, (unsigned)tiles, st)) {
-      k_pemit<Sem, false><<<(unsigned)tiles, 256, 0, st>>>(P, part);
+    // membership filter: 1 = new facts also written out, 2 = bitmap only
+    if (std::is_same<Sem, SemUnit>::value && P.bitmap && P.out_words) {
+      if (!try_fast<SemUnit, 1>(P, part, (unsigned)tiles, st))
+        k_pemit<SemUnit, 1><<<(unsigned)tiles, 256, 0, st>>>(P, part);
+    } else if (std::is_same<Sem, SemUnit>::value && P.bitmap) {
+      if (!try_fast<SemUnit, 2>(P, part, (unsigned)tiles, st))
+        k_pemit<SemUnit, 2><<<(unsigned)tiles, 256, 0, st>>>(P, part);
+    } else if (!try_fast<Sem, 0>(P, part, (unsigned)tiles, st)) {
+      k_pemit<Sem, 0><<<(unsigned)tiles, 256, 0, st>>>(P, part);
     }
   }
 };

@@ -216,3 +216,26 @@ def test_emission_paths(packed_join):
     src, dst, p = g["edge"]
     for sr in ("max_min", "diff_add_mult"):
         compare(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, sr, options=opts)
+
+
+# ---------------------------------------------------------------------------
+# bitmap delta mode: new facts read out of the membership bitmaps
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_bitmap_delta(mode):
+    opts = {"bitmap_delta": mode, "emit_filter": 2}
+    parent, child, _ = W.random_tree(2500, seed_index=170)
+    compare(W.SG_PROGRAM, {"parent": ((parent, child),)}, options=opts)
+    a, b = W.erdos_renyi(300, 1500, seed_index=171)
+    compare(W.TC_PROGRAM, {"edge": ((a, b),)}, options=opts)
+    # chunked candidate sets from the general kernels and projections
+    compare(W.TC_PROGRAM, {"edge": ((a, b),)}, options=dict(opts, max_candidates=4096, packed_join=0))
+    # the full relation is probed after iteration 1 (non-linear rule): merged every iteration
+    nonlinear = "path(x,y) :- edge(x,y).\npath(x,z) :- path(x,y), path(y,z).\n"
+    compare(nonlinear, {"edge": ((a, b),)}, options=opts)
+    A = W.andersen_program(3000, 9000, seed_index=172)
+    compare(W.ANDERSEN_PROGRAM, {k: ((v[0], v[1]),) for k, v in A.items()}, rels=["pt"], options=opts)
+    # 34-bit keys (u64 words, 2 GB bitmaps)
+    s, d = W.erdos_renyi(70000, 140000, seed_index=173)
+    compare(W.TC_PROGRAM, {"edge": ((s[:3000], d[:3000]),)}, options=opts)
