@@ -8,9 +8,9 @@
 // needed for them (Sec. 3.2's sort / unique / difference on candidate tuples,
 // computed here as a set difference of two bitmaps).
 //
-// Each 256-thread tile owns 4096 consecutive words (16 per thread); a first
-// pass counts the tile's bits, an exclusive scan places the tiles, and a second
-// pass writes every thread's keys in increasing order from its scanned offset.
+// Each 256-thread tile owns 4096 consecutive words; a first pass counts the
+// tile's bits, an exclusive scan places the tiles, and a second pass writes the
+// tile's keys in increasing order from its scanned offset.
 #include "kernels.h"
 #include "scan.cuh"
 
@@ -68,33 +68,66 @@ __global__ void __launch_bounds__(256) k_bits_count(const u32* __restrict__ a, c
   }
 }
 
+// Extraction: warp w of a tile owns the tile's words [w*512, (w+1)*512), held
+// lane-strided (lane l has words i*32 + l, i < 16) so every load and the
+// catch-up store of the copy are coalesced.  The warp walks its 16 batches of
+// 32 words in order: a warp scan of the batch's bit counts places each lane's
+// keys in the warp's shared-memory stage, and the warp then stores the batch's
+// keys to consecutive global addresses.
+constexpr int kWarpWords = kBitTileWords / 8;
+constexpr int kBatches = kWarpWords / 32;
+
 template <class K, bool kDiff>
 __global__ void __launch_bounds__(256) k_bits_extract(const u32* __restrict__ a, u32* __restrict__ b, u64 nwords,
                                                       u64 ntiles, const u64* __restrict__ tile_off, K* __restrict__ out) {
-  __shared__ u32 sm[256 / 32 + 1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  K* stage = reinterpret_cast<K*>(smem_raw) + (threadIdx.x >> 5) * 1024;
+  __shared__ u64 wbase[256 / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const u64 w0 = t * kBitTileWords + (u64)threadIdx.x * kSliceWords;
-    u32 x[kSliceWords];
-    load_slice<kDiff>(a, b, w0, nwords, x);
+    const u64 wf = t * kBitTileWords + (u64)warp * kWarpWords;  // this warp's first word
+    u32 x[kBatches], av[kBatches];
     u32 c = 0;
 #pragma unroll
-    for (int j = 0; j < kSliceWords; j++) c += __popc(x[j]);
-    u32 tot;
-    const u32 ex = block_exclusive_sum<u32>(c, sm, &tot);
-    u64 o = tile_off[t] + ex;
+    for (int i = 0; i < kBatches; i++) {
+      const u64 w = wf + (u64)i * 32 + lane;
+      av[i] = w < nwords ? a[w] : 0u;
+      x[i] = av[i];
+    }
+    if constexpr (kDiff) {
 #pragma unroll
-    for (int j = 0; j < kSliceWords; j++) {
-      u32 m = x[j];
-      const K base = (K)((w0 + j) << 5);
-      while (m) {
-        out[o++] = base | (K)(__ffs(m) - 1);
-        m &= m - 1;
+      for (int i = 0; i < kBatches; i++) {
+        const u64 w = wf + (u64)i * 32 + lane;
+        x[i] &= w < nwords ? ~b[w] : 0u;
       }
     }
-    if constexpr (kDiff) {  // the start-of-iteration copy catches up with the bitmap
 #pragma unroll
-      for (int j = 0; j < kSliceWords; j++)
-        if (x[j]) b[w0 + j] |= x[j];
+    for (int i = 0; i < kBatches; i++) c += __popc(x[i]);
+    c = warp_inclusive_sum(c);
+    if (lane == 31) wbase[warp] = c;
+    __syncthreads();
+    u64 base = tile_off[t];
+    for (int v = 0; v < warp; v++) base += wbase[v];
+    __syncthreads();  // wbase is rewritten by the next tile
+#pragma unroll
+    for (int i = 0; i < kBatches; i++) {
+      const u32 m0 = x[i];
+      const u32 cnt = __popc(m0);
+      const u32 inc = warp_inclusive_sum(cnt);
+      const u32 tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+      if (!tot) continue;
+      u32 pos = inc - cnt;
+      const K kw = (K)((wf + (u64)i * 32 + lane) << 5);
+      for (u32 m = m0; m; m &= m - 1) stage[pos++] = kw | (K)(__ffs(m) - 1);
+      __syncwarp();
+      for (u32 q = lane; q < tot; q += 32) out[base + q] = stage[q];
+      __syncwarp();
+      base += tot;
+    }
+    if constexpr (kDiff) {  // the start-of-iteration copy catches up (b is a subset of a)
+#pragma unroll
+      for (int i = 0; i < kBatches; i++)
+        if (x[i]) b[wf + (u64)i * 32 + lane] = av[i];
     }
   }
 }
@@ -129,11 +162,18 @@ void bits_extract(const u32* a, u32* b, u64 nbits, int key64, void* out, u64 n_o
   const u64* tile_off = reinterpret_cast<const u64*>(scratch) + nt;
   ProfScope ps("bitmap_extract", nw * (b ? 8.0 : 4.0) + n_out * (key64 ? 8.0 : 4.0), st);
   const unsigned g = bit_grid(nt);
+  const int sm32 = 8 * 1024 * 4, sm64 = 8 * 1024 * 8;  // one 1024-key stage per warp
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_bits_extract<u64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64);
+    cudaFuncSetAttribute(k_bits_extract<u64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64);
+    attr = true;
+  }
   if (key64) {
-    if (b) k_bits_extract<u64, true><<<g, 256, 0, st>>>(a, b, nw, nt, tile_off, reinterpret_cast<u64*>(out));
-    else k_bits_extract<u64, false><<<g, 256, 0, st>>>(a, nullptr, nw, nt, tile_off, reinterpret_cast<u64*>(out));
+    if (b) k_bits_extract<u64, true><<<g, 256, sm64, st>>>(a, b, nw, nt, tile_off, reinterpret_cast<u64*>(out));
+    else k_bits_extract<u64, false><<<g, 256, sm64, st>>>(a, nullptr, nw, nt, tile_off, reinterpret_cast<u64*>(out));
   } else {
-    if (b) k_bits_extract<u32, true><<<g, 256, 0, st>>>(a, b, nw, nt, tile_off, reinterpret_cast<u32*>(out));
-    else k_bits_extract<u32, false><<<g, 256, 0, st>>>(a, nullptr, nw, nt, tile_off, reinterpret_cast<u32*>(out));
+    if (b) k_bits_extract<u32, true><<<g, 256, sm32, st>>>(a, b, nw, nt, tile_off, reinterpret_cast<u32*>(out));
+    else k_bits_extract<u32, false><<<g, 256, sm32, st>>>(a, nullptr, nw, nt, tile_off, reinterpret_cast<u32*>(out));
   }
 }

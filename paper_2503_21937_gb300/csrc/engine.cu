@@ -1396,15 +1396,28 @@ static void maybe_enable_filter(lob_engine& e, RelSt& r) {
   }
 }
 
-// Bitmap delta mode for this iteration when reading the two bitmaps (about
-// 2.5 bitmap sizes of traffic) is predicted to cost less than sorting and
-// merging the new facts (the last iteration's count as the prediction).
+// Bitmap delta mode for this iteration when its predicted traffic is lower.
+// Bitmap delta: both bitmaps read twice and the copy written (about 2.5 bitmap
+// sizes).  Sorted candidates: about 64 bytes of sort work per new fact (the
+// last iteration's count as the prediction), plus reading the keys out of the
+// bitmap first when they are not materialised.  Both merge the new facts into
+// the full relation's keys (a read and a write of them) when a later arm probes
+// it; only the sorted path merges them otherwise.
 static void choose_dedup_mode(lob_engine& e, RelSt& r) {
   r.touched = false;
   r.extract = false;
   if (!r.filter_on || !r.prev_bitmap.p) return;
-  const u64 bitmap_bytes = bitmap_bits(r) / 8;
-  r.extract = e.opt_bitmap_delta == 2 || (e.opt_bitmap_delta == 1 && r.last_new * 64 >= bitmap_bytes);
+  if (e.opt_bitmap_delta != 1) {
+    r.extract = e.opt_bitmap_delta == 2;
+    return;
+  }
+  const double bitmap_bytes = (double)(bitmap_bits(r) / 8);
+  const double kb = r.views[0].lay.key64 ? 8.0 : 4.0;
+  const double merge = 2.0 * kb * (double)r.views[0].n;
+  const double delta_cost = 2.5 * bitmap_bytes + (probed_after_first(r) ? merge : 0.0);
+  const double sorted_cost = 64.0 * (double)r.last_new + merge +
+                             (r.keys_stale ? bitmap_bytes + kb * (double)r.views[0].n : 0.0);
+  r.extract = delta_cost <= sorted_cost;
 }
 
 static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
