@@ -359,7 +359,7 @@ def main():
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    times, derived, launches, iters = [], [], 0, {}
+    times, derived, launches, iters, cands = [], [], 0, {}, {}
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
             flush.fill_(1)  # L2 flush between timed steps (256 MiB write), outside the timed interval
@@ -372,6 +372,7 @@ def main():
             derived.append(sum(s["derived"] for s in st.values()))
             launches += sum(s["kernel_launches"] for s in st.values())
             iters = {k: s["iterations"] for k, s in st.items()}
+            cands = {k: s["candidates"] for k, s in st.items()}
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = sum(times)
@@ -457,7 +458,7 @@ def main():
                 "config": {"workload": WORKLOAD, "sg_tree_nodes": SG_NODES, "tc_nodes": TC_NODES,
                            "tc_edges": TC_EDGES, "semiring": "unit", "parallelism": "replicas" if world > 1 else "1 GPU",
                            "l2": "flushed between timed steps (256 MiB write)",
-                           "derived_per_step": derived[0], "iterations": iters,
+                           "derived_per_step": derived[0], "iterations": iters, "join_outputs": cands,
                            "engine_options": args.option},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "kernels": kernels, "kernels_by_workload": by_workload, "batched": batched}

@@ -128,6 +128,10 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
       if (!ok) continue;
       const u32 bit = 1u << (u32)(w & 31u);
       u32* word = P.bitmap + (w >> 5);
+      if constexpr (kFilter == 2) {  // bitmap only: set the bit, no old value needed
+        atomicOr(word, bit);
+        continue;
+      }
       if (*reinterpret_cast<volatile u32*>(word) & bit) continue;  // a known fact: no atomic needed
       if (atomicOr(word, bit) & bit) continue;
       if constexpr (kFilter == 1) kept[nkeep++] = w;
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
   const u64 invalid_in = P.in_w64 ? ~0ull : 0xFFFFFFFFull;
   u64 kept[kFilter == 1 ? kItems : 1];
   u32 nkeep = 0;
-  constexpr int B = 2;  // outputs whose loads are issued together (keeps registers, and occupancy, up)
+  constexpr int B = kFilter == 2 ? 4 : 2;  // outputs whose loads are issued together (keeps registers, and occupancy, up)
 #pragma unroll 1
   for (int i0 = 0; i0 < kItems; i0 += B) {
     u32 rr[B];
@@ -309,6 +313,10 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
         if (!ok) continue;
         const u32 bit = 1u << (u32)(w & 31u);
         u32* word = P.bitmap + (w >> 5);
+        if constexpr (kFilter == 2) {  // bitmap only: set the bit, no old value needed
+          atomicOr(word, bit);
+          continue;
+        }
         if (*reinterpret_cast<volatile u32*>(word) & bit) continue;
         if (atomicOr(word, bit) & bit) continue;
         if constexpr (kFilter == 1) kept[nkeep++] = w;
@@ -533,7 +541,9 @@ template <class Sem> struct PProjL {
 
 void pjoin_count(int sem, const PStep& P, cudaStream_t st) {
   const u64 n_blk = pjoin_loc_blocks(P.n_in);
-  ProfScope ps("join_count", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + 16.0 + 8.0) + n_blk * 8.0, st);
+  // input rows read, per-row offsets and match starts written (the index is
+  // read per distinct probe key, mostly from L2)
+  ProfScope ps("join_count", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + 8.0) + n_blk * 8.0, st);
   if (!P.n_in) return;
   const unsigned g = (unsigned)(n_blk < 152ull * 64 ? n_blk : 152ull * 64);
   if (P.index_mode == INDEX_DENSE && P.n_prefix == 1) k_pcount_loc<1><<<g, 256, 0, st>>>(P, n_blk);
@@ -548,9 +558,11 @@ void pjoin_partition(const PStep& P, u64 ntiles, u64* part, cudaStream_t st) {
 }
 
 void pjoin_emit(int sem, const PStep& P, const u64* part, cudaStream_t st) {
+  // read the input rows and their offsets once and each matched view key once;
+  // write each output (a membership-bitmap word per output in bitmap-only mode)
   const double vb = (P.v_key64 ? 8 : 4) + (sem == SR_UNIT ? 0 : (sem == SR_DIFF_MAX_MIN ? 8 : 4));
-  ProfScope ps("join_emit", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + 16.0) +
-                                P.total * (vb + row_bytes(sem, P.out_w64, false)), st);
+  const double ob = P.out_words ? row_bytes(sem, P.out_w64, false) : 4.0;
+  ProfScope ps("join_emit", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + 8.0) + P.total * (vb + ob), st);
   if (P.total) by_sem_p<PEmitL>(sem, P, part, st);
 }
 
