@@ -49,6 +49,9 @@ void EngineProfiler::end(const char* name, double bytes, cudaStream_t st) {
   open.pop_back();
   done.push_back({name, o.a, b, bytes});
 }
+void EngineProfiler::add_last_bytes(double bytes) {
+  if (!done.empty()) done.back().bytes += bytes;
+}
 void EngineProfiler::flush() {
   for (auto& d : done) {
     cudaEventSynchronize(d.b);
@@ -1075,6 +1078,54 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
     const IndexSt& I = W.index[S.prefix_len];
     P.index_mode = I.mode;
     P.dense_offs = I.offs.as<u64>();
+    // unit semiring: warp-balanced steps.  Views below 2^27 rows keep a 32-row
+    // group's outputs, and views below 2^22 rows a 1024-row block's outputs,
+    // under 2^32.
+    const bool warp = e.opt_warp_join && pjoin_warp_supported(sem, P) && W.n < (1ull << 27);
+    if (last && warp && H.extract) {  // one pass: probe, expand, set bits
+      H.touched = true;
+      P.out_words = nullptr;
+      P.bitmap = H.bitmap.as<u32>();
+      const u64 before = g_prof ? e.read_u64(e.counts.as<u64>() + 13) : 0;
+      pjoin_warp_bitmap(P, e.counts.as<u64>() + 13, e.stream);
+      e.after_launch("join emit");
+      e.launches++;
+      if (g_prof) {
+        const u64 outs = e.read_u64(e.counts.as<u64>() + 13) - before;
+        g_prof->add_last_bytes(outs * ((P.v_key64 ? 8.0 : 4.0) + 4.0));
+      }
+      return;
+    }
+    if (!last && warp && W.n < (1ull << 22)) {  // binding words placed per block of input rows
+      const u64 n_blk = pjoin_warp_blocks(n_in);
+      e.ensure(e.off, n_blk * 16);
+      pjoin_warp_count(P, e.off.as<u64>() + n_blk, e.stream);
+      e.after_launch("join count");
+      scratch_at_least(e, scan_scratch_elems(n_blk) * 8 + 64);
+      {
+        ProfScope ps("join_scan", n_blk * 16.0, e.stream);
+        exclusive_scan<u64, u64>(e.off.as<u64>() + n_blk, e.off.as<u64>(), n_blk, e.counts.as<u64>(), e.scratch.as<u64>(),
+                                 e.stream);
+      }
+      e.after_launch("join scan");
+      e.launches += 1 + scan_launches(n_blk);
+      const u64 total = e.read_u64(e.counts.as<u64>());
+      if (!total) return;
+      const int out_side = side ^ 1;
+      const int wb = P.out_w64 ? 8 : 4;
+      e.ensure(e.bind[out_side][0], total * wb);
+      P.out_words = e.bind[out_side][0].p;
+      P.out_tags = nullptr;
+      P.out_base = 0;
+      pjoin_warp_emit(P, total, e.off.as<u64>(), e.stream);
+      e.after_launch("join emit");
+      e.launches++;
+      side = out_side;
+      in_words = e.bind[side][0].p;
+      in_tags = nullptr;
+      n_in = total;
+      continue;
+    }
     const u64 n_blk = pjoin_loc_blocks(n_in);
     e.ensure(e.cnt, n_in * 4);
     e.ensure(e.lo, n_in * 4);
@@ -1438,6 +1489,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   e.iter_counts.clear();
   e.cand_emitted = 0;
   e.check(cudaMemsetAsync(sort_err(e), 0, sizeof(u32), e.stream), "sort error word");
+  e.check(cudaMemsetAsync(e.counts.as<u64>() + 13, 0, sizeof(u64), e.stream), "emitted counter");
   for (;;) {
     if (k >= max_iters) { rc = LOB_E_MAXITER; break; }
     k++;
@@ -1475,6 +1527,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   }
   for (auto& r : e.rels)
     if (r.keys_stale) materialize_keys(e, r, r.bitmap.as<u32>());
+  e.cand_emitted += e.read_u64(e.counts.as<u64>() + 13);  // outputs of bitmap-only warp steps
   e.check(cudaEventRecord(ev1, e.stream), "event");
   e.sync();
   e.prof.flush();
@@ -1924,6 +1977,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "sort_algo" && (value == 0 || value == 1)) e->opt_sort_algo = (int)value;
     else if (k == "packed_join" && (value == 0 || value == 1)) e->opt_packed_join = (int)value;
     else if (k == "bitmap_delta" && value >= 0 && value <= 2) e->opt_bitmap_delta = (int)value;
+    else if (k == "warp_join" && (value == 0 || value == 1)) e->opt_warp_join = (int)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

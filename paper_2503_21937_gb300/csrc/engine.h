@@ -155,6 +155,7 @@ struct EngineProfiler : KernelProfiler {
   cudaEvent_t take();
   void begin(const char* name, cudaStream_t st) override;
   void end(const char* name, double bytes, cudaStream_t st) override;
+  void add_last_bytes(double bytes) override;
   void flush();
   ~EngineProfiler();
 };
@@ -177,6 +178,7 @@ struct lob_engine {
   int opt_emit_filter = 1;        // unit semiring: membership bitmap at emission when duplicates dominate
   int opt_sort_algo = 0;          // 0: reduce-then-scan passes, 1: one kernel per pass with look-back
   int opt_packed_join = 1;        // packed-word join kernels when an arm's bindings fit 64 bits
+  int opt_warp_join = 1;          // unit semiring: warp-balanced packed join steps
   int opt_bitmap_delta = 1;       // filtered relations: 0 never, 1 when predicted cheaper, 2 always read new facts from the bitmap
   EngineProfiler prof;
   // run state

@@ -11,6 +11,8 @@ struct KernelProfiler {
   virtual void begin(const char* name, cudaStream_t st) = 0;
   // `bytes`: algorithmic bytes of this launch (what the step must read + write)
   virtual void end(const char* name, double bytes, cudaStream_t st) = 0;
+  // more algorithmic bytes for the last finished launch (known only after it ran)
+  virtual void add_last_bytes(double bytes) = 0;
   virtual ~KernelProfiler() {}
 };
 extern thread_local KernelProfiler* g_prof;

@@ -485,6 +485,184 @@ __global__ void k_ppartition(const __grid_constant__ PStep P, u64 n_blk, u64 nti
   part[t] = upper_bound_dev<u32>(P.loc, lo, hi, (u32)(j - P.blk_off[b])) - 1;
 }
 
+// ---------------------------------------------------------------------------
+// Warp-balanced expansion (unit semiring, where the order of a step's outputs
+// does not matter).  A warp takes 32 consecutive input rows, one per lane,
+// probes them, and scans the lanes' match counts; it then produces the rows'
+// outputs in rounds of 32, lane l taking output t = round * 32 + l, whose row
+// is found by a binary search over the lanes' scanned counts with shuffles.
+// No per-row arrays, no partition and no block barriers.  kMode 0: binding
+// words stored at positions claimed per warp with one atomicAdd (the step's
+// total is counted first, for the allocation); kMode 2: last step, every
+// output only sets its membership bit (a non-returning atomic OR).
+// ---------------------------------------------------------------------------
+LOB_DEV u32 probe_row(const PStep& P, u64 r, u64& wi, u32& lo) {
+  lo = 0;
+  wi = 0;
+  if (r >= P.n_in) return 0;
+  wi = load_word(P.in_words, P.in_w64, r);
+  if (wi == (P.in_w64 ? ~0ull : 0xFFFFFFFFull)) return 0;
+  if (P.in_stamp_mode != STAMP_NONE) {
+    const u32 st = P.in_stamp[r] & 0x7FFFFFFFu;
+    if (P.in_stamp_mode == STAMP_LT ? !(st < P.in_stamp_val) : st != P.in_stamp_val) return 0;
+  }
+  if (P.n_in_checks && !checks_ok(P.in_checks, P.n_in_checks, wi, 0)) return 0;
+  u64 pv = 0;
+  for (int q = 0; q < P.n_prefix; q++) {
+    const u64 x = pick(P.prefix[q].op, wi, 0);
+    if (P.prefix[q].limit_bits < 64 && (x >> P.prefix[q].limit_bits)) return 0;
+    pv |= x << P.prefix[q].shift;
+  }
+  u64 l, h;
+  if (P.index_mode == INDEX_DENSE) {
+    l = P.dense_offs[pv];
+    h = P.dense_offs[pv + 1];
+  } else if (P.whole_view) {
+    l = 0;
+    h = P.v_n;
+  } else {
+    const u64 klo = pv << P.rest_shift;
+    const u64 khi = klo + (1ull << P.rest_shift);
+    l = lower_bound_w(P.v_keys, P.v_key64, P.v_n, klo);
+    h = khi < klo ? P.v_n : lower_bound_w(P.v_keys, P.v_key64, P.v_n, khi);
+  }
+  lo = (u32)l;
+  return (u32)(h - l);
+}
+
+// Row blocks of the warp steps: 1024 rows, taken by a CTA as four rounds of
+// 256 (warp w of round i owns rows i*256 + w*32 .. +31, one per lane).
+constexpr u64 kWarpBlockRows = 1024;
+
+// outputs per row block (placement of an intermediate step's binding words)
+__global__ void __launch_bounds__(256) k_pwarp_count(const __grid_constant__ PStep P, u64* __restrict__ blk_cnt,
+                                                     u64 n_blk) {
+  __shared__ u64 part[256 / 32];
+  for (u64 b = blockIdx.x; b < n_blk; b += gridDim.x) {
+    u64 c = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      u64 wi;
+      u32 lo;
+      c += probe_row(P, b * kWarpBlockRows + (u64)i * 256 + threadIdx.x, wi, lo);
+    }
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      u64 t = 0;
+      for (int w = 0; w < 256 / 32; w++) t += part[w];
+      blk_cnt[b] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// the outputs of one 32-row group: lane l takes outputs l, l + 32, ...
+template <int kMode, int NOUT, int NCHK>
+LOB_DEV void warp_expand(const PStep& P, const RegOp* out_op, const u32* out_sh, const RegOp* ca, const RegOp* cb,
+                         const bool* ceq, u64 wi, u32 lo, u32 ex, u32 tot, u64 base) {
+  const int lane = threadIdx.x & 31;
+  for (u32 t0 = 0; t0 < tot; t0 += 32) {
+    const u32 t = t0 + lane;
+    int src = 0;  // the last lane whose outputs start at or before t
+#pragma unroll
+    for (int step = 16; step; step >>= 1) {
+      const u32 e = __shfl_sync(0xFFFFFFFFu, ex, src + step);
+      if (e <= t) src += step;
+    }
+    const u64 wr = __shfl_sync(0xFFFFFFFFu, wi, src);
+    const u32 lr = __shfl_sync(0xFFFFFFFFu, lo, src);
+    const u32 er = __shfl_sync(0xFFFFFFFFu, ex, src);
+    if (t >= tot) continue;
+    const u64 v = (u64)lr + (t - er);
+    const u64 wv = load_word(P.v_keys, P.v_key64, v);
+    bool ok = true;
+    if (P.v_stamp_mode != STAMP_NONE) {
+      const u32 st = P.v_stamp[v] & 0x7FFFFFFFu;
+      ok = P.v_stamp_mode == STAMP_LT ? st < P.v_stamp_val : st == P.v_stamp_val;
+    }
+#pragma unroll
+    for (int q = 0; q < NCHK; q++) ok = ok && ((reg_pick(ca[q], wr, wv) == reg_pick(cb[q], wr, wv)) == ceq[q]);
+    u64 w = 0;
+#pragma unroll
+    for (int q = 0; q < NOUT; q++) w |= reg_pick(out_op[q], wr, wv) << out_sh[q];
+    if constexpr (kMode == 2) {
+      if (ok) atomicOr(P.bitmap + (w >> 5), 1u << (u32)(w & 31u));
+    } else {
+      if (!ok) w = P.out_w64 ? ~0ull : 0xFFFFFFFFull;
+      const u64 o = base + t;
+      if (P.out_w64) reinterpret_cast<u64*>(P.out_words)[o] = w;
+      else reinterpret_cast<u32*>(P.out_words)[o] = (u32)w;
+    }
+  }
+}
+
+// kMode 0: binding words, row block b's outputs from blk_off[b] on, its groups
+// in (round, warp) order.  kMode 2: bitmap bits only; *emitted counts outputs.
+template <int kMode, int NOUT, int NCHK>
+__global__ void __launch_bounds__(256) k_pwarp_emit(const __grid_constant__ PStep P, const u64* __restrict__ blk_off,
+                                                    u64 n_blk, unsigned long long* emitted) {
+  RegOp out_op[NOUT];
+  u32 out_sh[NOUT];
+#pragma unroll
+  for (int q = 0; q < NOUT; q++) {
+    out_op[q] = reg_op(P.out[q].op);
+    out_sh[q] = P.out[q].shift;
+  }
+  RegOp ca[NCHK > 0 ? NCHK : 1], cb[NCHK > 0 ? NCHK : 1];
+  bool ceq[NCHK > 0 ? NCHK : 1];
+#pragma unroll
+  for (int q = 0; q < NCHK; q++) {
+    ca[q] = reg_op(P.checks[q].a);
+    cb[q] = reg_op(P.checks[q].b);
+    ceq[q] = P.checks[q].eq != 0;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if constexpr (kMode == 2) {
+    const u64 nwarps = (u64)gridDim.x * (blockDim.x / 32);
+    u64 mine = 0;
+    for (u64 g = (u64)blockIdx.x * (blockDim.x / 32) + warp; g * 32 < P.n_in; g += nwarps) {
+      u64 wi;
+      u32 lo;
+      const u32 c = probe_row(P, g * 32 + lane, wi, lo);
+      const u32 inc = warp_inclusive_sum(c);
+      const u32 tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+      if (!tot) continue;
+      mine += tot;
+      warp_expand<2, NOUT, NCHK>(P, out_op, out_sh, ca, cb, ceq, wi, lo, inc - c, tot, 0);
+    }
+    if (lane == 0 && mine) atomicAdd(emitted, (unsigned long long)mine);
+  } else {
+    __shared__ u32 gsum[32];
+    for (u64 b = blockIdx.x; b < n_blk; b += gridDim.x) {
+      u64 wi[4];
+      u32 lo[4], ex[4], tot[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const u32 c = probe_row(P, b * kWarpBlockRows + (u64)i * 256 + warp * 32 + lane, wi[i], lo[i]);
+        const u32 inc = warp_inclusive_sum(c);
+        ex[i] = inc - c;
+        tot[i] = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        if (lane == 0) gsum[i * 8 + warp] = tot[i];
+      }
+      __syncthreads();
+      if (warp == 0) {  // exclusive scan of the 32 group totals, in (round, warp) order
+        const u32 v = gsum[lane];
+        const u32 inc = warp_inclusive_sum(v);
+        __syncwarp();
+        gsum[lane] = inc - v;
+      }
+      __syncthreads();
+      const u64 bbase = blk_off[b];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        if (tot[i]) warp_expand<0, NOUT, NCHK>(P, out_op, out_sh, ca, cb, ceq, wi[i], lo[i], ex[i], tot[i], bbase + gsum[i * 8 + warp]);
+      __syncthreads();  // gsum is rewritten by the next block
+    }
+  }
+}
+
 unsigned grid_n(u64 n) {
   u64 b = (n + 255) / 256;
   if (b > 152ull * 16) b = 152ull * 16;
@@ -533,6 +711,15 @@ template <class Sem> struct PEmitL {
     }
   }
 };
+template <int M>
+bool try_warp(const PStep& P, unsigned grid, const u64* blk_off, u64 n_blk, unsigned long long* emitted, cudaStream_t st) {
+  const int no = P.n_out, nc = P.n_checks;
+#define LOB_WARP(NO, NC) if (no == NO && nc == NC) { k_pwarp_emit<M, NO, NC><<<grid, 256, 0, st>>>(P, blk_off, n_blk, emitted); return true; }
+  LOB_WARP(1, 0) LOB_WARP(2, 0) LOB_WARP(3, 0) LOB_WARP(4, 0)
+  LOB_WARP(1, 1) LOB_WARP(2, 1) LOB_WARP(3, 1) LOB_WARP(4, 1)
+#undef LOB_WARP
+  return false;
+}
 template <class Sem> struct PProjL {
   static void go(const PStep& P, cudaStream_t st) { k_pproject<Sem><<<grid_n(P.n_in), 256, 0, st>>>(P); }
 };
@@ -569,4 +756,31 @@ void pjoin_emit(int sem, const PStep& P, const u64* part, cudaStream_t st) {
 void pjoin_project(int sem, const PStep& P, cudaStream_t st) {
   ProfScope ps("project", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + row_bytes(sem, P.out_w64, false)), st);
   if (P.n_in) by_sem_p<PProjL>(sem, P, st);
+}
+
+bool pjoin_warp_supported(int sem, const PStep& P) {
+  return sem == SR_UNIT && P.n_out >= 1 && P.n_out <= 4 && P.n_checks <= 1;
+}
+
+u64 pjoin_warp_blocks(u64 n_in) { return (n_in + kWarpBlockRows - 1) / kWarpBlockRows; }
+
+void pjoin_warp_count(const PStep& P, u64* blk_cnt, cudaStream_t st) {
+  const u64 n_blk = pjoin_warp_blocks(P.n_in);
+  ProfScope ps("join_count", P.n_in * (P.in_w64 ? 8.0 : 4.0) + n_blk * 8.0, st);
+  if (n_blk) k_pwarp_count<<<(unsigned)(n_blk < 152ull * 16 ? n_blk : 152ull * 16), 256, 0, st>>>(P, blk_cnt, n_blk);
+}
+
+void pjoin_warp_emit(const PStep& P, u64 total, const u64* blk_off, cudaStream_t st) {
+  const double vb = P.v_key64 ? 8 : 4;
+  ProfScope ps("join_emit", P.n_in * (P.in_w64 ? 8.0 : 4.0) + total * (vb + (P.out_w64 ? 8 : 4)), st);
+  const u64 n_blk = pjoin_warp_blocks(P.n_in);
+  if (n_blk) try_warp<0>(P, (unsigned)(n_blk < 152ull * 16 ? n_blk : 152ull * 16), blk_off, n_blk, nullptr, st);
+}
+
+void pjoin_warp_bitmap(const PStep& P, u64* emitted_dev, cudaStream_t st) {
+  // the outputs' bytes (a matched key read and a bitmap word per output) are
+  // added by the caller once their number is known
+  ProfScope ps("join_emit", P.n_in * (P.in_w64 ? 8.0 : 4.0), st);
+  if (!P.n_in) return;
+  try_warp<2>(P, grid_n(P.n_in), nullptr, 0, reinterpret_cast<unsigned long long*>(emitted_dev), st);
 }

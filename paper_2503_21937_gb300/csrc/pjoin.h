@@ -57,3 +57,15 @@ void pjoin_count(int sem, const PStep& P, cudaStream_t st);
 void pjoin_partition(const PStep& P, u64 ntiles, u64* part, cudaStream_t st);
 void pjoin_emit(int sem, const PStep& P, const u64* part, cudaStream_t st);
 void pjoin_project(int sem, const PStep& P, cudaStream_t st);
+
+// Warp-balanced steps (unit semiring).  pjoin_warp_supported: the step has a
+// specialised warp kernel.  pjoin_warp_count: outputs per block of 1024 input
+// rows (pjoin_warp_blocks(n_in) entries); after an exclusive scan of them into
+// blk_off, pjoin_warp_emit writes the step's binding words at [0, total).
+// pjoin_warp_bitmap: last step, only sets the bits of P.bitmap and adds the
+// step's outputs to *emitted_dev.
+bool pjoin_warp_supported(int sem, const PStep& P);
+u64 pjoin_warp_blocks(u64 n_in);
+void pjoin_warp_count(const PStep& P, u64* blk_cnt, cudaStream_t st);
+void pjoin_warp_emit(const PStep& P, u64 total, const u64* blk_off, cudaStream_t st);
+void pjoin_warp_bitmap(const PStep& P, u64* emitted_dev, cudaStream_t st);

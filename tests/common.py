@@ -2,9 +2,27 @@
 the same seeded inputs and compare."""
 from __future__ import annotations
 
+import hashlib
+
 import numpy as np
 
 import oracle
+
+_ORACLE_CACHE: dict = {}
+
+
+def _digest(program: str, inputs: dict, semiring: str) -> str:
+    h = hashlib.sha256(program.encode() + semiring.encode())
+    for k in sorted(inputs):
+        h.update(k.encode())
+        for part in inputs[k]:
+            if part is None:
+                h.update(b"none")
+                continue
+            for a in (part if isinstance(part, (tuple, list)) else (part,)):
+                a = np.ascontiguousarray(a)
+                h.update(str(a.dtype).encode() + str(a.shape).encode() + a.tobytes())
+    return h.hexdigest()
 
 
 def engine_run(program: str, inputs: dict, semiring: str = "unit", max_iters: int = 1 << 30, options=None,
@@ -27,6 +45,15 @@ def engine_run(program: str, inputs: dict, semiring: str = "unit", max_iters: in
 
 
 def oracle_run(program: str, inputs: dict, semiring: str = "unit"):
+    """The oracle's result, memoised per process on (program, inputs, semiring)
+    so parametrised engine tests of one instance run the oracle once."""
+    key = _digest(program, inputs, semiring)
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = _oracle_run(program, inputs, semiring)
+    return _ORACLE_CACHE[key]
+
+
+def _oracle_run(program: str, inputs: dict, semiring: str = "unit"):
     return oracle.run(program, {k: (v[0], None if (len(v) < 2 or v[1] is None) else np.asarray(v[1], np.float32)
                                     .astype(np.float64), v[2] if len(v) > 2 else None)
                                 for k, v in inputs.items()}, semiring)

@@ -239,3 +239,22 @@ def test_bitmap_delta(mode):
     # 34-bit keys (u64 words, 2 GB bitmaps)
     s, d = W.erdos_renyi(70000, 140000, seed_index=173)
     compare(W.TC_PROGRAM, {"edge": ((s[:3000], d[:3000]),)}, options=opts)
+
+
+# ---------------------------------------------------------------------------
+# warp-balanced join steps (unit semiring) with and without the bitmap delta
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("warp_join", [0, 1])
+@pytest.mark.parametrize("bitmap_delta", [0, 2])
+def test_warp_join(warp_join, bitmap_delta):
+    opts = {"warp_join": warp_join, "bitmap_delta": bitmap_delta}
+    parent, child, _ = W.random_tree(3000, seed_index=180)
+    compare(W.SG_PROGRAM, {"parent": ((parent, child),)}, options=opts)
+    s, d = W.chung_lu_power_law(3000, 15000, seed_index=181)  # hub rows with thousands of matches
+    compare(W.TC_PROGRAM, {"edge": ((s, d),)}, options=opts)
+    A = W.andersen_program(3000, 9000, seed_index=182)
+    compare(W.ANDERSEN_PROGRAM, {k: ((v[0], v[1]),) for k, v in A.items()}, rels=["pt"], options=opts)
+    n, r, a, b, p = W.kinship_instance(W.stream(183))
+    c1, c2, c3 = W.composition_table()
+    compare(W.KIN_PROGRAM, {"fact": ((r, a, b),), "comp": ((c1, c2, c3),)}, rels=["kin"], options=opts)
