@@ -154,6 +154,13 @@ def cpu_oracle_sample(budget_s: float = 20.0):
                       f"{dt:.1f} s"}
 
 
+def base_config(world: int = 1) -> dict:
+    """The workload description both arms report."""
+    return {"workload": WORKLOAD, "sg_tree_nodes": SG_NODES, "tc_nodes": TC_NODES, "tc_edges": TC_EDGES,
+            "semiring": "unit", "parallelism": "replicas" if world > 1 else "1 GPU",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -180,7 +187,7 @@ def reference_arm(args):
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic", "config": {"workload": WORKLOAD + " [oracle sample]"},
+                      "data": "synthetic", "config": base_config(),
                       "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
                       "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
@@ -455,11 +462,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "sg_tree_nodes": SG_NODES, "tc_nodes": TC_NODES,
-                           "tc_edges": TC_EDGES, "semiring": "unit", "parallelism": "replicas" if world > 1 else "1 GPU",
-                           "l2": "flushed between timed steps (256 MiB write)",
-                           "derived_per_step": derived[0], "iterations": iters, "join_outputs": cands,
-                           "engine_options": args.option},
+                "config": {**base_config(world), "derived_per_step": derived[0], "iterations": iters,
+                           "join_outputs": cands, "engine_options": args.option},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "kernels": kernels, "kernels_by_workload": by_workload, "batched": batched}
         print(json.dumps(line))

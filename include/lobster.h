@@ -166,9 +166,9 @@ int lob_reset(lob_engine* e);
  *   "packed_join"  1: join kernels on packed words when an arm's bindings
  *                  fit 64 bits; 0: the general kernels               (default 1)
  *   "warp_join"    1: unit-semiring packed join steps expand 32 input rows
- *                  per warp (no per-row offsets; intermediate binding rows
- *                  in no particular order); 0: count / offsets / tile
- *                  emission for every step                           (default 1)
+ *                  per warp (no per-row offsets); 2: only bitmap-only last
+ *                  steps do; 0: count / offsets / tile emission for every
+ *                  step                                              (default 1)
  *   "bitmap_delta" relations with a membership filter: 2 = the joins only
  *                  set bits and each iteration's new facts are read, in key
  *                  order, out of the bitmap and its start-of-iteration copy;

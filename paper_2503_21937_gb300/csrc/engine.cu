@@ -1096,7 +1096,7 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
       }
       return;
     }
-    if (!last && warp && W.n < (1ull << 22)) {  // binding words placed per block of input rows
+    if (!last && warp && e.opt_warp_join == 1 && W.n < (1ull << 22)) {  // binding words placed per block of input rows
       const u64 n_blk = pjoin_warp_blocks(n_in);
       e.ensure(e.off, n_blk * 16);
       pjoin_warp_count(P, e.off.as<u64>() + n_blk, e.stream);
@@ -1977,7 +1977,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "sort_algo" && (value == 0 || value == 1)) e->opt_sort_algo = (int)value;
     else if (k == "packed_join" && (value == 0 || value == 1)) e->opt_packed_join = (int)value;
     else if (k == "bitmap_delta" && value >= 0 && value <= 2) e->opt_bitmap_delta = (int)value;
-    else if (k == "warp_join" && (value == 0 || value == 1)) e->opt_warp_join = (int)value;
+    else if (k == "warp_join" && value >= 0 && value <= 2) e->opt_warp_join = (int)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });
