@@ -120,6 +120,33 @@ int lob_add_rule(lob_engine* e, const char* text);
  * call needs lob_reset first (LOB_E_STATE).  `stats` may be NULL. */
 int lob_run_to_fixpoint(lob_engine* e, int semiring, uint32_t max_iters, lob_stats* stats);
 
+/* Options chosen by lob_autotune and the timings behind them. */
+typedef struct lob_tune_report {
+  int32_t packed_join, warp_join, bitmap_delta, join_index, radix_bits, emit_filter;
+  uint32_t trials;  /* fixpoint runs timed (warm-up excluded) */
+  double first_ms;  /* median run time with the options in force when called */
+  double best_ms;   /* median run time with the chosen options */
+} lob_tune_report;
+
+/* Autotuner for the loaded program (not part of the paper's method).  It picks
+ * the engine's strategy options for this program and these inputs by running
+ * the fixpoint under candidate settings and timing each run on the engine's
+ * stream (CUDA events).  The search is coordinate descent over these knobs:
+ *   - packed_join: packed-word vs general join steps;
+ *   - join_index: dense offset table vs binary search;
+ *   - radix_bits: the sort's digit width;
+ *   - for the unit semiring also warp_join (warp-balanced vs tile emission),
+ *     bitmap_delta (bitmap read-out vs sorted candidates) and emit_filter
+ *     (membership filter).
+ * Each setting runs `repeats` times (0 = 1) and scores its median run time; a
+ * change must win by 2 %.  All settings compute the same relations, so only
+ * time decides.  The engine must be loaded and not yet run (LOB_E_STATE
+ * otherwise).  On return the chosen options are set, the inputs stay loaded and
+ * lob_run_to_fixpoint runs next.  A trial that fails (LOB_E_MAXITER, LOB_E_OOM,
+ * ...) ends the search with its status, and the options in force at the call
+ * are restored.  `report` may be NULL. */
+int lob_autotune(lob_engine* e, int semiring, uint32_t max_iters, uint32_t repeats, lob_tune_report* report);
+
 /* Number of facts of `rel` after the run (or after loading, before it). */
 int lob_relation_size(lob_engine* e, uint32_t rel, uint64_t* n);
 

@@ -1767,6 +1767,94 @@ int lob_run_to_fixpoint(lob_engine* e, int semiring, uint32_t max_iters, lob_sta
   return guarded(e, [&] { return run_fixpoint(*e, semiring, max_iters, stats); });
 }
 
+// ---------------------------------------------------------------------------
+// autotuner: coordinate descent over strategy options, timed fixpoint runs
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneKnob {
+  int* field;
+  std::vector<int> values;
+};
+}  // namespace
+
+static int autotune(lob_engine& e, int sem, u32 max_iters, u32 repeats, lob_tune_report* rep) {
+  if (e.state != 0) throw LobError(LOB_E_STATE, "autotune a loaded engine before lob_run_to_fixpoint");
+  if (sem < 0 || sem > 4) throw LobError(LOB_E_ARG, "unknown semiring id");
+  if (!repeats) repeats = 1;
+  std::vector<TuneKnob> knobs = {{&e.opt_packed_join, {1, 0}}, {&e.opt_join_index, {0, 1, 2}}, {&e.opt_radix_bits, {8, 6}}};
+  if (sem == SR_UNIT) {
+    knobs.push_back({&e.opt_warp_join, {1, 2, 0}});
+    knobs.push_back({&e.opt_bitmap_delta, {1, 2, 0}});
+    knobs.push_back({&e.opt_emit_filter, {1, 2, 0}});
+  }
+  std::vector<int> saved;
+  for (auto& k : knobs) saved.push_back(*k.field);
+  u32 trials = 0;
+  auto one_run = [&]() -> double {
+    lob_stats st{};
+    int rc;
+    try {
+      rc = run_fixpoint(e, sem, max_iters, &st);
+    } catch (...) {
+      release_derived(e);
+      e.state = 0;
+      throw;
+    }
+    release_derived(e);
+    e.state = 0;
+    e.ran_diff = false;
+    if (rc != LOB_OK) throw LobError(rc, "autotune: a trial run did not reach the fixpoint");
+    return st.ms;
+  };
+  auto score = [&]() -> double {
+    std::vector<double> ms;
+    for (u32 r = 0; r < repeats; r++) {
+      ms.push_back(one_run());
+      trials++;
+    }
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+  };
+  try {
+    one_run();  // warm-up: first-touch allocations and kernel attributes
+    const double first = score();
+    double best = first;
+    for (auto& k : knobs) {
+      const int cur = *k.field;
+      int keep = cur;
+      for (int v : k.values) {
+        if (v == cur) continue;
+        *k.field = v;
+        const double t = score();
+        if (t < best * 0.98) {
+          best = t;
+          keep = v;
+        }
+      }
+      *k.field = keep;
+    }
+    if (rep) {
+      rep->packed_join = e.opt_packed_join;
+      rep->warp_join = e.opt_warp_join;
+      rep->bitmap_delta = e.opt_bitmap_delta;
+      rep->join_index = e.opt_join_index;
+      rep->radix_bits = e.opt_radix_bits;
+      rep->emit_filter = e.opt_emit_filter;
+      rep->trials = trials;
+      rep->first_ms = first;
+      rep->best_ms = best;
+    }
+  } catch (...) {
+    for (size_t i = 0; i < knobs.size(); i++) *knobs[i].field = saved[i];
+    throw;
+  }
+  return LOB_OK;
+}
+
+int lob_autotune(lob_engine* e, int semiring, uint32_t max_iters, uint32_t repeats, lob_tune_report* report) {
+  return guarded(e, [&] { return autotune(*e, semiring, max_iters, repeats, report); });
+}
+
 int lob_relation_size(lob_engine* e, uint32_t rel, uint64_t* n) {
   return guarded(e, [&] {
     if (rel >= e->rels.size()) throw LobError(LOB_E_UNKNOWN_REL, "unknown relation id");

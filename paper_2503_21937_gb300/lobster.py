@@ -31,7 +31,7 @@ EXPORTS = ["lob_create", "lob_destroy", "lob_last_error", "lob_declare_relation"
            "lob_load_relation", "lob_add_rule", "lob_run_to_fixpoint", "lob_relation_size", "lob_read_relation",
            "lob_backward", "lob_reset", "lob_set_option", "lob_profile_count", "lob_profile_entry",
            "lob_profile_reset", "lob_prim_sort", "lob_prim_exclusive_scan", "lob_prim_unique",
-           "lob_prim_diff_merge", "lob_unique_rows_noalloc"]
+           "lob_prim_diff_merge", "lob_unique_rows_noalloc", "lob_autotune"]
 NOALLOC_MAX_ROWS = 262144
 
 _lib = None
@@ -47,6 +47,15 @@ class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_uint32), ("semiring", ctypes.c_uint32), ("derived", ctypes.c_uint64),
                 ("candidates", ctypes.c_uint64), ("new_facts", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
                 ("ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("packed_join", ctypes.c_int32), ("warp_join", ctypes.c_int32), ("bitmap_delta", ctypes.c_int32),
+                ("join_index", ctypes.c_int32), ("radix_bits", ctypes.c_int32), ("emit_filter", ctypes.c_int32),
+                ("trials", ctypes.c_uint32), ("first_ms", ctypes.c_double), ("best_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -71,6 +80,7 @@ def load_library(path: str = LIB_PATH):
     lib.lob_load_relation.argtypes = [vp, u32, vp, vp, vp, u64, ctypes.c_int]
     lib.lob_add_rule.argtypes = [vp, ctypes.c_char_p]
     lib.lob_run_to_fixpoint.argtypes = [vp, ctypes.c_int, u32, P(Stats)]
+    lib.lob_autotune.argtypes = [vp, ctypes.c_int, u32, u32, P(TuneReport)]
     lib.lob_relation_size.argtypes = [vp, u32, P(u64)]
     lib.lob_read_relation.argtypes = [vp, u32, vp, vp, vp, u64, P(u64), ctypes.c_int]
     lib.lob_backward.argtypes = [vp, u32, vp, vp, ctypes.c_int]
@@ -222,6 +232,14 @@ class Engine:
         st = Stats()
         self._chk(self.lib.lob_run_to_fixpoint(self.h, sr, max_iters, ctypes.byref(st)))
         return st.as_dict()
+
+    def autotune(self, semiring="unit", max_iters: int = 1 << 30, repeats: int = 3) -> dict:
+        """lob_autotune: choose strategy options for the loaded program by timed
+        fixpoint runs; the inputs stay loaded and run() comes next."""
+        sr = SEMIRINGS[semiring] if isinstance(semiring, str) else int(semiring)
+        rep = TuneReport()
+        self._chk(self.lib.lob_autotune(self.h, sr, max_iters, repeats, ctypes.byref(rep)))
+        return rep.as_dict()
 
     def size(self, name: str) -> int:
         n = ctypes.c_uint64()

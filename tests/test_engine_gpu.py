@@ -258,3 +258,40 @@ def test_warp_join(warp_join, bitmap_delta):
     n, r, a, b, p = W.kinship_instance(W.stream(183))
     c1, c2, c3 = W.composition_table()
     compare(W.KIN_PROGRAM, {"fact": ((r, a, b),), "comp": ((c1, c2, c3),)}, rels=["kin"], options=opts)
+
+
+# ---------------------------------------------------------------------------
+# autotuner: timed trials, then a normal run with the chosen options
+# ---------------------------------------------------------------------------
+
+def test_autotune_then_run_matches_oracle():
+    from paper_2503_21937_gb300 import Engine, LobsterError
+    from tests.common import oracle_run
+    s, d = W.chung_lu_power_law(1500, 6000, seed_index=190)
+    e = Engine()
+    e.program(W.TC_PROGRAM)
+    e.load("edge", (s, d))
+    rep = e.autotune("unit", repeats=1)
+    assert rep["trials"] >= 1 + 1 + 2 + 1 + 2 + 2 + 2  # the first setting + every alternative of 6 knobs
+    assert 0 < rep["best_ms"] <= rep["first_ms"]
+    assert rep["warp_join"] in (0, 1, 2) and rep["bitmap_delta"] in (0, 1, 2) and rep["radix_bits"] in (6, 8)
+    e.run("unit")
+    want = oracle_run(W.TC_PROGRAM, {"edge": ((s, d),)}).relation("path")
+    assert np.array_equal(e.read("path").cols, want.cols)
+    with pytest.raises(LobsterError, match="STATE"):
+        e.autotune("unit")
+    e.close()
+    g = W.grid_reach_instance(16, sub=191)
+    src, dst, p = g["edge"]
+    inputs = {"edge": ((src, dst), p), "start": (g["start"],)}
+    e = Engine()
+    e.program(W.REACH_PROGRAM)
+    e.load("edge", (src, dst), np.asarray(p, np.float32))
+    e.load("start", g["start"])
+    rep = e.autotune("max_min", repeats=1)
+    assert rep["trials"] == 1 + 1 + 2 + 1  # semirings with tags tune packed_join, join_index, radix_bits
+    e.run("max_min")
+    want = oracle_run(W.REACH_PROGRAM, inputs, "max_min").relation("reach")
+    got = e.read("reach")
+    assert np.array_equal(got.cols, want.cols) and np.array_equal(got.tags, want.tags.astype(np.float32))
+    e.close()
