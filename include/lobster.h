@@ -175,9 +175,11 @@ int lob_backward(lob_engine* e, uint32_t out_rel, const float* grad_tags, float*
 int lob_reset(lob_engine* e);
 
 /* Engine options (key, value):
- *   "join_index"   0 auto, 1 dense offset table, 2 binary search   (default 0)
+ *   "join_index"   0 dense offset table up to dense_bits, else binary
+ *                  search; 1 dense up to 30 bits; 2 binary search  (default 0)
  *   "dense_bits"   largest join-prefix width, in bits, indexed densely (default 24)
- *   "radix_bits"   bits per radix-sort pass, 4..11                  (default 8)
+ *   "radix_bits"   bits per radix-sort pass: 4, 6 or 8 (other values
+ *                  in 4..11 select 8)                                (default 8)
  *   "sync_check"   1: check CUDA errors after every kernel (debug)   (default 0)
  *   "profile"      1: time every kernel launch with CUDA events      (default 0)
  *   "max_candidates" candidates sorted at once; larger candidate sets are
@@ -199,9 +201,11 @@ int lob_reset(lob_engine* e);
  *   "bitmap_delta" relations with a membership filter: 2 = the joins only
  *                  set bits and each iteration's new facts are read, in key
  *                  order, out of the bitmap and its start-of-iteration copy;
- *                  1 = that whenever the last iteration's new facts
- *                  outnumber bitmap bytes / 64; 0 = never (candidates are
- *                  sorted and merged)                                (default 1)
+ *                  1 = per iteration, whichever a traffic model predicts
+ *                  cheaper: reading the two bitmaps, or sorting the
+ *                  predicted new facts (the last iteration's count) and
+ *                  merging them / reading the relation's keys out first;
+ *                  0 = never (candidates are sorted and merged)      (default 1)
  * LOB_E_ARG for an unknown key or a value out of range. */
 int lob_set_option(lob_engine* e, const char* key, int64_t value);
 
