@@ -28,7 +28,11 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.cpp")
-_LIB = os.path.join(_HERE, "liboracle.so")
+# ORACLE_MUTANT=k (k > 0) selects a library with one deliberate mistake compiled
+# in (oracle.cpp lists them); only tests/test_oracle_mutants.py sets it, to show
+# that the pins catch each mistake.  Unset: the oracle itself.
+_MUTANT = int(os.environ.get("ORACLE_MUTANT", "0"))
+_LIB = os.path.join(_HERE, "liboracle.so" if _MUTANT == 0 else f"liboracle_mutant{_MUTANT}.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -39,7 +43,8 @@ def build(force: bool = False) -> str:
     """Compile oracle.cpp into liboracle.so (g++, no GPU code)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC], check=True)
+        subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", f"-DORACLE_MUTANT={_MUTANT}", "-o", tmp, _SRC],
+                       check=True)
         os.replace(tmp, _LIB)
     return _LIB
 

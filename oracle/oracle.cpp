@@ -36,6 +36,13 @@
 //
 // Batched inputs (Sec. 4.3): facts carry a sample id and samples never join; the
 // oracle states that directly by running the fixpoint once per sample.
+//
+// ORACLE_MUTANT (default 0, the oracle itself): a positive value compiles one
+// deliberate, plausible mistake into a separate library, so that
+// tests/test_oracle_mutants.py can show that the pins of tests/test_oracle_pins.py
+// catch it.  The mutants (a wrong operator, a dropped term, a transposed operand,
+// a missing clamp, a wrong tie-break or policy, a skipped check, early stopping,
+// samples that join) are listed at each #if below.
 #include <algorithm>
 #include <array>
 #include <cctype>
@@ -47,6 +54,10 @@
 #include <set>
 #include <string>
 #include <vector>
+
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
 
 namespace {
 
@@ -200,6 +211,9 @@ struct Parser {
 // a "greater than" b in the diff-max-min order: larger value, then smaller id.
 bool dmm_greater(const Tag& a, const Tag& b) {
   if (a.v != b.v) return a.v > b.v;
+#if ORACLE_MUTANT == 3  // mutant: ties go to the larger input-fact id
+  return a.id > b.id;
+#endif
   return a.id < b.id;
 }
 
@@ -207,13 +221,23 @@ Tag otimes(int sr, const Tag& a, const Tag& b) {
   Tag r;
   switch (sr) {
     case UNIT: r.v = 1.0; break;
+#if ORACLE_MUTANT == 1  // mutant: max-min (x) takes the larger tag
+    case MAX_MIN: r.v = std::max(a.v, b.v); break;
+#else
     case MAX_MIN: r.v = std::min(a.v, b.v); break;
+#endif
     case ADD_MULT: r.v = a.v * b.v; break;
+#if ORACLE_MUTANT == 12  // mutant: diff-max-min (x) keeps the greater operand
+    case DIFF_MAX_MIN: r = dmm_greater(a, b) ? a : b; break;
+#else
     case DIFF_MAX_MIN: r = dmm_greater(a, b) ? b : a; break;
+#endif
     case DIFF_ADD_MULT:
       r.v = a.v * b.v;
       for (auto& kv : a.d) r.d[kv.first] += b.v * kv.second;
+#if ORACLE_MUTANT != 4  // mutant 4: the product rule's second term is dropped
       for (auto& kv : b.d) r.d[kv.first] += a.v * kv.second;
+#endif
       break;
   }
   return r;
@@ -254,8 +278,16 @@ void acc_add(int sr, Acc& acc, const Tag& g) {
 Tag acc_value(int sr, const Acc& acc) {
   if (sr == ADD_MULT || sr == DIFF_ADD_MULT) {
     Tag r;
+#if ORACLE_MUTANT == 2  // mutant: (+) without the clamp to 1
+    r.v = acc.sum;
+#else
     r.v = std::min(1.0, acc.sum);
+#endif
+#if ORACLE_MUTANT == 5  // mutant: the derivative survives a clamped (+)
+    if (sr == DIFF_ADD_MULT) r.d = acc.dsum;
+#else
     if (sr == DIFF_ADD_MULT && !(acc.sum > 1.0)) r.d = acc.dsum;  // clamped: derivative 0
+#endif
     return r;
   }
   return acc.t;
@@ -312,7 +344,11 @@ struct Engine {
     }
     std::function<void(size_t)> rec = [&](size_t j) {
       if (j == r.body.size()) {
+#if ORACLE_MUTANT == 6  // mutant: the rule's ==/!= filters are ignored
+        for (const Filter& f : std::vector<Filter>()) {
+#else
         for (const Filter& f : r.filters) {
+#endif
           uint32_t x = f.a.is_var ? val[f.a.value] : f.a.value;
           uint32_t y = f.b.is_var ? val[f.b.value] : f.b.value;
           if ((x == y) != f.equal) return;
@@ -320,6 +356,9 @@ struct Engine {
         Tuple h{};
         for (size_t c = 0; c < r.head.args.size(); c++)
           h[c] = r.head.args[c].is_var ? val[r.head.args[c].value] : r.head.args[c].value;
+#if ORACLE_MUTANT == 11  // mutant: the first two head columns are transposed
+        if (r.head.args.size() >= 2) std::swap(h[0], h[1]);
+#endif
         emit(h, tags);
         return;
       }
@@ -335,7 +374,9 @@ struct Engine {
           const Term& t = a.args[c];
           if (!t.is_var) continue;  // constants were part of the index key
           if (bound[t.value]) {
+#if ORACLE_MUTANT != 7  // mutant 7: a variable bound earlier is not compared
             if (val[t.value] != f->first[c]) ok = false;
+#endif
           } else {
             bound[t.value] = 1;
             val[t.value] = f->first[c];
@@ -354,7 +395,11 @@ struct Engine {
 
   // returns 0 on fixpoint, -2 when max_iters iterations did not reach it
   int run(uint32_t max_iters) {
+#if ORACLE_MUTANT == 9  // mutant: max-min keeps the first tag of a key (key policy)
+    const bool key_policy = (sr == ADD_MULT || sr == DIFF_ADD_MULT || sr == MAX_MIN);
+#else
     const bool key_policy = (sr == ADD_MULT || sr == DIFF_ADD_MULT);
+#endif
     for (uint32_t it = 0; it < max_iters; it++) {
       std::map<std::string, std::map<Tuple, Acc>> derived;
       for (const Rule& r : rules) {
@@ -394,6 +439,9 @@ struct Engine {
         }
       }
       iterations = (int)it + 1;
+#if ORACLE_MUTANT == 8  // mutant: stops after the second iteration
+      if (it == 1) return 0;
+#endif
       if (!changed) return 0;
     }
     return -2;
@@ -459,7 +507,11 @@ int orc_run(const char* program, int semiring, int n_inputs, const char* const* 
     for (uint64_t r = 0; r < nrows[k]; r++) {
       Tuple t{};
       for (uint32_t c = 0; c < arities[k]; c++) t[c] = cols[k][c * nrows[k] + r];
+#if ORACLE_MUTANT == 10  // mutant: sample ids are ignored, so samples join
+      uint32_t s = 0;
+#else
       uint32_t s = samples && samples[k] ? samples[k][r] : 0;
+#endif
       Tag g;
       g.v = tags && tags[k] ? tags[k][r] : 1.0;
       if (semiring == UNIT) g.v = 1.0;

@@ -315,3 +315,29 @@ def test_maxmin_gradient_matches_finite_differences():
         return d.min() < 2e-6
 
     _fd_check(W.REACH_PROGRAM, inputs, "reach", "diff_max_min", gout, range(len(src)), skip=near_tie)
+
+
+def test_addmult_gradient_is_zero_through_a_clamped_sum():
+    """(+) = min(1, a + b): an output whose summed derivations exceed 1 strictly
+    is flat in every input, so its FP64 central differences are 0, while the
+    unclamped outputs keep theirs.  Source 0 -> k middle nodes -> target, every
+    edge probability 0.9: the target sums k * 0.81 > 1 for k >= 2."""
+    k = 4
+    mid = np.arange(1, k + 1, dtype=np.uint32)
+    src = np.concatenate([np.zeros(k, np.uint32), mid])
+    dst = np.concatenate([mid, np.full(k, k + 1, np.uint32)])
+    p = np.full(2 * k, 0.9)
+    inputs = {"edge": ((src, dst), p), "start": ((np.array([0], np.uint32),),)}
+    res = oracle.run(W.REACH_PROGRAM, inputs, "add_mult")
+    reach = res.relation("reach")
+    assert reach.tags[list(reach.cols[0]).index(k + 1)] == 1.0  # clamped
+    n_out = reach.cols.shape[1]
+    target_only = np.zeros(n_out)
+    target_only[list(reach.cols[0]).index(k + 1)] = 1.0
+    _fd_check(W.REACH_PROGRAM, inputs, "reach", "diff_add_mult", target_only, range(len(src)))
+    grads = oracle.run(W.REACH_PROGRAM, inputs, "diff_add_mult").vjp({"reach": target_only})["edge"]
+    assert np.all(grads == 0.0)
+    # a middle node is unclamped: d t(m) / d p(0 -> m) = 1
+    middle_only = np.zeros(n_out)
+    middle_only[list(reach.cols[0]).index(1)] = 1.0
+    _fd_check(W.REACH_PROGRAM, inputs, "reach", "diff_add_mult", middle_only, range(len(src)))
