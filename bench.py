@@ -154,6 +154,22 @@ def cpu_oracle_sample(budget_s: float = 20.0):
                       f"{dt:.1f} s"}
 
 
+def max_over_ranks(ms: float, dist=None, device: str = "cuda") -> float:
+    """The job's time: the slowest rank's (all_reduce MAX); `ms` itself when
+    there is one process."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step: float, steps: int, world: int, job_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the job's time."""
+    return units_per_rank_step * steps * world / (job_ms / 1000.0)
+
+
 def base_config(world: int = 1) -> dict:
     """The workload description both arms report."""
     return {"workload": WORKLOAD, "sg_tree_nodes": SG_NODES, "tc_nodes": TC_NODES, "tc_edges": TC_EDGES,
@@ -381,13 +397,12 @@ def main():
             iters = {k: s["iterations"] for k, s in st.items()}
             cands = {k: s["candidates"] for k, s in st.items()}
     torch.cuda.synchronize()
-    clk = clocks.stop()
-    total_ms = sum(times)
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = derived[0] * args.steps * world / (total_ms / 1000.0)
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(sum(times), dist)
+    value = job_throughput(derived[0], args.steps, world, total_ms)
 
     # per-kernel CUDA-event timing on extra steps (not part of the timed value)
     prof = {}
