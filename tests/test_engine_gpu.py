@@ -239,6 +239,11 @@ def test_bitmap_delta(mode):
     # 34-bit keys (u64 words, 2 GB bitmaps)
     s, d = W.erdos_renyi(70000, 140000, seed_index=173)
     compare(W.TC_PROGRAM, {"edge": ((s[:3000], d[:3000]),)}, options=opts)
+    # batched: the sample id is the key's top field, so one bitmap spans all samples
+    B = W.batched_instance(6)
+    e = B["edge"]
+    compare(W.REACH_PROGRAM, {"edge": ((e[0], e[1]), None, e[3]), "start": ((B["start"][0],), None, B["start"][2])},
+            rels=["reach"], options=opts)
 
 
 # ---------------------------------------------------------------------------
