@@ -300,3 +300,14 @@ def test_autotune_then_run_matches_oracle():
     got = e.read("reach")
     assert np.array_equal(got.cols, want.cols) and np.array_equal(got.tags, want.tags.astype(np.float32))
     e.close()
+
+
+# ---------------------------------------------------------------------------
+# the paper's Pathfinder example (tests/golden/pathfinder_example.txt)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("semiring", ["unit", "max_min", "add_mult", "diff_max_min", "diff_add_mult"])
+def test_pathfinder_example(semiring):
+    from tests.golden.load import pathfinder_example
+    program, inputs = pathfinder_example()
+    compare(program, inputs, semiring)

@@ -341,3 +341,31 @@ def test_addmult_gradient_is_zero_through_a_clamped_sum():
     middle_only = np.zeros(n_out)
     middle_only[list(reach.cols[0]).index(1)] = 1.0
     _fd_check(W.REACH_PROGRAM, inputs, "reach", "diff_add_mult", middle_only, range(len(src)))
+
+
+# ----------------------------------------------------------------------------
+# the paper's printed example and semiring table (tests/golden/, cited there)
+# ----------------------------------------------------------------------------
+
+def test_pathfinder_example_from_the_paper():
+    from tests.golden.load import pathfinder_example, provenance_semirings
+    program, inputs = pathfinder_example()
+    table = provenance_semirings()
+    chain = [0.9, 0.8, 0.95, 0.85]
+    # Bool: the discrete result; 5 cannot reach 1, and x != y drops (x, x)
+    r = oracle.run(program, inputs, "unit")
+    assert rel_set(r.relation("connected")) == {(1, 5)}
+    assert (0, 1) in rel_set(r.relation("path")) and (1, 5) in rel_set(r.relation("path"))
+    # Max-Min-Prob: (x) = min along the single proof, (+) = max; endpoint facts
+    # carry the semiring's 1, the identity of min
+    assert table["max_min"]["otimes"] == "min" and table["max_min"]["one"] == 1.0
+    r = oracle.run(program, inputs, "max_min")
+    path = r.relation("path")
+    tag = dict(zip(map(tuple, path.cols.T.tolist()), path.tags.tolist()))
+    assert tag[(0, 1)] == 0.97  # the printed fact 0.97::edge(0, 1)
+    assert tag[(0, 5)] == min([0.97] + chain)
+    conn = r.relation("connected")
+    assert conn.tags.tolist() == [min(chain)]
+    # add-mult: the single proof's probability is the product of its facts
+    r = oracle.run(program, inputs, "add_mult")
+    assert r.relation("connected").tags[0] == pytest.approx(math.prod(chain), rel=1e-12)
