@@ -52,6 +52,14 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class LobAlloc(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("release", _RELEASE_FN), ("ctx", ctypes.c_void_p)]
+
+
 class TuneReport(ctypes.Structure):
     _fields_ = [("packed_join", ctypes.c_int32), ("warp_join", ctypes.c_int32), ("bitmap_delta", ctypes.c_int32),
                 ("join_index", ctypes.c_int32), ("radix_bits", ctypes.c_int32), ("emit_filter", ctypes.c_int32),
@@ -154,11 +162,20 @@ class Relation:
 class Engine:
     """One fixpoint engine on the current CUDA device."""
 
-    def __init__(self, stream=None):
+    def __init__(self, stream=None, allocator=None):
+        """allocator: optional (alloc(nbytes, stream) -> device pointer or 0,
+        release(ptr, nbytes, stream)) pair passed to lob_create as lob_alloc."""
         self.lib = load_library()
         self.h = ctypes.c_void_p()
         stream = _torch_stream() if stream is None else stream
-        rc = self.lib.lob_create(ctypes.byref(self.h), None, ctypes.c_void_p(stream) if stream else None)
+        alloc = None
+        if allocator is not None:
+            fa, fr = allocator
+            self._alloc_cbs = (_ALLOC_FN(lambda n, st, ctx: fa(n, st or 0) or None),
+                               _RELEASE_FN(lambda p, n, st, ctx: fr(p, n, st or 0)))
+            self._alloc_struct = LobAlloc(self._alloc_cbs[0], self._alloc_cbs[1], None)
+            alloc = ctypes.cast(ctypes.pointer(self._alloc_struct), ctypes.c_void_p)
+        rc = self.lib.lob_create(ctypes.byref(self.h), alloc, ctypes.c_void_p(stream) if stream else None)
         if rc != LOB_OK:
             raise LobsterError(rc, self.lib.lob_last_error(None).decode())
         self.ids = {}

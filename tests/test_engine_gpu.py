@@ -311,3 +311,73 @@ def test_pathfinder_example(semiring):
     from tests.golden.load import pathfinder_example
     program, inputs = pathfinder_example()
     compare(program, inputs, semiring)
+
+
+# ---------------------------------------------------------------------------
+# failure handling on the host side (no GPU fault): allocator refusal,
+# too-small read buffers; and run-to-run determinism despite atomics
+# ---------------------------------------------------------------------------
+
+def test_allocator_refusal_reports_oom_and_engine_stays_usable():
+    import torch
+    from paper_2503_21937_gb300 import Engine, LobsterError
+    from tests.common import oracle_run
+    budget = {"left": 1 << 16}
+    live = {}
+
+    def alloc(nbytes, stream):
+        if nbytes > budget["left"]:
+            return 0
+        p = torch.cuda.caching_allocator_alloc(nbytes, stream=stream)
+        budget["left"] -= nbytes
+        live[p] = nbytes
+        return p
+
+    def release(p, nbytes, stream):
+        torch.cuda.caching_allocator_delete(p)
+        budget["left"] += live.pop(p)
+
+    a, b = W.erdos_renyi(300, 1500, seed_index=200)
+    e = Engine(allocator=(alloc, release))
+    e.program(W.TC_PROGRAM)
+    e.load("edge", (a, b))
+    with pytest.raises(LobsterError, match="OOM"):
+        e.run("unit")
+    budget["left"] += 1 << 32
+    e.reset()
+    e.load("edge", (a, b))
+    e.run("unit")
+    want = oracle_run(W.TC_PROGRAM, {"edge": ((a, b),)}).relation("path")
+    assert np.array_equal(e.read("path").cols, want.cols)
+    e.close()
+    torch.cuda.synchronize()
+    assert not live  # every allocation was returned
+
+
+def test_read_capacity_error_reports_the_size():
+    import ctypes
+    from paper_2503_21937_gb300 import lobster
+    a, b = W.ktree_chain(40)
+    e, st, _ = engine_run(W.TC_PROGRAM, {"edge": ((a, b),)}, read=[])
+    n = ctypes.c_uint64()
+    cols = np.zeros((2, 5), np.uint32)
+    rc = e.lib.lob_read_relation(e.h, e.ids["path"], cols.ctypes.data, None, None, 5, ctypes.byref(n),
+                                 lobster.MEM_HOST)
+    assert lobster.ERRORS[rc] == "LOB_E_CAPACITY"
+    assert n.value == 40 * 39 // 2
+    e.close()
+
+
+def test_runs_are_bitwise_repeatable():
+    parent, child, _ = W.random_tree(4000, seed_index=201)
+    s, d = W.chung_lu_power_law(2000, 9000, seed_index=202)
+    for program, inputs, rel, sr in [(W.SG_PROGRAM, {"parent": ((parent, child),)}, "sg", "unit"),
+                                     (W.TC_PROGRAM, {"edge": ((s, d),)}, "path", "unit"),
+                                     (W.TC_PROGRAM, {"edge": ((s, d), W.stream(203).prob(len(s)))}, "path", "max_min")]:
+        outs = []
+        for _ in range(2):
+            e, st, got = engine_run(program, inputs, sr, read=[rel])
+            outs.append(got[rel])
+            e.close()
+        assert np.array_equal(outs[0].cols, outs[1].cols)
+        assert np.array_equal(outs[0].tags, outs[1].tags)
