@@ -230,3 +230,59 @@ def andersen_sparse(addr, assign, load, store, n_vars):
         if nxt.nnz == P.nnz:
             return nxt
         P = nxt
+
+
+def kinship_closure(r, a, b, comp):
+    """Least fixpoint of kin(r,x,y) :- fact(r,x,y) and
+    kin(r3,x,z) :- kin(r1,x,y), kin(r2,y,z), comp(r1,r2,r3), x != z
+    by a worklist over facts: each new fact is composed with every known fact
+    on either side (a different algorithm from naive iteration)."""
+    c1, c2, c3 = comp
+    table = defaultdict(list)
+    for p, q, s in zip(c1.tolist(), c2.tolist(), c3.tolist()):
+        table[(p, q)].append(s)
+    known = set()
+    by_src = defaultdict(set)  # x -> {(r, y)}
+    by_dst = defaultdict(set)  # y -> {(r, x)}
+    work = deque()
+
+    def add(f):
+        if f in known:
+            return
+        known.add(f)
+        by_src[f[1]].add((f[0], f[2]))
+        by_dst[f[2]].add((f[0], f[1]))
+        work.append(f)
+
+    for f in zip(r.tolist(), a.tolist(), b.tolist()):
+        add(f)
+    while work:
+        r1, x, y = work.popleft()
+        for r2, z in list(by_src[y]):  # (r1,x,y) then (r2,y,z)
+            if x != z:
+                for r3 in table[(r1, r2)]:
+                    add((r3, x, z))
+        for r0, w in list(by_dst[x]):  # (r0,w,x) then (r1,x,y)
+            if w != y:
+                for r3 in table[(r0, r1)]:
+                    add((r3, w, y))
+    return known
+
+
+def possible_worlds_maxmin(facts, probs, closure):
+    """Max-min tags by enumerating every subset W of the input facts: a key's
+    tag is the max over W whose closure contains it of min over W of
+    (p, -index) (the empty world's min is (1, -inf)).  Returns {key: (value, index)}."""
+    m = len(facts)
+    best = {}
+    for mask in range(1 << m):
+        W = [i for i in range(m) if mask >> i & 1]
+        if W:
+            lo = min(W, key=lambda i: (probs[i], -i))
+            val = (float(probs[lo]), -lo)
+        else:
+            val = (1.0, -(2 ** 40))
+        for k in closure([facts[i] for i in W]):
+            if k not in best or val > best[k]:
+                best[k] = val
+    return {k: (v, -nid) for k, (v, nid) in best.items()}

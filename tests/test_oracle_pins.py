@@ -369,3 +369,40 @@ def test_pathfinder_example_from_the_paper():
     # add-mult: the single proof's probability is the product of its facts
     r = oracle.run(program, inputs, "add_mult")
     assert r.relation("connected").tags[0] == pytest.approx(math.prod(chain), rel=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# kinship composition (the batched workload's non-linear program)
+# ----------------------------------------------------------------------------
+
+def test_kinship_unit_matches_worklist_closure():
+    for seed in (140, 141, 142):
+        n, r, a, b, p = W.kinship_instance(W.stream(seed))
+        comp = W.composition_table()
+        res = oracle.run(W.KIN_PROGRAM, {"fact": ((r, a, b),), "comp": (comp,)})
+        assert rel_set(res.relation("kin")) == pins.kinship_closure(r, a, b, comp)
+
+
+def test_kinship_maxmin_possible_worlds():
+    s = W.stream(143)
+    labels = 3
+    r = s.below(9, labels).astype(np.uint32)
+    a = s.below(9, 5).astype(np.uint32)
+    b = ((a + 1 + s.below(9, 4)) % 5).astype(np.uint32)  # no self pairs
+    p = s.prob(9).astype(np.float64)
+    comp = tuple(np.asarray(c, np.uint32) for c in zip(*[(i, j, (i + 2 * j + 1) % labels)
+                                                           for i in range(labels) for j in range(labels)]))
+    facts = list(zip(r.tolist(), a.tolist(), b.tolist()))
+    if len(set(facts)) != len(facts):  # the enumeration treats facts as distinct inputs
+        pytest.skip("duplicate facts in this draw")
+    res = oracle.run(W.KIN_PROGRAM, {"fact": ((r, a, b), p), "comp": (comp,)}, "diff_max_min")
+    kin = res.relation("kin")
+    ids = res.ids("kin")
+    want = pins.possible_worlds_maxmin(facts, p, lambda fs: pins.kinship_closure(
+        np.array([f[0] for f in fs], np.int64), np.array([f[1] for f in fs], np.int64),
+        np.array([f[2] for f in fs], np.int64), comp) if fs else set())
+    got = {tuple(k): (float(v), int(i)) for k, v, i in zip(kin.cols.T.tolist(), kin.tags, ids)}
+    assert set(got) == set(want)
+    for k, (v, i) in want.items():
+        assert got[k][0] == v, k
+        assert got[k][1] == i, k
