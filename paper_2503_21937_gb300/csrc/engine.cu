@@ -776,6 +776,7 @@ static void flush_candidates(lob_engine& e, RelSt& H) {
     e.after_launch("bitmap");
     e.launches += n ? 1 : 0;
     H.n_cand = 0;
+    if (n) H.touched = true;  // the iteration's read-out must run even if no candidates follow
     return;
   }
   H.flushed = true;
