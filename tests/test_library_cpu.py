@@ -48,3 +48,13 @@ def test_relation_arity_scan():
     assert lobster.relation_arities(W.ANDERSEN_PROGRAM) == {"pt": 2, "addr": 2, "assign": 2, "load": 2, "store": 2}
     assert lobster.relation_arities(W.KIN_PROGRAM) == {"kin": 3, "fact": 3, "comp": 3}
     assert len(lobster.split_rules(W.SG_PROGRAM)) == 2
+
+
+def test_every_engine_option_is_documented_in_the_header():
+    src = open(os.path.join(ROOT, "paper_2503_21937_gb300", "csrc", "engine.cu")).read()
+    body = src[src.index("int lob_set_option("):]
+    body = body[: body.index("\n}\n")]
+    keys = set(re.findall(r'k == "([a-z_]+)"', body))
+    header = open(os.path.join(ROOT, "include", "lobster.h")).read()
+    doc = header[header.index("Engine options (key, value)"): header.index("int lob_set_option(")]
+    assert keys and keys == set(re.findall(r'"([a-z_]+)"', doc)), (keys, doc)
