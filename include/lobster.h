@@ -263,11 +263,13 @@ int lob_prim_diff_merge(lob_engine* e, int semiring, const void* f_keys, const v
  * The call works in one fixed scratch array compiled into the library (about
  * 4.3 MB, held on every GPU that loads the library until the process exits)
  * and allocates nothing.  n > LOB_NOALLOC_MAX_ROWS returns LOB_E_CAPACITY;
- * a bad arity or a null pointer returns LOB_E_ARG.  The first call on a device
+ * a bad arity or a null pointer returns LOB_E_ARG (cols and out_cols may be
+ * NULL when n is 0; *n_out then gets 0).  The first call on a device
  * looks up the scratch array's device address; make that first call before
  * any stream capture.  All calls on a device share the scratch array, so
  * calls whose work overlaps on the GPU race: order them (one stream, or
- * events).  A row whose every column is 0xFFFFFFFF is dropped.  The work is
+ * events).  A row whose every column is 0xFFFFFFFF is dropped (at arity 1
+ * and 2 alike).  The work is
  * queued on cuda_stream (NULL: legacy default stream); the call does not wait. */
 #define LOB_NOALLOC_MAX_ROWS 262144u
 int lob_unique_rows_noalloc(const uint32_t* cols, uint32_t arity, uint64_t n, uint32_t* out_cols, uint64_t* n_out,

@@ -163,13 +163,9 @@ void bits_extract(const u32* a, u32* b, u64 nbits, int key64, void* out, u64 n_o
   ProfScope ps("bitmap_extract", nw * (b ? 8.0 : 4.0) + n_out * (key64 ? 8.0 : 4.0), st);
   const unsigned g = bit_grid(nt);
   const int sm32 = 8 * 1024 * 4, sm64 = 8 * 1024 * 8;  // one 1024-key stage per warp
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_bits_extract<u64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64);
-    cudaFuncSetAttribute(k_bits_extract<u64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64);
-    attr = true;
-  }
   if (key64) {
+    if (b) allow_dynamic_smem(k_bits_extract<u64, true>, sm64);
+    else allow_dynamic_smem(k_bits_extract<u64, false>, sm64);
     if (b) k_bits_extract<u64, true><<<g, 256, sm64, st>>>(a, b, nw, nt, tile_off, reinterpret_cast<u64*>(out));
     else k_bits_extract<u64, false><<<g, 256, sm64, st>>>(a, nullptr, nw, nt, tile_off, reinterpret_cast<u64*>(out));
   } else {

@@ -21,6 +21,16 @@ constexpr int kMaxFilters = 8;
 // the unique step.
 template <class K> LOB_HD K invalid_key() { return ~K(0); }
 
+// Dynamic shared memory above 48 KB is an attribute of one kernel on one
+// device.  It is set before every launch that needs it (a cheap host call, no
+// stream work), so it holds on every device and from every host thread.  A
+// failure is recorded as the runtime's last error, which the launch check that
+// follows reports.
+template <class T>
+inline cudaError_t allow_dynamic_smem(T* kernel, int bytes) {
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(kernel), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 // ---------------------------------------------------------------------------
 // packed keys
 // ---------------------------------------------------------------------------

@@ -517,12 +517,17 @@ void merge_impl(const MergeArgs& a, void* scratch, cudaStream_t st) {
   u64* tdup = apart + tiles + 1;
   u64* tr = tdup + tiles + 1;
   u64* ws = tr + tiles + 1;
-  MergeCtx<K, Sem> c;
+  MergeCtx<K, Sem> c{};
   c.fk = (const K*)a.fkeys; c.ft = (const typename Sem::Stored*)a.ftags; c.fs = a.fstamp; c.nf = a.nf;
   c.uk = (const K*)a.ukeys; c.ut = a.utags; c.nu = a.nu; c.u_stored = a.u_stored;
   c.ok = (K*)a.okeys; c.ot = (typename Sem::Stored*)a.otags; c.os = a.ostamp;
   c.rk = (K*)a.rkeys; c.rt = (typename Sem::Stored*)a.rtags;
   c.stamp = a.stamp;
+  // counts_dev[2]: set by a merge tile whose partition is not monotone (the
+  // inputs were not sorted distinct keys); cleared here so that every call
+  // reports only its own inputs
+  c.err = a.counts_dev + 2;
+  cudaMemsetAsync(c.err, 0, sizeof(u64), st);
   const double kb = sizeof(K), sb = Sem::kTags ? sizeof(typename Sem::Stored) : 0, ub = a.u_stored ? sb : (Sem::kTags ? sizeof(typename Sem::Cand) : 0);
   const double fsb = a.fstamp ? 4 : 0;
   { ProfScope ps("merge_path", (tiles + 1) * 8.0, st);

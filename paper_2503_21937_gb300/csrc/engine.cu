@@ -1477,9 +1477,16 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   if (sem < 0 || sem > 4) throw LobError(LOB_E_ARG, "unknown semiring id");
   e.peak_bytes = e.live_bytes;
   e.launches = 0;
-  cudaEvent_t ev0, ev1;
-  e.check(cudaEventCreate(&ev0), "event");
-  e.check(cudaEventCreate(&ev1), "event");
+  struct RunEvents {  // destroyed on every exit, the error paths included
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~RunEvents() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  e.check(cudaEventCreate(&ev.a), "event");
+  e.check(cudaEventCreate(&ev.b), "event");
+  cudaEvent_t ev0 = ev.a, ev1 = ev.b;
   e.check(cudaEventRecord(ev0, e.stream), "event");
   prepare(e, sem);
   load_facts(e);
@@ -1536,8 +1543,6 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
     throw LobError(LOB_E_TIMEOUT, "a bounded device wait of the sort gave up; the run's results are invalid");
   float ms = 0;
   cudaEventElapsedTime(&ms, ev0, ev1);
-  cudaEventDestroy(ev0);
-  cudaEventDestroy(ev1);
   s.iterations = k;
   s.ms = ms;
   s.candidates = e.cand_emitted;
@@ -1624,7 +1629,11 @@ int lob_create(lob_engine** out, const lob_alloc* alloc, void* cuda_stream) {
     return LOB_E_CUDA;
   }
   int rc = guarded(e, [&] {
+    // status and count words: every flag a kernel may set starts cleared, so a
+    // flag read back reports the call that set it, never an allocator's leftovers
     e->ensure(e->counts, 64 * sizeof(u64) + 256);
+    e->check(cudaMemsetAsync(e->counts.p, 0, e->counts.cap, e->stream), "clear status words");
+    e->sync();
     return LOB_OK;
   });
   if (rc != LOB_OK) {

@@ -39,6 +39,12 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_ptr[kMaxDevices] = {nullptr};
 
+// The sort and unique steps size their workspaces at run time; the fixed
+// regions above must hold them for the largest accepted batch.
+bool scratch_layout_fits() {
+  return sort_scratch_bytes(kMaxRows, 8) <= kHistBytes && unique_scratch_bytes(kMaxRows) + 256 <= kUniqueBytes;
+}
+
 // Host code must not use g_noalloc_scratch directly: on the host that name is
 // only a stand-in for the device symbol.  The device address comes from
 // cudaGetSymbolAddress, once per device, with that device current.
@@ -51,6 +57,7 @@ int scratch_for_current_device(unsigned char** out) {
   if (dev < 0 || dev >= kMaxDevices) return LOB_E_ARG;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_scratch_ptr[dev]) {
+    if (!scratch_layout_fits()) return LOB_E_CUDA;
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
@@ -65,7 +72,11 @@ int scratch_for_current_device(unsigned char** out) {
 __global__ void k_pack_rows_u64(const u32* __restrict__ cols, u32 arity, u64 n, u64* __restrict__ keys) {
   const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  keys[i] = arity == 1 ? (u64)cols[i] : ((u64)cols[i] << 32) | (u64)cols[n + i];
+  // an all-ones row becomes the all-ones key, which the unique step drops
+  // (arity 1: the value 0xFFFFFFFF alone, widened to 64 bits; it still sorts
+  // last on the low 32 bits)
+  const u32 c0 = cols[i];
+  keys[i] = arity == 1 ? (c0 == 0xFFFFFFFFu ? ~0ull : (u64)c0) : ((u64)c0 << 32) | (u64)cols[n + i];
 }
 
 __global__ void k_unpack_rows_u64(const u64* __restrict__ keys, const u64* __restrict__ count, u32 arity, u64 stride,
@@ -87,7 +98,7 @@ __global__ void k_unpack_rows_u64(const u64* __restrict__ keys, const u64* __res
 
 extern "C" int lob_unique_rows_noalloc(const uint32_t* cols, uint32_t arity, uint64_t n, uint32_t* out_cols,
                                        uint64_t* n_out, void* cuda_stream) {
-  if (!cols || !out_cols || !n_out || (arity != 1 && arity != 2)) return LOB_E_ARG;
+  if (!n_out || (arity != 1 && arity != 2) || (n && (!cols || !out_cols))) return LOB_E_ARG;
   if (n > kMaxRows) return LOB_E_CAPACITY;
   unsigned char* s = nullptr;
   int rc = scratch_for_current_device(&s);

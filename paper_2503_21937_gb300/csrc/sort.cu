@@ -178,11 +178,7 @@ void sort_impl(void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits,
   constexpr int SMEM = SortCfg<K, P>::kSmem;
   if (n <= 1 || bits <= 0) return;
   const u64 ntiles = (n + TILE - 1) / TILE;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_radix_scatter<K, P, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    attr_set = true;
-  }
+  allow_dynamic_smem(k_radix_scatter<K, P, RB>, SMEM);
   u32* hist = reinterpret_cast<u32*>(scratch);
   u32* scan_ws = hist + (u64)D * ntiles + 1;
   K* src_k = reinterpret_cast<K*>(*keys);
@@ -404,11 +400,7 @@ void onesweep_impl(void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int b
   if (n <= 1 || bits <= 0) return;
   const int passes = (bits + RB - 1) / RB;
   const u64 ntiles = (n + TILE - 1) / TILE;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_onesweep_scatter<K, P, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    attr_set = true;
-  }
+  allow_dynamic_smem(k_onesweep_scatter<K, P, RB>, SMEM);
   unsigned long long* ghist = reinterpret_cast<unsigned long long*>(scratch);
   u32* counters = reinterpret_cast<u32*>(ghist + 8 * D);
   unsigned long long* status = reinterpret_cast<unsigned long long*>(counters + 64);

@@ -26,11 +26,12 @@ def _digest(program: str, inputs: dict, semiring: str) -> str:
 
 
 def engine_run(program: str, inputs: dict, semiring: str = "unit", max_iters: int = 1 << 30, options=None,
-               read=None):
-    """Run the CUDA engine.  inputs: name -> (cols, tags, samples).
+               read=None, allocator=None):
+    """Run the CUDA engine.  inputs: name -> (cols, tags, samples); allocator:
+    optional (alloc, release) pair handed to lob_create.
     Returns (engine, stats, {relation: Relation})."""
     from paper_2503_21937_gb300 import Engine
-    e = Engine()
+    e = Engine(allocator=allocator)
     e.program(program)
     for k, v in (options or {}).items():
         e.set_option(k, v)
@@ -59,11 +60,11 @@ def _oracle_run(program: str, inputs: dict, semiring: str = "unit"):
                                 for k, v in inputs.items()}, semiring)
 
 
-def compare(program: str, inputs: dict, semiring: str = "unit", rels=None, rtol=1e-5, options=None):
+def compare(program: str, inputs: dict, semiring: str = "unit", rels=None, rtol=1e-5, options=None, allocator=None):
     """Engine vs oracle: key sets bit-exact, tags per semiring tolerance.
     Returns (engine stats, oracle result)."""
     res = oracle_run(program, inputs, semiring)
-    e, st, got = engine_run(program, inputs, semiring, options=options, read=rels)
+    e, st, got = engine_run(program, inputs, semiring, options=options, read=rels, allocator=allocator)
     for name, rel in got.items():
         want = res.relation(name)
         assert rel.cols.shape == want.cols.shape, (name, rel.cols.shape, want.cols.shape)

@@ -354,6 +354,70 @@ def test_allocator_refusal_reports_oom_and_engine_stays_usable():
     assert not live  # every allocation was returned
 
 
+def _poisoned_allocator(live):
+    """An allocator whose every block starts as 0xFF bytes (a torch tensor kept
+    alive until the engine releases it), so that no status word or counter of
+    the engine can rely on memory an allocator happens to hand out zeroed."""
+    import torch
+
+    def alloc(nbytes, stream):
+        t = torch.full((nbytes,), 0xFF, dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def release(p, nbytes, stream):
+        live.pop(p)
+
+    return alloc, release
+
+
+@pytest.mark.parametrize("semiring", ["unit", "max_min", "add_mult", "diff_max_min", "diff_add_mult"])
+def test_status_words_do_not_depend_on_allocator_contents(semiring):
+    """Runs through every flag-reporting step -- the difference+merge, the
+    merge into a secondary view (the kinship program's kin(r1,x,y) probe by
+    (r1, y)), the (+)-combination of candidate chunks -- with all-ones device
+    memory from the allocator, against the oracle."""
+    import torch
+    live = {}
+    alloc = _poisoned_allocator(live)
+    g = W.grid_reach_instance(12, sub=12)
+    src, dst, p = g["edge"]
+    compare(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, semiring, allocator=alloc)
+    s = W.stream(130)
+    n, r, a, b, pk = W.kinship_instance(s)
+    c1, c2, c3 = W.composition_table()
+    compare(W.KIN_PROGRAM, {"fact": ((r, a, b), pk), "comp": ((c1, c2, c3),)}, semiring, rels=["kin"],
+            allocator=alloc)
+    g = W.grid_reach_instance(40, sub=141)
+    src, dst, p = g["edge"]
+    compare(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, semiring, options=CHUNK,
+            allocator=alloc)
+    torch.cuda.synchronize()
+    assert not live  # every allocation was returned
+
+
+def test_prim_diff_merge_with_poisoned_allocator():
+    import torch
+    from paper_2503_21937_gb300 import Engine
+    live = {}
+    e = Engine(allocator=_poisoned_allocator(live))
+    s = W.stream(960)
+    for call in range(2):  # the second call must not see the first one's flags
+        F = np.unique(s.below(40_000, 1 << 24)).astype(np.uint32)
+        U = np.unique(np.concatenate([F[::5], s.below(30_000, 1 << 24)])).astype(np.uint32)
+        dev = lambda x: torch.from_numpy(x.astype(np.int32)).cuda()
+        ok = torch.zeros(len(F) + len(U), dtype=torch.int32, device="cuda")
+        rk = torch.zeros(len(U), dtype=torch.int32, device="cuda")
+        no, nr = e.prim_diff_merge("unit", dev(F), None, dev(U), None, ok, None, rk, None)
+        want_new = np.setdiff1d(U, F)
+        assert nr == len(want_new)
+        assert np.array_equal(rk.cpu().numpy().astype(np.uint32)[:nr], want_new)
+        assert np.array_equal(ok.cpu().numpy().astype(np.uint32)[:no], np.union1d(F, U))
+    e.close()
+    torch.cuda.synchronize()
+    assert not live
+
+
 def test_read_capacity_error_reports_the_size():
     import ctypes
     from paper_2503_21937_gb300 import lobster
