@@ -110,33 +110,61 @@ def test_andersen_200k_vars_1m_statements():
     e.close()
 
 
-def test_batched_512_samples_sampled_against_oracle():
-    """One launch over all 512 samples; three samples checked against the oracle
-    run on that sample alone (forward tags and gradients)."""
+def _spread_samples(sides, k=8):
+    """k sample ids spread over the side range, the smallest and largest side included."""
+    order = np.argsort(sides, kind="stable")
+    pick = np.unique(np.linspace(0, len(order) - 1, k).round().astype(int))
+    return sorted(int(order[i]) for i in pick)
+
+
+@pytest.mark.parametrize("semiring", ["diff_add_mult", "diff_max_min"])
+def test_batched_512_samples_sampled_against_oracle(semiring):
+    """One launch over all 512 samples (grid reachability + kinship composition),
+    forward and backward from both outputs.  Eight samples spread over the side
+    range are checked against the oracle run on that sample alone (a batched
+    run restricted to sample i equals the single run of sample i): tags of
+    reach and kin (bitwise for max-min, 1e-5 relative for add-mult) and the
+    gradients of both inputs (1e-4).  For max-min the gradient of an output
+    lands on the input fact that bounds its tag, so matching gradients under a
+    random upstream gradient also check those input ids."""
     B = W.batched_instance(512)
     program = W.REACH_PROGRAM + W.KIN_PROGRAM
     e_, f, c, st = B["edge"], B["fact"], B["comp"], B["start"]
     inputs = {"edge": (np.stack([e_[0], e_[1]]), e_[2], e_[3]), "start": (st[0][None, :], None, st[2]),
               "fact": (np.stack([f[0], f[1], f[2]]), f[3], f[4]), "comp": (np.stack([c[0], c[1], c[2]]), None, c[4])}
-    e, stats = _engine(program, inputs, "diff_add_mult")
+    e, stats = _engine(program, inputs, semiring)
     reach = e.read("reach")
     kin = e.read("kin")
     g_reach = W.stream(993).normal(reach.cols.shape[1]).astype(np.float32)
+    g_kin = W.stream(994).normal(kin.cols.shape[1]).astype(np.float32)
     gin = {"edge": np.zeros(len(e_[0]), np.float32), "fact": np.zeros(len(f[0]), np.float32)}
     e.backward("reach", g_reach, gin)
-    for smp in (0, 177, 511):
+    e.backward("kin", g_kin, gin)
+    e.close()
+    samples = _spread_samples(B["sides"])
+    assert B["sides"][samples].min() == 8 and B["sides"][samples].max() == 48
+    exact = semiring == "diff_max_min"
+    for smp in samples:
         me, mf = e_[3] == smp, f[4] == smp
         single = {"edge": ((e_[0][me], e_[1][me]), e_[2][me]), "start": ((np.array([0], np.uint32),),)}
-        res = oracle_run(W.REACH_PROGRAM, single, "diff_add_mult")
+        res = oracle_run(W.REACH_PROGRAM, single, semiring)
         want = res.relation("reach")
         m = reach.samples == smp
-        assert np.array_equal(reach.cols[:, m], want.cols)
-        np.testing.assert_allclose(reach.tags[m], want.tags, rtol=1e-5, atol=0)
+        assert np.array_equal(reach.cols[:, m], want.cols), smp
+        if exact:
+            assert np.array_equal(reach.tags[m], want.tags.astype(np.float32)), smp
+        else:
+            np.testing.assert_allclose(reach.tags[m], want.tags, rtol=1e-5, atol=0, err_msg=str(smp))
         gw = res.vjp({"reach": g_reach[m].astype(np.float64)})["edge"]
-        np.testing.assert_allclose(gin["edge"][me], gw, rtol=1e-4, atol=1e-4)
+        np.testing.assert_allclose(gin["edge"][me], gw, rtol=1e-4, atol=1e-4, err_msg=str(smp))
         singlek = {"fact": ((f[0][mf], f[1][mf], f[2][mf]), f[3][mf]), "comp": (W.composition_table(),)}
-        wk = oracle_run(W.KIN_PROGRAM, singlek, "add_mult").relation("kin")
+        resk = oracle_run(W.KIN_PROGRAM, singlek, semiring)
+        wk = resk.relation("kin")
         mk = kin.samples == smp
-        assert np.array_equal(kin.cols[:, mk], wk.cols)
-        np.testing.assert_allclose(kin.tags[mk], wk.tags, rtol=1e-5, atol=0)
-    e.close()
+        assert np.array_equal(kin.cols[:, mk], wk.cols), smp
+        if exact:
+            assert np.array_equal(kin.tags[mk], wk.tags.astype(np.float32)), smp
+        else:
+            np.testing.assert_allclose(kin.tags[mk], wk.tags, rtol=1e-5, atol=0, err_msg=str(smp))
+        gk = resk.vjp({"kin": g_kin[mk].astype(np.float64)})["fact"]
+        np.testing.assert_allclose(gin["fact"][mf], gk, rtol=1e-4, atol=1e-4, err_msg=str(smp))
