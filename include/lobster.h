@@ -206,6 +206,15 @@ int lob_reset(lob_engine* e);
  *                  predicted new facts (the last iteration's count) and
  *                  merging them / reading the relation's keys out first;
  *                  0 = never (candidates are sorted and merged)      (default 1)
+ *   "acc_dense"    1: under the tagged semirings, a derived relation whose
+ *                  key has at most acc_bits bits keeps a dense array of one
+ *                  candidate tag per key plus a bitmap; join outputs are
+ *                  (+)-added into their key's slot (atomics) instead of being
+ *                  written, sorted and uniqued, and each iteration's unique
+ *                  candidates are read out of the bitmap in key order; 0: never
+ *                  (default 1; the array takes 2^acc_bits x 4 or 8 bytes)
+ *   "acc_bits"     largest key width, in bits, given a dense accumulator
+ *                  (1..30, default 28)
  * LOB_E_ARG for an unknown key or a value out of range. */
 int lob_set_option(lob_engine* e, const char* key, int64_t value);
 

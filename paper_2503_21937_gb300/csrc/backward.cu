@@ -36,14 +36,20 @@ struct BwdParams {
   float* out_fact_tag[kMaxArity];
   int last;
   const void* h_keys; int h_key64; u64 h_n; const u32* h_stamp; const double* h_adj; u32 k;
-  double* fact_adj[kMaxArity];       // adjoint array of the relation of fact m
+  const u32* h_row;                  // dense key -> row of the head relation (0xFFFFFFFF: absent), or null
+  const u32* h_new;                  // bitmap of the head keys first derived, unclamped, in iteration k (or null)
+  double* fact_adj[kMaxArity];       // adjoint array of the relation of fact m (null: no adjoint needed)
+  int n_facts;                       // body facts of a grounding at the last step
 };
 
 // adjoint of the head of a grounding emitted in iteration B.k, or 0 when the
 // head was not new in that iteration or its (+) was clamped
 LOB_DEV double head_adjoint(const BwdParams& B, u64 key) {
   u64 j;
-  if (B.h_key64) {
+  if (B.h_row) {
+    j = B.h_row[key];
+    if (j == 0xFFFFFFFFull) return 0.0;
+  } else if (B.h_key64) {
     j = lower_bound_dev<u64>(reinterpret_cast<const u64*>(B.h_keys), 0, B.h_n, key);
     if (j >= B.h_n || reinterpret_cast<const u64*>(B.h_keys)[j] != key) return 0.0;
   } else {
@@ -63,15 +69,6 @@ LOB_DEV u64 head_key(const StepParams& P, const u32* val, u32 sample) {
     key |= (u64)x << L.shift[j];
   }
   return key;
-}
-
-LOB_DEV void push_adjoints(const BwdParams& B, double a, int m, const u32* rows, const float* tags) {
-  for (int i = 0; i < m; i++) {
-    double prod = 1.0;
-    for (int l = 0; l < m; l++)
-      if (l != i) prod *= (double)tags[l];
-    atomicAdd(B.fact_adj[i] + rows[i], a * prod);
-  }
 }
 
 __global__ void __launch_bounds__(256) k_bwd_emit(const __grid_constant__ StepParams P, const __grid_constant__ BwdParams B,
@@ -122,7 +119,38 @@ __global__ void __launch_bounds__(256) k_bwd_emit(const __grid_constant__ StepPa
     for (int c = 0; c < P.v_lay.arity; c++)
       if (c >= P.prefix_len && ok) ok = apply_act(P.v_act[c], (u32)field_of(vk, P.v_lay.shift[c], P.v_lay.width[c]), val);
     for (int f = 0; f < P.n_filters && ok; f++) ok = eval_filter(P.filters[f], val);
-    // facts of the grounding so far
+    if (B.last) {
+      if (!ok) continue;
+      const u64 hk = head_key(P, val, sample);
+      // most groundings re-derive a head that existed before iteration k: one
+      // bit of the iteration's new-head bitmap rules them out
+      if (B.h_new && !((B.h_new[hk >> 5] >> (hk & 31)) & 1u)) continue;
+      const double a = head_adjoint(B, hk);
+      if (a == 0.0) continue;
+      u32 rows[kMaxArity + 1];
+      float tags[kMaxArity + 1];
+      int nf = 0;
+      if (B.packed_source) {
+        rows[nf] = (u32)r;
+        tags[nf++] = reinterpret_cast<const float*>(P.in_tags)[r];
+      } else {
+        for (int q = 0; q < B.n_in_facts; q++) {
+          rows[nf] = B.in_fact_row[q][r];
+          tags[nf++] = B.in_fact_tag[q][r];
+        }
+      }
+      rows[nf] = B.v_prow ? B.v_prow[v] : (u32)v;
+      tags[nf++] = reinterpret_cast<const float*>(P.v_tags)[v];
+      for (int q = 0; q < nf; q++) {
+        if (!B.fact_adj[q]) continue;
+        double c = a;
+        for (int l = 0; l < nf; l++)
+          if (l != q) c *= (double)tags[l];
+        atomicAdd(B.fact_adj[q] + rows[q], c);
+      }
+      continue;
+    }
+    // facts of the grounding so far, carried to the next step
     u32 rows[kMaxArity + 1];
     float tags[kMaxArity + 1];
     int nf = 0;
@@ -138,16 +166,11 @@ __global__ void __launch_bounds__(256) k_bwd_emit(const __grid_constant__ StepPa
     rows[nf] = B.v_prow ? B.v_prow[v] : (u32)v;
     tags[nf++] = reinterpret_cast<const float*>(P.v_tags)[v];
     tag = Sem::mul(tag, (double)tags[nf - 1]);
-    if (!B.last) {
-      const u64 o = j - P.j_begin;
-      write_output<Sem>(P, P.out_base + o, ok, val, sample, tag);
-      for (int q = 0; q < nf; q++) {
-        B.out_fact_row[q][o] = rows[q];
-        B.out_fact_tag[q][o] = tags[q];
-      }
-    } else if (ok) {
-      const double a = head_adjoint(B, head_key(P, val, sample));
-      if (a != 0.0) push_adjoints(B, a, nf, rows, tags);
+    const u64 o = j - P.j_begin;
+    write_output<Sem>(P, P.out_base + o, ok, val, sample, tag);
+    for (int q = 0; q < nf; q++) {
+      B.out_fact_row[q][o] = rows[q];
+      B.out_fact_tag[q][o] = tags[q];
     }
   }
 }
@@ -160,8 +183,10 @@ __global__ void k_bwd_project(const __grid_constant__ StepParams P, const __grid
     u32 sample;
     double tag;
     if (!read_input<SemAddMult>(P, r, val, sample, tag)) continue;
-    const double a = head_adjoint(B, head_key(P, val, sample));
-    if (a != 0.0) atomicAdd(B.fact_adj[0] + r, a);
+    const u64 hk = head_key(P, val, sample);
+    if (B.h_new && !((B.h_new[hk >> 5] >> (hk & 31)) & 1u)) continue;
+    const double a = head_adjoint(B, hk);
+    if (a != 0.0 && B.fact_adj[0]) atomicAdd(B.fact_adj[0] + r, a);
   }
 }
 
@@ -172,6 +197,23 @@ __global__ void k_locate(const void* __restrict__ keys, int key64, u64 n, const 
     if (key64) out[i] = (u32)lower_bound_dev<u64>(reinterpret_cast<const u64*>(keys), 0, n, reinterpret_cast<const u64*>(q)[i]);
     else out[i] = (u32)lower_bound_dev<u32>(reinterpret_cast<const u32*>(keys), 0, n, reinterpret_cast<const u32*>(q)[i]);
   }
+}
+
+// dense key -> row map of a sorted relation (every other slot stays all ones)
+__global__ void k_dense_rows(const void* __restrict__ keys, int key64, u64 n, u32* __restrict__ map) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) map[load_key(keys, key64, i)] = (u32)i;
+}
+
+// bits of the facts first derived, with an unclamped (+), in iteration k
+__global__ void k_mark_new(const void* __restrict__ keys, int key64, const u32* __restrict__ stamps, u64 n, u32 k,
+                           u32* __restrict__ bm) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    if (stamps[i] == k) {
+      const u64 key = load_key(keys, key64, i);
+      atomicOr(bm + (key >> 5), 1u << (u32)(key & 31u));
+    }
 }
 
 __global__ void k_f32_to_f64(const float* __restrict__ a, u64 n, double* __restrict__ out) {
@@ -228,11 +270,15 @@ namespace {
 
 struct BwdState {
   std::vector<DevBuf> adj;                   // per relation, f64, primary view order
+  std::vector<DevBuf> hrow;                  // per derived relation with a small key space: dense key -> row
+  std::vector<DevBuf> hnew;                  // and its bitmap of the facts new in the iteration being replayed
   std::vector<std::vector<DevBuf>> prow;     // per relation, per view (index 0 unused)
 };
 
 void free_state(lob_engine& e, BwdState& S) {
   for (auto& b : S.adj) e.release(b);
+  for (auto& b : S.hrow) e.release(b);
+  for (auto& b : S.hnew) e.release(b);
   for (auto& v : S.prow)
     for (auto& b : v) e.release(b);
 }
@@ -283,11 +329,21 @@ void replay_arm(lob_engine& e, BwdState& S, const RulePlan& rp, const ArmPlan& A
   B.h_n = HV.n;
   B.h_stamp = HV.stamps.as<u32>();
   B.h_adj = S.adj[R.head.rel].as<double>();
+  B.h_row = S.hrow[R.head.rel].as<u32>();
+  B.h_new = S.hnew[R.head.rel].as<u32>();
   B.k = k;
-  B.fact_adj[0] = S.adj[R.body[A.delta].rel].as<double>();
-  for (size_t s = 1; s < A.steps.size(); s++) B.fact_adj[s] = S.adj[R.body[A.steps[s].atom].rel].as<double>();
+  // adjoints are kept for derived relations and for tagged inputs; an untagged
+  // input fact (tag 1, not differentiable) needs none
+  auto adj_of = [&](u32 rel) -> double* {
+    const RelSt& q = e.rels[rel];
+    return q.idb || q.in_has_tags ? S.adj[rel].as<double>() : nullptr;
+  };
+  B.fact_adj[0] = adj_of(R.body[A.delta].rel);
+  for (size_t s = 1; s < A.steps.size(); s++) B.fact_adj[s] = adj_of(R.body[A.steps[s].atom].rel);
+  B.n_facts = (int)A.steps.size();
   if (A.steps.size() == 1) {
     B.last = 1;
+    ProfScope ps("bwd_project", P.n_in * (16.0 + 12.0), e.stream);
     k_bwd_project<<<grid_for_n(P.n_in), 256, 0, e.stream>>>(P, B);
     e.after_launch("backward project");
     e.launches++;
@@ -361,7 +417,14 @@ void replay_arm(lob_engine& e, BwdState& S, const RulePlan& rp, const ArmPlan& A
     P.off = e.off.as<u64>();
     P.total = total;
     P.j_begin = 0;
-    k_bwd_emit<<<(unsigned)ntiles, 256, 0, e.stream>>>(P, B, e.part.as<u64>());
+    {
+      // per grounding: its input row and matched fact read; an intermediate
+      // row (+ carried facts) written, or the head's adjoint looked up and one
+      // adjoint pushed per body fact
+      const double per = last ? 8.0 + 4.0 + 8.0 + 8.0 * nf : 8.0 + 4.0 + 16.0 + 8.0 * nf;
+      ProfScope ps("bwd_emit", P.n_in * 24.0 + total * per, e.stream);
+      k_bwd_emit<<<(unsigned)ntiles, 256, 0, e.stream>>>(P, B, e.part.as<u64>());
+    }
     e.after_launch("backward emit");
     e.launches += 2;
     if (last) return;
@@ -438,10 +501,21 @@ int backward_impl(lob_engine* e, u32 out_rel, const float* grad_tags, float* con
     BwdState S;
     try {
       S.adj.resize(nrel);
+      S.hrow.resize(nrel);
+      S.hnew.resize(nrel);
       S.prow.resize(nrel);
       for (size_t k = 0; k < nrel; k++) {
         RelSt& r = e->rels[k];
         const u64 n = r.views[0].n;
+        const Layout& L = r.views[0].lay;
+        if (r.idb && n && L.bits <= e->opt_acc_bits) {  // heads are found by one load instead of a binary search
+          const u64 slots = 1ull << L.bits;
+          e->ensure(S.hrow[k], slots * 4);
+          e->check(cudaMemsetAsync(S.hrow[k].p, 0xFF, slots * 4, e->stream), "head rows");
+          k_dense_rows<<<grid_for_n(n), 256, 0, e->stream>>>(r.views[0].keys.p, L.key64, n, S.hrow[k].as<u32>());
+          e->after_launch("head rows");
+          e->ensure(S.hnew[k], std::max<u64>(16, slots / 8));
+        }
         e->ensure(S.adj[k], std::max<u64>(n, 1) * 8);
         e->check(cudaMemsetAsync(S.adj[k].p, 0, std::max<u64>(n, 1) * 8, e->stream), "adjoint init");
         if (n > 0xFFFFFFFFull) throw LobError(LOB_E_ARG, "backward supports relations below 2^32 facts");
@@ -463,6 +537,15 @@ int backward_impl(lob_engine* e, u32 out_rel, const float* grad_tags, float* con
         e->after_launch("adjoint seed");
       }
       for (u32 k = e->last_iter; k >= 1; k--) {
+        for (size_t q = 0; q < nrel; q++) {  // the heads new in iteration k
+          if (!S.hnew[q].p) continue;
+          RelSt& r = e->rels[q];
+          e->check(cudaMemsetAsync(S.hnew[q].p, 0, S.hnew[q].cap, e->stream), "new heads");
+          k_mark_new<<<grid_for_n(r.views[0].n), 256, 0, e->stream>>>(r.views[0].keys.p, r.views[0].lay.key64,
+                                                                      r.views[0].stamps.as<u32>(), r.views[0].n, k,
+                                                                      S.hnew[q].as<u32>());
+          e->after_launch("new heads");
+        }
         for (auto& p : e->plans)
           for (auto& A : p.arms) {
             const auto& cnt = e->iter_counts[k - 1];  // (total, recent) per relation at the start of iteration k

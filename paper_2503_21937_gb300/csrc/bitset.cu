@@ -132,6 +132,80 @@ __global__ void __launch_bounds__(256) k_bits_extract(const u32* __restrict__ a,
   }
 }
 
+// Dense (+)-accumulation read-out (tagged semirings): the touched bitmap `a`
+// lists the keys that received candidates this iteration and acc[key] holds
+// their (+)-reduced candidate tag.  Reading both in key order yields the
+// iteration's unique candidates already sorted, with their reduced tags -- the
+// result of Sec. 3.2's sort + unique<(+)> over the candidate tuples, without
+// materialising or sorting the candidates.  Each read slot is reset to 0 and
+// each bitmap word cleared, ready for the next iteration.  Same tiling as
+// k_bits_extract; the warp stages keys and tags side by side.
+template <class K, class C>
+__global__ void __launch_bounds__(256) k_dense_extract(u32* __restrict__ a, u64 nwords, u64 ntiles,
+                                                       const u64* __restrict__ tile_off, C* __restrict__ acc,
+                                                       K* __restrict__ out, C* __restrict__ otags) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tstage = reinterpret_cast<C*>(smem_raw) + (threadIdx.x >> 5) * 1024;
+  K* stage = reinterpret_cast<K*>(reinterpret_cast<C*>(smem_raw) + 8 * 1024) + (threadIdx.x >> 5) * 1024;
+  __shared__ u64 wbase[256 / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const u64 wf = t * kBitTileWords + (u64)warp * kWarpWords;
+    u32 x[kBatches];
+    u32 c = 0;
+#pragma unroll
+    for (int i = 0; i < kBatches; i++) {
+      const u64 w = wf + (u64)i * 32 + lane;
+      x[i] = w < nwords ? a[w] : 0u;
+      c += __popc(x[i]);
+    }
+    c = warp_inclusive_sum(c);
+    if (lane == 31) wbase[warp] = c;
+    __syncthreads();
+    u64 base = tile_off[t];
+    for (int v = 0; v < warp; v++) base += wbase[v];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kBatches; i++) {
+      const u32 m0 = x[i];
+      const u32 cnt = __popc(m0);
+      const u32 inc = warp_inclusive_sum(cnt);
+      const u32 tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+      if (!tot) continue;
+      u32 pos = inc - cnt;
+      const u64 kw = (wf + (u64)i * 32 + lane) << 5;
+      for (u32 m = m0; m; m &= m - 1) {
+        const u64 key = kw | (u64)(__ffs(m) - 1);
+        tstage[pos] = acc[key];
+        acc[key] = C(0);
+        stage[pos++] = (K)key;
+      }
+      __syncwarp();
+      for (u32 q = lane; q < tot; q += 32) {
+        out[base + q] = stage[q];
+        otags[base + q] = tstage[q];
+      }
+      __syncwarp();
+      base += tot;
+      if (m0) a[wf + (u64)i * 32 + lane] = 0u;
+    }
+  }
+}
+
+// candidates written by other producers (projections, general join steps)
+// folded into the dense accumulator; all-ones keys (dropped rows) are skipped
+template <class Sem>
+__global__ void k_dense_fold(const void* __restrict__ keys, int key64, const typename Sem::Cand* __restrict__ tags, u64 n,
+                             void* __restrict__ acc, u32* __restrict__ bm) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const u64 k = load_key(keys, key64, i);
+    if (k == invalid_of(key64)) continue;
+    dense_add<Sem>(acc, k, tags[i]);
+    touch_bit(bm, k);
+  }
+}
+
 u64 bit_words(u64 nbits) { return (nbits + 31) / 32; }
 u64 bit_tiles(u64 nbits) { return (bit_words(nbits) + kBitTileWords - 1) / kBitTileWords; }
 unsigned bit_grid(u64 ntiles) { return (unsigned)(ntiles < 152ull * 16 ? ntiles : 152ull * 16); }
@@ -171,5 +245,52 @@ void bits_extract(const u32* a, u32* b, u64 nbits, int key64, void* out, u64 n_o
   } else {
     if (b) k_bits_extract<u32, true><<<g, 256, sm32, st>>>(a, b, nw, nt, tile_off, reinterpret_cast<u32*>(out));
     else k_bits_extract<u32, false><<<g, 256, sm32, st>>>(a, nullptr, nw, nt, tile_off, reinterpret_cast<u32*>(out));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dense (+)-accumulation (host side)
+// ---------------------------------------------------------------------------
+namespace {
+template <class K, class C>
+void dense_extract_t(u32* a, u64 nbits, void* acc, void* out, void* otags, void* scratch, cudaStream_t st) {
+  const u64 nw = bit_words(nbits), nt = bit_tiles(nbits);
+  const u64* tile_off = reinterpret_cast<const u64*>(scratch) + nt;
+  const int smem = 8 * 1024 * (int)(sizeof(K) + sizeof(C));
+  allow_dynamic_smem(k_dense_extract<K, C>, smem);
+  k_dense_extract<K, C><<<bit_grid(nt), 256, smem, st>>>(a, nw, nt, tile_off, reinterpret_cast<C*>(acc),
+                                                         reinterpret_cast<K*>(out), reinterpret_cast<C*>(otags));
+}
+template <class Sem>
+void dense_fold_t(const void* keys, int key64, const void* tags, u64 n, void* acc, u32* bm, cudaStream_t st) {
+  u64 b = (n + 255) / 256;
+  if (b > 152ull * 16) b = 152ull * 16;
+  k_dense_fold<Sem><<<(unsigned)(b ? b : 1), 256, 0, st>>>(keys, key64, reinterpret_cast<const typename Sem::Cand*>(tags),
+                                                           n, acc, bm);
+}
+}  // namespace
+
+int dense_cand_bytes(int sem) { return sem == SR_MAX_MIN ? 4 : 8; }
+
+void dense_extract(int sem, int key64, u32* touched, void* acc, u64 nbits, void* okeys, void* otags, u64 n_out,
+                   void* scratch, cudaStream_t st) {
+  const double cb = dense_cand_bytes(sem), kb = key64 ? 8 : 4;
+  ProfScope ps("dense_extract", bit_words(nbits) * 4.0 + n_out * (2.0 * cb + kb + cb), st);
+  if (sem == SR_MAX_MIN) {
+    if (key64) dense_extract_t<u64, float>(touched, nbits, acc, okeys, otags, scratch, st);
+    else dense_extract_t<u32, float>(touched, nbits, acc, okeys, otags, scratch, st);
+  } else {
+    if (key64) dense_extract_t<u64, u64>(touched, nbits, acc, okeys, otags, scratch, st);
+    else dense_extract_t<u32, u64>(touched, nbits, acc, okeys, otags, scratch, st);
+  }
+}
+
+void dense_fold(int sem, int key64, const void* keys, const void* tags, u64 n, void* acc, u32* touched, cudaStream_t st) {
+  ProfScope ps("dense_fold", n * ((key64 ? 8.0 : 4.0) + 2.0 * dense_cand_bytes(sem) + 4.0), st);
+  if (!n) return;
+  switch (sem) {
+    case SR_MAX_MIN: dense_fold_t<SemMaxMin>(keys, key64, tags, n, acc, touched, st); break;
+    case SR_DIFF_MAX_MIN: dense_fold_t<SemDiffMaxMin>(keys, key64, tags, n, acc, touched, st); break;
+    default: dense_fold_t<SemAddMult>(keys, key64, tags, n, acc, touched, st); break;
   }
 }

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 typedef unsigned int u32;
 typedef unsigned long long u64;
 
@@ -140,6 +142,32 @@ LOB_HD u64 dmm_pack(float v, u32 id) {
 }
 LOB_HD u32 dmm_id(u64 t) { return 0xFFFFFFFFu - (u32)(t & 0xFFFFFFFFull); }
 LOB_DEV float dmm_value(u64 t) { return __uint_as_float((u32)(t >> 32)); }
+
+// Dense (+)-accumulation of a candidate tag into slot `key` of a per-key array
+// holding candidate tags (every slot starts at 0, the identity of (+) for the
+// tagged semirings: tags are non-negative, and 0 is below every packed
+// diff-max-min tag).  add-mult: FP64 add; max-min: max of the f32 bit patterns
+// (non-negative floats order like their bits); diff-max-min: max of the packed
+// u64 tags.  A slot whose tag cannot grow is left alone without an atomic.
+template <class Sem>
+LOB_DEV void dense_add(void* acc, u64 key, typename Sem::Cand t) {
+  if constexpr (std::is_same<Sem, SemAddMult>::value) {
+    atomicAdd(reinterpret_cast<double*>(acc) + key, t);
+  } else if constexpr (std::is_same<Sem, SemMaxMin>::value) {
+    int* a = reinterpret_cast<int*>(acc) + key;
+    const int v = __float_as_int(t);
+    if (*reinterpret_cast<volatile int*>(a) < v) atomicMax(a, v);
+  } else if constexpr (std::is_same<Sem, SemDiffMaxMin>::value) {
+    unsigned long long* a = reinterpret_cast<unsigned long long*>(acc) + key;
+    if (*reinterpret_cast<volatile unsigned long long*>(a) < t) atomicMax(a, (unsigned long long)t);
+  }
+}
+// mark `key` as touched in this iteration's bitmap (no atomic when already set)
+LOB_DEV void touch_bit(u32* bm, u64 key) {
+  const u32 bit = 1u << (u32)(key & 31u);
+  u32* w = bm + (key >> 5);
+  if (!(*reinterpret_cast<volatile u32*>(w) & bit)) atomicOr(w, bit);
+}
 
 // ---------------------------------------------------------------------------
 // scans

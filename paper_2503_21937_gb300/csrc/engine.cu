@@ -149,9 +149,10 @@ static void release_derived(lob_engine& e) {
     for (auto& v : r.views) release_view(e, v);
     r.views.clear();
     for (DevBuf* b : {&r.rkeys, &r.rtags, &r.nkeys, &r.ntags, &r.ckeys, &r.ctags, &r.ckeys2, &r.ctags2, &r.row_factor,
-                      &r.row_keys, &r.akeys, &r.atags, &r.akeys2, &r.atags2, &r.bitmap, &r.prev_bitmap})
+                      &r.row_keys, &r.akeys, &r.atags, &r.akeys2, &r.atags2, &r.bitmap, &r.prev_bitmap, &r.dacc,
+                      &r.dtouched})
       e.release(*b);
-    r.extract = r.touched = r.keys_stale = false;
+    r.extract = r.touched = r.keys_stale = r.dense = false;
     r.n_recent = r.n_next = r.n_cand = r.n_acc = 0;
     r.flushed = false;
     r.filter_on = false;
@@ -771,6 +772,15 @@ static void ensure_cand(lob_engine& e, RelSt& H, u64 extra) {
 // iteration's accumulator, so that no sort ever sees more than opt_max_cand keys.
 static void flush_candidates(lob_engine& e, RelSt& H) {
   const u64 n = H.n_cand;
+  if (H.dense) {  // dense accumulation: candidates are (+)-added into their slots
+    dense_fold(sem_kernel(e.semiring), H.views[0].lay.key64, H.ckeys.p, H.ctags.p, n, H.dacc.p, H.dtouched.as<u32>(),
+               e.stream);
+    e.after_launch("dense fold");
+    e.launches += n ? 1 : 0;
+    H.n_cand = 0;
+    if (n) H.touched = true;
+    return;
+  }
   if (H.extract) {  // bitmap delta mode: candidates only need their bits set
     bitmap_set_keys(H.ckeys.p, H.views[0].lay.key64, n, H.bitmap.as<u32>(), e.stream);
     e.after_launch("bitmap");
@@ -1175,6 +1185,29 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
       }
       return;
     }
+    if (last && H.dense) {  // outputs (+)-added into the head's dense accumulator
+      H.touched = true;
+      P.out_words = nullptr;
+      P.out_tags = nullptr;
+      P.out_base = 0;
+      P.out_count = nullptr;
+      P.bitmap = H.dtouched.as<u32>();
+      P.acc = H.dacc.p;
+      for (u64 jb = 0; jb < total; jb += e.opt_max_cand) {
+        const u64 sub = std::min(e.opt_max_cand, total - jb);
+        const u64 nt = (sub + kEmitTile - 1) / kEmitTile;
+        e.ensure(e.part, (nt + 1) * 8);
+        P.total = sub;
+        P.j_begin = jb;
+        pjoin_partition(P, nt, e.part.as<u64>(), e.stream);
+        pjoin_emit(sem, P, e.part.as<u64>(), e.stream);
+        e.after_launch("join emit");
+        e.launches += 2;
+        H.cand_iter += sub;
+        e.cand_emitted += sub;
+      }
+      return;
+    }
     if (last) {  // candidates, in sub-ranges of at most opt_max_cand outputs
       for (u64 jb = 0; jb < total; jb += e.opt_max_cand) {
         const u64 sub = std::min(e.opt_max_cand, total - jb);
@@ -1229,6 +1262,7 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
 
 // sort + unique + difference/merge of one head relation's candidates
 static void dedup_sorted(lob_engine& e, RelSt& H, u32 k);
+static void merge_unique(lob_engine& e, RelSt& H, u32 k, const void* ukeys, const void* utags, u64 nu);
 static u64 bitmap_bits(const RelSt& H) { return 1ull << H.views[0].lay.bits; }
 
 // The primary view's keys, read out of a membership bitmap (sorted).
@@ -1303,10 +1337,45 @@ static void dedup_bitmap_delta(lob_engine& e, RelSt& H, u32 k) {
   update_secondary_views(e, H, k, nr);
 }
 
+// Dense accumulation: the iteration's unique candidates, already (+)-reduced,
+// are the touched slots read out in key order; then the usual difference+merge.
+static void dedup_dense(lob_engine& e, RelSt& H, u32 k) {
+  if (H.n_cand) flush_candidates(e, H);
+  H.unfiltered = false;
+  H.flushed = false;
+  if (!H.touched) {
+    H.last_new = 0;
+    return;
+  }
+  H.touched = false;
+  const int ks = sem_kernel(e.semiring);
+  const Layout& L = H.views[0].lay;
+  const int kb = L.key64 ? 8 : 4, cb = cand_bytes(e.semiring);
+  const u64 nbits = 1ull << L.bits;
+  scratch_at_least(e, bits_scratch_bytes(nbits));
+  e.launches += bits_count(H.dtouched.as<u32>(), nullptr, nbits, e.scratch.p, e.counts.as<u64>() + 1, e.stream);
+  e.after_launch("dense count");
+  const u64 nu = e.read_u64(e.counts.as<u64>() + 1);
+  if (!nu) {
+    H.last_new = 0;
+    return;
+  }
+  e.ensure(H.akeys, nu * kb);
+  e.ensure(H.atags, nu * cb);
+  dense_extract(ks, L.key64, H.dtouched.as<u32>(), H.dacc.p, nbits, H.akeys.p, H.atags.p, nu, e.scratch.p, e.stream);
+  e.after_launch("dense extract");
+  e.launches++;
+  merge_unique(e, H, k, H.akeys.p, H.atags.p, nu);
+}
+
 static void dedup_relation(lob_engine& e, RelSt& H, u32 k) {
   H.n_next = 0;
   H.last_cand = H.cand_iter;
   H.cand_iter = 0;
+  if (H.dense) {
+    dedup_dense(e, H, k);
+    return;
+  }
   if (H.extract) {
     dedup_bitmap_delta(e, H, k);
     return;
@@ -1386,7 +1455,20 @@ static void dedup_sorted(lob_engine& e, RelSt& H, u32 k) {
     e.launches += 2 + scan_launches((n + 4095) / 4096);
     nu = e.read_u64(e.counts.as<u64>() + 1);
   }
+  merge_unique(e, H, k, ukeys, utags, nu);
+}
+
+// Difference of the iteration's unique candidates U (sorted keys, candidate
+// tags) against F, fused with their merge into F; the new (or improved) facts
+// become the next recent set and reach the secondary views.
+static void merge_unique(lob_engine& e, RelSt& H, u32 k, const void* ukeys, const void* utags, u64 nu) {
   if (!nu) return;
+  const int sem = e.semiring;
+  const int ks = sem_kernel(sem);
+  ViewSt& V = H.views[0];
+  const Layout& L = V.lay;
+  const int kb = L.key64 ? 8 : 4, sb = stored_bytes(sem);
+  const bool stamps = sem_stamps(sem);
   // difference against F fused with the merge into F
   e.ensure(V.keys2, (V.n + nu) * kb);
   if (sb) e.ensure(V.tags2, (V.n + nu) * sb);
@@ -1472,6 +1554,25 @@ static void choose_dedup_mode(lob_engine& e, RelSt& r) {
   r.extract = delta_cost <= sorted_cost;
 }
 
+// Dense (+)-accumulation for every derived relation of a tagged run whose key
+// space has at most opt_acc_bits bits (accumulator: 2^bits candidate tags).
+static void enable_dense(lob_engine& e) {
+  if (!e.opt_acc_dense || e.semiring == SR_UNIT) return;
+  const int cb = dense_cand_bytes(sem_kernel(e.semiring));
+  for (auto& r : e.rels) {
+    const Layout& L = r.views[0].lay;
+    if (!r.idb || L.bits > e.opt_acc_bits) continue;
+    const u64 slots = 1ull << L.bits;
+    const u64 bm_bytes = std::max<u64>(16, slots / 8);
+    e.ensure(r.dacc, slots * cb);
+    e.ensure(r.dtouched, bm_bytes);
+    e.check(cudaMemsetAsync(r.dacc.p, 0, slots * cb, e.stream), "dense accumulator");
+    e.check(cudaMemsetAsync(r.dtouched.p, 0, bm_bytes, e.stream), "dense bitmap");
+    r.dense = true;
+    r.touched = false;
+  }
+}
+
 static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   if (e.state != 0) throw LobError(LOB_E_STATE, "run_to_fixpoint was already called; call lob_reset first");
   if (sem < 0 || sem > 4) throw LobError(LOB_E_ARG, "unknown semiring id");
@@ -1490,6 +1591,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   e.check(cudaEventRecord(ev0, e.stream), "event");
   prepare(e, sem);
   load_facts(e);
+  enable_dense(e);
   lob_stats s{};
   s.semiring = (u32)sem;
   int rc = LOB_OK;
@@ -2076,6 +2178,8 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "packed_join" && (value == 0 || value == 1)) e->opt_packed_join = (int)value;
     else if (k == "bitmap_delta" && value >= 0 && value <= 2) e->opt_bitmap_delta = (int)value;
     else if (k == "warp_join" && value >= 0 && value <= 2) e->opt_warp_join = (int)value;
+    else if (k == "acc_dense" && (value == 0 || value == 1)) e->opt_acc_dense = (int)value;
+    else if (k == "acc_bits" && value >= 1 && value <= 30) e->opt_acc_bits = (int)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

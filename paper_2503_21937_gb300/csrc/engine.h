@@ -96,6 +96,11 @@ struct RelSt {
   bool keys_stale = false;  // primary view keys not materialised (the bitmaps hold the relation)
   bool filter_on = false;
   bool unfiltered = false;  // this iteration appended candidates that bypassed the filter
+  // dense (+)-accumulation (tagged semirings, small key spaces): candidates are
+  // (+)-added into dacc[key] and marked in dtouched instead of being written,
+  // sorted and uniqued; the iteration's unique candidates are read out in key order
+  bool dense = false;
+  DevBuf dacc, dtouched;
   u64 last_cand = 0, last_new = 0, cand_iter = 0;
   // gradient routing of loaded rows
   DevBuf row_factor, row_keys;
@@ -180,6 +185,8 @@ struct lob_engine {
   int opt_packed_join = 1;        // packed-word join kernels when an arm's bindings fit 64 bits
   int opt_warp_join = 1;          // unit semiring: warp-balanced packed join steps
   int opt_bitmap_delta = 1;       // filtered relations: 0 never, 1 when predicted cheaper, 2 always read new facts from the bitmap
+  int opt_acc_dense = 1;          // tagged semirings: dense (+)-accumulation for head relations of at most opt_acc_bits key bits
+  int opt_acc_bits = 28;
   EngineProfiler prof;
   // run state
   int state = 0;  // 0 loading, 1 ran

@@ -155,6 +155,17 @@ void bitmap_set_keys(const void* keys, int key64, u64 n, u32* bitmap, cudaStream
 size_t bits_scratch_bytes(u64 nbits);
 int bits_count(const u32* a, const u32* b, u64 nbits, void* scratch, u64* total_dev, cudaStream_t st);
 void bits_extract(const u32* a, u32* b, u64 nbits, int key64, void* out, u64 n_out, void* scratch, cudaStream_t st);
+// Dense (+)-accumulation of tagged candidates (bitset.cu).  acc holds one
+// candidate tag (dense_cand_bytes) per key of the relation's key space, all 0
+// between iterations; `touched` is a bitmap over the same keys.  dense_fold
+// (+)-adds candidate (key, tag) pairs into acc and marks their bits (the packed
+// join's emission does the same directly).  After bits_count(touched, nullptr,
+// ...) has placed the touched keys, dense_extract writes them in increasing
+// order with their reduced tags (n_out of them) and resets acc and touched.
+int dense_cand_bytes(int sem);
+void dense_fold(int sem, int key64, const void* keys, const void* tags, u64 n, void* acc, u32* touched, cudaStream_t st);
+void dense_extract(int sem, int key64, u32* touched, void* acc, u64 nbits, void* okeys, void* otags, u64 n_out,
+                   void* scratch, cudaStream_t st);
 // merge two sorted key lists known to share no key (keys only)
 size_t merge_nodup_scratch_bytes(u64 na, u64 nb);
 void merge_nodup(int key64, const void* a, u64 na, const void* b, u64 nb, void* out, void* scratch, cudaStream_t st);

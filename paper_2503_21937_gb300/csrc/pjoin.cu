@@ -124,7 +124,11 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
                                           : (P.v_stamp[v] & 0x7FFFFFFFu) == P.v_stamp_val);
     ok = ok && checks_ok(P.checks, P.n_checks, wi, wv);
     const u64 w = ok ? compose(P.out, P.n_out, wi, wv) : invalid_out;
-    if constexpr (kFilter) {
+    if constexpr (kFilter == 3) {
+      if (!ok) continue;
+      dense_add<Sem>(P.acc, w, Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v])));
+      touch_bit(P.bitmap, w);
+    } else if constexpr (kFilter) {
       if (!ok) continue;
       const u32 bit = 1u << (u32)(w & 31u);
       u32* word = P.bitmap + (w >> 5);
@@ -309,7 +313,14 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
       u64 w = 0;
 #pragma unroll
       for (int q = 0; q < NOUT; q++) w |= reg_pick(out_op[q], wi[b], wv[b]) << out_sh[q];
-      if constexpr (kFilter) {
+      if constexpr (kFilter == 3) {
+        if (!ok) continue;
+        const u64 r = r0 + rr[b];
+        const C tag = P.in_packed ? Sem::from_stored(reinterpret_cast<const S*>(P.in_tags)[r])
+                                  : reinterpret_cast<const C*>(P.in_tags)[r];
+        dense_add<Sem>(P.acc, w, Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v])));
+        touch_bit(P.bitmap, w);
+      } else if constexpr (kFilter) {
         if (!ok) continue;
         const u32 bit = 1u << (u32)(w & 31u);
         u32* word = P.bitmap + (w >> 5);
@@ -699,8 +710,11 @@ bool try_fast(const PStep& P, const u64* part, unsigned tiles, cudaStream_t st) 
 template <class Sem> struct PEmitL {
   static void go(const PStep& P, const u64* part, cudaStream_t st) {
     const u64 tiles = (P.total + kEmitTile - 1) / kEmitTile;
-    // membership filter: 1 = new facts also written out, 2 = bitmap only
-    if (std::is_same<Sem, SemUnit>::value && P.bitmap && P.out_words) {
+    // membership filter: 1 = new facts also written out, 2 = bitmap only;
+    // 3 = dense (+)-accumulation of tagged outputs
+    if (!std::is_same<Sem, SemUnit>::value && P.acc) {
+      if (!try_fast<Sem, 3>(P, part, (unsigned)tiles, st)) k_pemit<Sem, 3><<<(unsigned)tiles, 256, 0, st>>>(P, part);
+    } else if (std::is_same<Sem, SemUnit>::value && P.bitmap && P.out_words) {
       if (!try_fast<SemUnit, 1>(P, part, (unsigned)tiles, st))
         k_pemit<SemUnit, 1><<<(unsigned)tiles, 256, 0, st>>>(P, part);
     } else if (std::is_same<Sem, SemUnit>::value && P.bitmap) {
@@ -748,7 +762,9 @@ void pjoin_emit(int sem, const PStep& P, const u64* part, cudaStream_t st) {
   // read the input rows and their offsets once and each matched view key once;
   // write each output (a membership-bitmap word per output in bitmap-only mode)
   const double vb = (P.v_key64 ? 8 : 4) + (sem == SR_UNIT ? 0 : (sem == SR_DIFF_MAX_MIN ? 8 : 4));
-  const double ob = P.out_words ? row_bytes(sem, P.out_w64, false) : 4.0;
+  // an output is written as a word (+ tag), or as a bitmap word, or as a
+  // (+)-accumulation into its dense slot plus its bitmap word
+  const double ob = P.acc ? (sem == SR_MAX_MIN ? 4.0 : 8.0) + 4.0 : (P.out_words ? row_bytes(sem, P.out_w64, false) : 4.0);
   ProfScope ps("join_emit", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + 8.0) + P.total * (vb + ob), st);
   if (P.total) by_sem_p<PEmitL>(sem, P, part, st);
 }

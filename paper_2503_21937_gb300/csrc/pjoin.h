@@ -45,6 +45,9 @@ struct PStep {
   u32* loc; u32* lo32; u64* blk_cnt; const u64* blk_off; u32* err;  // view rows < 2^32
   u64 total; u64 j_begin;
   u32* bitmap; u64* out_count;
+  // dense (+)-accumulation (tagged semirings): each output's tag is added into
+  // acc[output word] and its bit set in `bitmap`; nothing else is written
+  void* acc;
 };
 
 constexpr u64 kLocRows = 1024;  // rows per offset block: 256 threads x 4 consecutive rows

@@ -118,7 +118,9 @@ def test_batched_kinship_matches_oracle():
 # candidate sets larger than one sort: chunked sort + unique + (+)-accumulation
 # ---------------------------------------------------------------------------
 
-CHUNK = {"max_candidates": 4096}
+# sorted candidates in chunks: the dense (+)-accumulation (which needs no
+# candidate sort) is switched off so the tagged runs take the chunked path
+CHUNK = {"max_candidates": 4096, "acc_dense": 0}
 
 
 def test_chunked_tc_unit():
@@ -147,6 +149,28 @@ def test_chunked_batched_kinship_add_mult():
 # ---------------------------------------------------------------------------
 
 FILTER = {"emit_filter": 2}
+
+
+# ---------------------------------------------------------------------------
+# dense (+)-accumulation of tagged candidates vs sorted candidates
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("semiring", ["max_min", "add_mult", "diff_max_min", "diff_add_mult"])
+@pytest.mark.parametrize("opts", [{"acc_dense": 1}, {"acc_dense": 1, "packed_join": 0}, {"acc_dense": 0},
+                                  {"acc_dense": 1, "acc_bits": 12}])
+def test_dense_accumulation(semiring, opts):
+    """Dense accumulation from the packed emission (atomics) and from folded
+    candidates of the general join steps, the sorted path, and a key-width
+    limit that leaves kin (26 bits) sorted while reach (12 bits) is dense;
+    every variant against the oracle, on a linear and a non-linear program
+    with a filter, samples and duplicate derivations."""
+    g = W.grid_reach_instance(16, sub=77)
+    src, dst, p = g["edge"]
+    compare(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, semiring, options=opts)
+    B = W.batched_instance(6)
+    f, c = B["fact"], B["comp"]
+    inputs = {"fact": ((f[0], f[1], f[2]), f[3], f[4]), "comp": ((c[0], c[1], c[2]), None, c[4])}
+    compare(W.KIN_PROGRAM, inputs, semiring, rels=["kin"], options=opts)
 
 
 def test_filter_tc_and_sg():
