@@ -71,6 +71,9 @@ typedef struct lob_stats {
   uint64_t peak_bytes;      /* peak device memory held by the engine during the run */
   double ms;                /* wall time of the run on the engine's stream (CUDA events) */
   uint64_t kernel_launches; /* kernels launched by the run */
+  uint64_t host_syncs;      /* times the host waited for the GPU during the run */
+  uint32_t device_iterations; /* iterations run by the device-driven loop (option "driver") */
+  uint32_t graph_launches;  /* launches of that loop's graph (1 unless a buffer had to grow) */
 } lob_stats;
 
 /* Create an engine on the current CUDA device.  `alloc` may be NULL (stream-
@@ -117,7 +120,15 @@ int lob_add_rule(lob_engine* e, const char* text);
 /* Evaluate all rules to the least fixpoint with the given semiring (Algorithm 1
  * with the semi-naive arms of the appendix's Join rule).  At most max_iters
  * iterations run; on LOB_E_MAXITER the partial state stays readable.  A second
- * call needs lob_reset first (LOB_E_STATE).  `stats` may be NULL. */
+ * call needs lob_reset first (LOB_E_STATE).  `stats` may be NULL.
+ * With option "driver" = 1 (default), a tagged run whose derived relations all
+ * use dense accumulation and whose recursive rules are packed join pipelines
+ * runs its iterations after the first as one CUDA graph: a conditional WHILE
+ * node around two iterations (buffer sets 0 -> 1, then 1 -> 0 under an IF
+ * node), every size and the stop decision held in device memory, and no host
+ * wait between iterations; buffers that turn out too small end the graph
+ * early, grow, and the graph is launched again from the last committed
+ * iteration. */
 int lob_run_to_fixpoint(lob_engine* e, int semiring, uint32_t max_iters, lob_stats* stats);
 
 /* Options chosen by lob_autotune and the timings behind them. */
@@ -215,6 +226,17 @@ int lob_reset(lob_engine* e);
  *                  (default 1; the array takes 2^acc_bits x 4 or 8 bytes)
  *   "acc_bits"     largest key width, in bits, given a dense accumulator
  *                  (1..30, default 28)
+ *   "driver"       1: iterations after the first run as a device-driven
+ *                  CUDA graph when the run qualifies (see
+ *                  lob_run_to_fixpoint) and an earlier host-driven run of
+ *                  this engine recorded the sizes the graph's buffers are
+ *                  planned from (the first qualifying run records them);
+ *                  2: as 1 without waiting for recorded sizes (the buffers
+ *                  start from estimates and grow); 0: the host drives
+ *                  every iteration                                   (default 1)
+ *   "loop_cap_floor" smallest row capacity the device-driven loop plans its
+ *                  buffers with before they grow (256..2^24, default 65536;
+ *                  small values exercise the regrowth path)
  * LOB_E_ARG for an unknown key or a value out of range. */
 int lob_set_option(lob_engine* e, const char* key, int64_t value);
 

@@ -15,13 +15,47 @@ from .lobster import Engine, relation_arities
 
 _DIFF = {"diff_max_min", "diff_add_mult"}
 
+# Idle engines per (program, relations, stream, device, input-size class).  An
+# engine is taken for one forward (+ backward) and returned afterwards, so a
+# training loop reuses its device buffers and the sizes it recorded (the
+# device-driven iteration loop plans from them), and calls of very different
+# sizes do not share capacity plans.
+_IDLE: dict = {}
+_MAX_IDLE = 4
+
+
+def _engine_key(program, names, cols):
+    rows = sum(int(c.shape[1]) for c in cols)
+    stream = torch.cuda.current_stream().cuda_stream
+    return (program, tuple(names), tuple(int(c.shape[0]) for c in cols), stream, torch.cuda.current_device(),
+            max(rows, 1).bit_length())
+
+
+def _take_engine(key, program):
+    idle = _IDLE.get(key)
+    if idle:
+        e = idle.pop()
+        e.reset()
+        return e
+    e = Engine()
+    e.program(program)
+    return e
+
+
+def _give_back(key, e):
+    idle = _IDLE.setdefault(key, [])
+    if len(idle) < _MAX_IDLE:
+        idle.append(e)
+    else:
+        e.close()
+
 
 class _FixpointFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, spec, *probs):
         program, names, cols, samples, semiring, outputs = spec
-        e = Engine()
-        e.program(program)
+        key = _engine_key(program, names, cols)
+        e = _take_engine(key, program)
         for name, c, p, s in zip(names, cols, probs, samples):
             if name not in e.ids:
                 e.declare(name, c.shape[0])
@@ -29,6 +63,7 @@ class _FixpointFn(torch.autograd.Function):
         e.run(semiring)
         rels = [e.read(o, device=True) for o in outputs]
         ctx.engine = e
+        ctx.key = key
         ctx.spec = spec
         ctx.sizes = [c.shape[1] for c in cols]
         ctx.has_prob = [p is not None for p in probs]
@@ -36,13 +71,16 @@ class _FixpointFn(torch.autograd.Function):
         out_cols = [r.cols.clone() for r in rels]
         out_smp = [r.samples.clone() for r in rels]
         ctx.mark_non_differentiable(*out_cols, *out_smp)
+        if semiring not in _DIFF:  # no backward will need this engine's state
+            ctx.engine = None
+            _give_back(key, e)
         return (*tags, *out_cols, *out_smp)
 
     @staticmethod
     def backward(ctx, *grads):
         program, names, cols, samples, semiring, outputs = ctx.spec
         e = ctx.engine
-        if semiring not in _DIFF:
+        if semiring not in _DIFF or e is None:
             raise RuntimeError("gradients need a diff_* semiring")
         gin = {n: torch.zeros(sz, dtype=torch.float32, device="cuda")
                for n, sz, hp in zip(names, ctx.sizes, ctx.has_prob) if hp}
@@ -50,8 +88,8 @@ class _FixpointFn(torch.autograd.Function):
             if g is not None:
                 e.backward(o, g.contiguous().to(torch.float32), gin)
         torch.cuda.synchronize()
-        e.close()
         ctx.engine = None
+        _give_back(ctx.key, e)
         return (None, *[gin.get(n) if hp else None for n, hp in zip(names, ctx.has_prob)])
 
 

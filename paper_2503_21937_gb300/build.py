@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblobster.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["engine.cu", "rules.cu", "join.cu", "pjoin.cu", "sort.cu", "dedup.cu", "bitset.cu", "backward.cu", "noalloc.cu"]
+SOURCES = ["engine.cu", "rules.cu", "join.cu", "pjoin.cu", "sort.cu", "dedup.cu", "bitset.cu", "backward.cu", "noalloc.cu",
+           "driver.cu"]
 
 
 def nvcc() -> str:

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) k_bits_extract(const u32* __restrict__ a,
 template <class K, class C>
 __global__ void __launch_bounds__(256) k_dense_extract(u32* __restrict__ a, u64 nwords, u64 ntiles,
                                                        const u64* __restrict__ tile_off, C* __restrict__ acc,
-                                                       K* __restrict__ out, C* __restrict__ otags) {
+                                                       K* __restrict__ out, C* __restrict__ otags, u64 cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tstage = reinterpret_cast<C*>(smem_raw) + (threadIdx.x >> 5) * 1024;
   K* stage = reinterpret_cast<K*>(reinterpret_cast<C*>(smem_raw) + 8 * 1024) + (threadIdx.x >> 5) * 1024;
@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(256) k_dense_extract(u32* __restrict__ a, u64 
       }
       __syncwarp();
       for (u32 q = lane; q < tot; q += 32) {
+        if (base + q >= cap) break;  // beyond the output's capacity: only the resets happen
         out[base + q] = stage[q];
         otags[base + q] = tstage[q];
       }
@@ -253,13 +254,13 @@ void bits_extract(const u32* a, u32* b, u64 nbits, int key64, void* out, u64 n_o
 // ---------------------------------------------------------------------------
 namespace {
 template <class K, class C>
-void dense_extract_t(u32* a, u64 nbits, void* acc, void* out, void* otags, void* scratch, cudaStream_t st) {
+void dense_extract_t(u32* a, u64 nbits, void* acc, void* out, void* otags, void* scratch, cudaStream_t st, u64 cap) {
   const u64 nw = bit_words(nbits), nt = bit_tiles(nbits);
   const u64* tile_off = reinterpret_cast<const u64*>(scratch) + nt;
   const int smem = 8 * 1024 * (int)(sizeof(K) + sizeof(C));
   allow_dynamic_smem(k_dense_extract<K, C>, smem);
   k_dense_extract<K, C><<<bit_grid(nt), 256, smem, st>>>(a, nw, nt, tile_off, reinterpret_cast<C*>(acc),
-                                                         reinterpret_cast<K*>(out), reinterpret_cast<C*>(otags));
+                                                         reinterpret_cast<K*>(out), reinterpret_cast<C*>(otags), cap);
 }
 template <class Sem>
 void dense_fold_t(const void* keys, int key64, const void* tags, u64 n, void* acc, u32* bm, cudaStream_t st) {
@@ -273,15 +274,15 @@ void dense_fold_t(const void* keys, int key64, const void* tags, u64 n, void* ac
 int dense_cand_bytes(int sem) { return sem == SR_MAX_MIN ? 4 : 8; }
 
 void dense_extract(int sem, int key64, u32* touched, void* acc, u64 nbits, void* okeys, void* otags, u64 n_out,
-                   void* scratch, cudaStream_t st) {
+                   void* scratch, cudaStream_t st, u64 cap) {
   const double cb = dense_cand_bytes(sem), kb = key64 ? 8 : 4;
   ProfScope ps("dense_extract", bit_words(nbits) * 4.0 + n_out * (2.0 * cb + kb + cb), st);
   if (sem == SR_MAX_MIN) {
-    if (key64) dense_extract_t<u64, float>(touched, nbits, acc, okeys, otags, scratch, st);
-    else dense_extract_t<u32, float>(touched, nbits, acc, okeys, otags, scratch, st);
+    if (key64) dense_extract_t<u64, float>(touched, nbits, acc, okeys, otags, scratch, st, cap);
+    else dense_extract_t<u32, float>(touched, nbits, acc, okeys, otags, scratch, st, cap);
   } else {
-    if (key64) dense_extract_t<u64, u64>(touched, nbits, acc, okeys, otags, scratch, st);
-    else dense_extract_t<u32, u64>(touched, nbits, acc, okeys, otags, scratch, st);
+    if (key64) dense_extract_t<u64, u64>(touched, nbits, acc, okeys, otags, scratch, st, cap);
+    else dense_extract_t<u32, u64>(touched, nbits, acc, okeys, otags, scratch, st, cap);
   }
 }
 

@@ -98,7 +98,10 @@ constexpr int kMTile = kMThreads * kMItems;
 // a = number of A elements among the first d merged elements (A first on ties)
 template <class K>
 __global__ void k_merge_path(const K* __restrict__ A, u64 na, const K* __restrict__ B, u64 nb, u64 nparts,
-                             u64* __restrict__ apart) {
+                             u64* __restrict__ apart, const u64* __restrict__ na_dev = nullptr,
+                             const u64* __restrict__ nb_dev = nullptr) {
+  if (na_dev) na = *na_dev < na ? *na_dev : na;  // device-resident sizes, capped by the launch's capacities
+  if (nb_dev) nb = *nb_dev < nb ? *nb_dev : nb;
   const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nparts) return;
   const u64 d = min(t * (u64)kMTile, na + nb);
@@ -122,6 +125,12 @@ template <class K>
 LOB_DEV MergeTile<K> load_merge_tile(const K* A, u64 na, const K* B, u64 nb, const u64* apart, K* sk, u64* err) {
   MergeTile<K> t;
   t.d0 = (u64)blockIdx.x * kMTile;
+  if (t.d0 >= na + nb) {  // a tile past a device-resident total: empty
+    t.a0 = na;
+    t.b0 = nb;
+    t.na_t = t.nb_t = 0;
+    return t;
+  }
   const u64 d1 = min(t.d0 + kMTile, na + nb);
   t.a0 = apart[blockIdx.x];
   const u64 a1 = apart[blockIdx.x + 1];
@@ -172,7 +181,18 @@ struct MergeCtx {
   K* rk; typename Sem::Stored* rt;
   u32 stamp;
   u64* err;
+  const u64* nf_dev; const u64* nu_dev;  // device-resident sizes (nf, nu are then capacities)
+  const u64* stamp_dev;                  // device-resident stamp base (stamp is then added to it)
+  u64 rcap;                              // R entries past it are not written (0: no limit)
 };
+
+template <class K, class Sem>
+LOB_DEV MergeCtx<K, Sem> resolve_sizes(MergeCtx<K, Sem> c) {
+  if (c.nf_dev) c.nf = *c.nf_dev < c.nf ? *c.nf_dev : c.nf;
+  if (c.nu_dev) c.nu = *c.nu_dev < c.nu ? *c.nu_dev : c.nu;
+  if (c.stamp_dev) c.stamp = (u32)*c.stamp_dev + c.stamp;
+  return c;
+}
 
 template <class Sem>
 LOB_DEV typename Sem::Stored u_tag_stored(const void* ut, int u_stored, u64 i) {
@@ -221,8 +241,9 @@ LOB_DEV void walk_items(const MergeCtx<K, Sem>& c, const MergeTile<K>& t, const 
 }
 
 template <class K, class Sem>
-__global__ void __launch_bounds__(kMThreads) k_diffmerge_count(MergeCtx<K, Sem> c, const u64* __restrict__ apart,
+__global__ void __launch_bounds__(kMThreads) k_diffmerge_count(MergeCtx<K, Sem> c0, const u64* __restrict__ apart,
                                                                u64* __restrict__ tile_dup, u64* __restrict__ tile_r) {
+  const MergeCtx<K, Sem> c = resolve_sizes(c0);
   __shared__ K sk[kMTile];
   __shared__ u64 sm[kMThreads / 32 + 1];
   MergeTile<K> t = load_merge_tile(c.fk, c.nf, c.uk, c.nu, apart, sk, c.err);
@@ -241,8 +262,9 @@ __global__ void __launch_bounds__(kMThreads) k_diffmerge_count(MergeCtx<K, Sem> 
 }
 
 template <class K, class Sem>
-__global__ void __launch_bounds__(kMThreads) k_diffmerge_write(MergeCtx<K, Sem> c, const u64* __restrict__ apart,
+__global__ void __launch_bounds__(kMThreads) k_diffmerge_write(MergeCtx<K, Sem> c0, const u64* __restrict__ apart,
                                                                const u64* __restrict__ dup_off, const u64* __restrict__ r_off) {
+  const MergeCtx<K, Sem> c = resolve_sizes(c0);
   __shared__ K sk[kMTile];
   __shared__ u64 sm[kMThreads / 32 + 1];
   MergeTile<K> t = load_merge_tile(c.fk, c.nf, c.uk, c.nu, apart, sk, (u64*)nullptr);
@@ -294,7 +316,7 @@ __global__ void __launch_bounds__(kMThreads) k_diffmerge_write(MergeCtx<K, Sem> 
         dups_before++;
       }
       if (!dup || improved) {
-        if (c.rk) {
+        if (c.rk && (!c.rcap || rpos < c.rcap)) {
           c.rk[rpos] = k;
           if constexpr (Sem::kTags) c.rt[rpos] = u_tag_stored<Sem>(c.ut, c.u_stored, gb);
         }
@@ -527,11 +549,16 @@ void merge_impl(const MergeArgs& a, void* scratch, cudaStream_t st) {
   // inputs were not sorted distinct keys); cleared here so that every call
   // reports only its own inputs
   c.err = a.counts_dev + 2;
+  c.nf_dev = a.nf_dev;
+  c.nu_dev = a.nu_dev;
+  c.stamp_dev = a.stamp_dev;
+  c.rcap = a.rcap;
   cudaMemsetAsync(c.err, 0, sizeof(u64), st);
   const double kb = sizeof(K), sb = Sem::kTags ? sizeof(typename Sem::Stored) : 0, ub = a.u_stored ? sb : (Sem::kTags ? sizeof(typename Sem::Cand) : 0);
   const double fsb = a.fstamp ? 4 : 0;
   { ProfScope ps("merge_path", (tiles + 1) * 8.0, st);
-    k_merge_path<K><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, st>>>(c.fk, a.nf, c.uk, a.nu, tiles + 1, apart); }
+    k_merge_path<K><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, st>>>(c.fk, a.nf, c.uk, a.nu, tiles + 1, apart,
+                                                                          a.nf_dev, a.nu_dev); }
   { ProfScope ps("diffmerge_count", (a.nf + a.nu) * kb, st);
     k_diffmerge_count<K, Sem><<<(unsigned)tiles, kMThreads, 0, st>>>(c, apart, tdup, tr); }
   { ProfScope ps("diffmerge_scan", tiles * 32.0, st);

@@ -132,10 +132,14 @@ void lob_engine::release(DevBuf& b) {
 u64 lob_engine::read_u64(const u64* dev) {
   check(cudaMemcpyAsync(pinned, dev, sizeof(u64), cudaMemcpyDeviceToHost, stream), "readback");
   check(cudaStreamSynchronize(stream), "readback sync");
+  host_syncs++;
   return pinned[0];
 }
 
-void lob_engine::sync() { check(cudaStreamSynchronize(stream), "synchronize"); }
+void lob_engine::sync() {
+  check(cudaStreamSynchronize(stream), "synchronize");
+  host_syncs++;
+}
 
 static void release_view(lob_engine& e, ViewSt& v) {
   for (DevBuf* b : {&v.keys, &v.tags, &v.stamps, &v.keys2, &v.tags2, &v.stamps2}) e.release(*b);
@@ -180,23 +184,6 @@ void lob_engine::release_all() {
 // ---------------------------------------------------------------------------
 static int bitlen(u64 x) { return x ? 64 - __builtin_clzll(x) : 0; }
 
-static int cand_bytes(int sem) {
-  switch (sem) {
-    case SR_UNIT: return 0;
-    case SR_MAX_MIN: return 4;
-    default: return 8;
-  }
-}
-static int stored_bytes(int sem) {
-  switch (sem) {
-    case SR_UNIT: return 0;
-    case SR_DIFF_MAX_MIN: return 8;
-    default: return 4;
-  }
-}
-static bool sem_idempotent(int sem) { return sem == SR_UNIT || sem == SR_MAX_MIN || sem == SR_DIFF_MAX_MIN; }
-static bool sem_stamps(int sem) { return sem == SR_ADD_MULT || sem == SR_DIFF_ADD_MULT; }
-static int sem_kernel(int sem) { return sem == SR_DIFF_ADD_MULT ? SR_ADD_MULT : sem; }
 
 static void make_layout(const lob_engine& e, const RelSt& r, const int* perm, Layout& L) {
   std::memset(&L, 0, sizeof(L));
@@ -1025,6 +1012,7 @@ static void update_secondary_views(lob_engine& e, RelSt& H, u32 k, u64 nr) {
     if (e.pinned[2]) throw LobError(LOB_E_CUDA, "internal error: unsorted input to a view merge");
     const u64 d2 = e.pinned[0];
     W.n = W.n + nr - d2;
+    if (H.dense) note_loop_cap(e, "v" + std::to_string(&H - &e.rels[0]) + "." + std::to_string(vi), W.n);
     std::swap(W.keys, W.keys2);
     std::swap(W.tags, W.tags2);
     std::swap(W.stamps, W.stamps2);
@@ -1163,6 +1151,8 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
       throw LobError(LOB_E_ARG, "join step: 1024 consecutive input rows have 2^32 or more matches");
     const u64 total = e.pinned[0];
     if (!total) return;
+    note_loop_cap(e, "tiles", (total + kEmitTile - 1) / kEmitTile);
+    if (!last) note_loop_cap(e, "bind", total);
     if (last && H.extract) {  // new facts only set their bits in the membership bitmap
       H.touched = true;
       P.out_words = nullptr;
@@ -1356,6 +1346,7 @@ static void dedup_dense(lob_engine& e, RelSt& H, u32 k) {
   e.launches += bits_count(H.dtouched.as<u32>(), nullptr, nbits, e.scratch.p, e.counts.as<u64>() + 1, e.stream);
   e.after_launch("dense count");
   const u64 nu = e.read_u64(e.counts.as<u64>() + 1);
+  note_loop_cap(e, "u" + std::to_string(&H - &e.rels[0]), nu);
   if (!nu) {
     H.last_new = 0;
     return;
@@ -1494,6 +1485,10 @@ static void merge_unique(lob_engine& e, RelSt& H, u32 k, const void* ukeys, cons
   if (e.pinned[2]) throw LobError(LOB_E_CUDA, "internal error: unsorted input to the difference/merge");
   const u64 dups = e.pinned[0], nr = e.pinned[1];
   V.n = V.n + nu - dups;
+  if (H.dense) {
+    note_loop_cap(e, "full" + std::to_string(&H - &e.rels[0]), V.n);
+    note_loop_cap(e, "r" + std::to_string(&H - &e.rels[0]), nr);
+  }
   std::swap(V.keys, V.keys2);
   std::swap(V.tags, V.tags2);
   std::swap(V.stamps, V.stamps2);
@@ -1578,6 +1573,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   if (sem < 0 || sem > 4) throw LobError(LOB_E_ARG, "unknown semiring id");
   e.peak_bytes = e.live_bytes;
   e.launches = 0;
+  const u64 syncs0 = e.host_syncs;
   struct RunEvents {  // destroyed on every exit, the error paths included
     cudaEvent_t a = nullptr, b = nullptr;
     ~RunEvents() {
@@ -1634,6 +1630,14 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
     }
     s.new_facts += total_new;
     if (!total_new) break;
+    if (k == 1) {  // the rest of the run as a device-driven graph, when it qualifies
+      bool taken = false;
+      const int r2 = run_device_loop(e, k, max_iters, s, &taken);
+      if (taken) {
+        rc = r2;
+        break;
+      }
+    }
   }
   for (auto& r : e.rels)
     if (r.keys_stale) materialize_keys(e, r, r.bitmap.as<u32>());
@@ -1652,6 +1656,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
     if (r.idb) s.derived += r.views[0].n;
   s.peak_bytes = e.peak_bytes;
   s.kernel_launches = e.launches;
+  s.host_syncs = e.host_syncs - syncs0;
   e.stats = s;
   e.last_iter = k;
   e.state = 1;
@@ -1759,6 +1764,7 @@ void lob_destroy(lob_engine* e) {
   } catch (...) {
   }
   if (e->pool) cudaMemPoolDestroy(e->pool);
+  if (e->capture_stream) cudaStreamDestroy(e->capture_stream);
   cudaFreeHost(e->pinned);
   delete e;
 }
@@ -2180,6 +2186,8 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "warp_join" && value >= 0 && value <= 2) e->opt_warp_join = (int)value;
     else if (k == "acc_dense" && (value == 0 || value == 1)) e->opt_acc_dense = (int)value;
     else if (k == "acc_bits" && value >= 1 && value <= 30) e->opt_acc_bits = (int)value;
+    else if (k == "driver" && value >= 0 && value <= 2) e->opt_driver = (int)value;
+    else if (k == "loop_cap_floor" && value >= 256 && value <= (1 << 24)) e->opt_loop_cap_floor = (int)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

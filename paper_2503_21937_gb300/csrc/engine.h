@@ -1,5 +1,6 @@
 // Host-side state of one fixpoint engine (internal).
 #pragma once
+#include <algorithm>
 #include <map>
 #include <memory>
 #include <stdexcept>
@@ -187,6 +188,12 @@ struct lob_engine {
   int opt_bitmap_delta = 1;       // filtered relations: 0 never, 1 when predicted cheaper, 2 always read new facts from the bitmap
   int opt_acc_dense = 1;          // tagged semirings: dense (+)-accumulation for head relations of at most opt_acc_bits key bits
   int opt_acc_bits = 28;
+  int opt_driver = 1;             // iterations after the first as a device-driven graph when the run qualifies:
+                                  // 1 once a host-driven run of the program recorded its sizes, 2 always, 0 never
+  int opt_loop_cap_floor = 1 << 16;  // smallest buffer capacity (rows) the device loop plans with
+  std::map<std::string, u64> loop_caps;  // buffer capacities the device loop needed, kept across runs
+  u64 host_syncs = 0;             // host waits for the GPU (statistics)
+  cudaStream_t capture_stream = nullptr;  // private stream the device loop's graph is captured on (created on first use)
   EngineProfiler prof;
   // run state
   int state = 0;  // 0 loading, 1 ran
@@ -218,3 +225,18 @@ struct lob_engine {
 };
 
 void engine_ensure_index(lob_engine& e, ViewSt& v, int prefix);
+// device-driven iterations after iteration k (driver.cu)
+int run_device_loop(lob_engine& e, u32& k, u32 max_iters, lob_stats& s, bool* taken);
+// A size a host-driven iteration reached, kept (with a quarter of slack) so
+// that later device-driven runs of the program plan their buffers from it.
+inline void note_loop_cap(lob_engine& e, const std::string& key, u64 v) {
+  u64& c = e.loop_caps[key];
+  c = std::max<u64>(c, v + v / 4);
+}
+
+// tag widths and update policy per semiring
+inline int cand_bytes(int sem) { return sem == SR_UNIT ? 0 : (sem == SR_MAX_MIN ? 4 : 8); }
+inline int stored_bytes(int sem) { return sem == SR_UNIT ? 0 : (sem == SR_DIFF_MAX_MIN ? 8 : 4); }
+inline bool sem_idempotent(int sem) { return sem == SR_UNIT || sem == SR_MAX_MIN || sem == SR_DIFF_MAX_MIN; }
+inline bool sem_stamps(int sem) { return sem == SR_ADD_MULT || sem == SR_DIFF_ADD_MULT; }
+inline int sem_kernel(int sem) { return sem == SR_DIFF_ADD_MULT ? SR_ADD_MULT : sem; }

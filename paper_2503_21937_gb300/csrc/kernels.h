@@ -37,7 +37,7 @@ size_t sort_scratch_bytes(u64 n, int rb);
 // pay point at the input and are updated to whichever buffer holds the result
 // (the inputs or ktmp/ptmp).  pay_bytes is 0 (no payload), 4 or 8.
 void sort_pairs(int key64, int pay_bytes, void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits, int rb,
-                void* scratch, cudaStream_t st);
+                void* scratch, cudaStream_t st, const u64* n_dev = nullptr);
 int sort_kernel_launches(u64 n, int bits, int rb);
 // Same result with one kernel per digit pass (decoupled look-back); *err is set
 // (never cleared) if a bounded wait gave up, in which case the output is invalid.
@@ -63,6 +63,11 @@ struct MergeArgs {
   void* rkeys; void* rtags;                                         // R: new or improved facts (nullable)
   u32 stamp;                                                        // stamp of new / improved facts
   u64* counts_dev;                                                  // [0] = #dups of U in F, [1] = |R|, [2] = error flag
+  // device-resident sizes (a captured iteration): |F| = *nf_dev, |U| = *nu_dev,
+  // with nf and nu the capacities the launches are sized for
+  const u64* nf_dev; const u64* nu_dev;
+  const u64* stamp_dev;  // when set, new / improved facts get the stamp *stamp_dev + stamp
+  u64 rcap;              // when non-zero, R entries past it are not written (the caller checks |R| against it)
 };
 size_t merge_scratch_bytes(u64 nf, u64 nu);
 void diff_merge(const MergeArgs& a, void* scratch, cudaStream_t st);
@@ -164,17 +169,23 @@ void bits_extract(const u32* a, u32* b, u64 nbits, int key64, void* out, u64 n_o
 // order with their reduced tags (n_out of them) and resets acc and touched.
 int dense_cand_bytes(int sem);
 void dense_fold(int sem, int key64, const void* keys, const void* tags, u64 n, void* acc, u32* touched, cudaStream_t st);
+// (keys past `cap` are not written, but every touched slot is reset)
 void dense_extract(int sem, int key64, u32* touched, void* acc, u64 nbits, void* okeys, void* otags, u64 n_out,
-                   void* scratch, cudaStream_t st);
+                   void* scratch, cudaStream_t st, u64 cap = ~0ull);
 // merge two sorted key lists known to share no key (keys only)
 size_t merge_nodup_scratch_bytes(u64 na, u64 nb);
 void merge_nodup(int key64, const void* a, u64 na, const void* b, u64 nb, void* out, void* scratch, cudaStream_t st);
 
-void build_dense_index(const Layout& L, int prefix_len, const void* keys, u64 n, u64* offs, u64 domain, cudaStream_t st);
+// n_dev (optional): the key count in device memory, n its capacity;
+// changed_dev (optional): when it holds 0 the view is unchanged and the index is kept
+void build_dense_index(const Layout& L, int prefix_len, const void* keys, u64 n, u64* offs, u64 domain, cudaStream_t st,
+                       const u64* n_dev = nullptr, const u64* changed_dev = nullptr);
+// copy n elements of elem_bytes (a multiple of 4); n_dev as above
+void copy_elems(void* dst, const void* src, u64 n, int elem_bytes, const u64* n_dev, cudaStream_t st);
 // re-encode keys of layout `from` into layout `to`; view column j of `to` is
 // relation column perm_to[j], view column j of `from` is relation column perm_from[j]
 void repack_keys(const Layout& from, const int* perm_from, const Layout& to, const int* perm_to, const void* in, void* out,
-                 u64 n, cudaStream_t st);
+                 u64 n, cudaStream_t st, const u64* n_dev = nullptr);
 void pack_rows(const Layout& L, const u32* cols, u64 stride, const u32* samples, u64 n, void* keys, u32* rows,
                cudaStream_t st);
 void read_rows(int sem, const Layout& L, const int* perm, const void* keys, const void* tags, u64 n, u32* cols,

@@ -8,6 +8,8 @@
 // checks and the output word, so the kernels only shift, mask, compare and OR
 // values held in registers.  A dropped binding row is the all-ones word (no
 // field is ever all ones, so no valid row is).
+#include <algorithm>
+
 #include "pjoin.h"
 
 namespace {
@@ -80,10 +82,14 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
   __shared__ u32 sm[256 / 32 + 1];
   __shared__ u32 th_inc[256];
   __shared__ u64 block_base;
-  const u64 j0 = P.j_begin + (u64)blockIdx.x * kEmitTile;
-  const u64 j_end = P.j_begin + P.total;
-  const u64 r0 = part[blockIdx.x];
-  const u64 r_end = part[blockIdx.x + 1];
+  // tiles of kEmitTile outputs; a block takes tiles blockIdx.x, + gridDim.x, ...
+  // (one tile per block when the grid has one block per tile)
+  const u64 j_end = P.j_begin + dev_size(P.total, P.total_dev);
+  for (u64 tile = blockIdx.x;; tile += gridDim.x) {
+  const u64 j0 = P.j_begin + tile * kEmitTile;
+  if (j0 >= j_end) break;
+  const u64 r0 = part[tile];
+  const u64 r_end = part[tile + 1];
   for (int i = threadIdx.x; i < kEmitTile; i += 256) row_of[i] = 0;
   __syncthreads();
   for (u64 r = r0 + 1 + threadIdx.x; r <= r_end; r += 256) {
@@ -107,6 +113,7 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
   for (int i = 0; i < kItems; i++) row_of[threadIdx.x * kItems + i] = loc[i] > ex ? loc[i] : ex;
   __syncthreads();
   const u64 invalid_out = P.out_w64 ? ~0ull : 0xFFFFFFFFull;
+  const u32 vsv = P.stamp_dev ? (u32)*P.stamp_dev + P.v_stamp_val : P.v_stamp_val;
   u64 kept[kFilter == 1 ? kItems : 1];
   u32 nkeep = 0;
 #pragma unroll 2
@@ -120,8 +127,7 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
     input_row<Sem>(P, r, wi, tag);
     const u64 wv = load_word(P.v_keys, P.v_key64, v);
     bool ok = P.v_stamp_mode == STAMP_NONE ||
-              (P.v_stamp_mode == STAMP_LT ? (P.v_stamp[v] & 0x7FFFFFFFu) < P.v_stamp_val
-                                          : (P.v_stamp[v] & 0x7FFFFFFFu) == P.v_stamp_val);
+              (P.v_stamp_mode == STAMP_LT ? (P.v_stamp[v] & 0x7FFFFFFFu) < vsv : (P.v_stamp[v] & 0x7FFFFFFFu) == vsv);
     ok = ok && checks_ok(P.checks, P.n_checks, wi, wv);
     const u64 w = ok ? compose(P.out, P.n_out, wi, wv) : invalid_out;
     if constexpr (kFilter == 3) {
@@ -171,6 +177,8 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
       __syncthreads();
       for (u32 i = threadIdx.x; i < tot; i += 256) reinterpret_cast<u32*>(P.out_words)[base + i] = row_of[i];
     }
+  }
+  __syncthreads();  // shared memory is reused by the block's next tile
   }
 }
 
@@ -227,10 +235,14 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
   __shared__ u32 sm[256 / 32 + 1];
   __shared__ u32 th_inc[256];
   __shared__ u64 block_base;
-  const u64 j0 = P.j_begin + (u64)blockIdx.x * kEmitTile;
-  const u64 j_end = P.j_begin + P.total;
-  const u64 r0 = part[blockIdx.x];
-  const u64 r_end = part[blockIdx.x + 1];
+  // tiles of kEmitTile outputs; a block takes tiles blockIdx.x, + gridDim.x, ...
+  // (one tile per block when the grid has one block per tile)
+  const u64 j_end = P.j_begin + dev_size(P.total, P.total_dev);
+  for (u64 tile = blockIdx.x;; tile += gridDim.x) {
+  const u64 j0 = P.j_begin + tile * kEmitTile;
+  if (j0 >= j_end) break;
+  const u64 r0 = part[tile];
+  const u64 r_end = part[tile + 1];
   for (int i = threadIdx.x; i < kEmitTile; i += 256) row_of[i] = 0;
   __syncthreads();
   for (u64 r = r0 + 1 + threadIdx.x; r <= r_end; r += 256) {
@@ -272,6 +284,7 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
   }
   const u64 invalid_out = P.out_w64 ? ~0ull : 0xFFFFFFFFull;
   const u64 invalid_in = P.in_w64 ? ~0ull : 0xFFFFFFFFull;
+  const u32 vsv = P.stamp_dev ? (u32)*P.stamp_dev + P.v_stamp_val : P.v_stamp_val;
   u64 kept[kFilter == 1 ? kItems : 1];
   u32 nkeep = 0;
   constexpr int B = kFilter == 2 ? 4 : 2;  // outputs whose loads are issued together (keeps registers, and occupancy, up)
@@ -306,7 +319,7 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
       const u64 v = (u64)lov[b] + (j - offv[b]);
       if (P.v_stamp_mode != STAMP_NONE) {
         const u32 st = P.v_stamp[v] & 0x7FFFFFFFu;
-        ok = ok && (P.v_stamp_mode == STAMP_LT ? st < P.v_stamp_val : st == P.v_stamp_val);
+        ok = ok && (P.v_stamp_mode == STAMP_LT ? st < vsv : st == vsv);
       }
 #pragma unroll
       for (int q = 0; q < NCHK; q++) ok = ok && ((reg_pick(ca[q], wi[b], wv[b]) == reg_pick(cb[q], wi[b], wv[b])) == ceq[q]);
@@ -369,6 +382,8 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
       for (u32 i = threadIdx.x; i < tot; i += 256) reinterpret_cast<u32*>(P.out_words)[base + i] = row_of[i];
     }
   }
+  __syncthreads();  // shared memory is reused by the block's next tile
+  }
 }
 
 // Count: the matches of every input row in the probed view (lo32: first matched
@@ -391,9 +406,14 @@ __global__ void __launch_bounds__(256) k_pcount_loc(const __grid_constant__ PSte
   }
   const u64 invalid_in = P.in_w64 ? ~0ull : 0xFFFFFFFFull;
   const bool vec_in = (reinterpret_cast<uintptr_t>(P.in_words) & 15) == 0;
+  const u64 n_in = dev_size(P.n_in, P.n_in_dev);  // blocks past it get count 0
   for (u64 b = blockIdx.x; b < n_blk; b += gridDim.x) {
+    if (b * kLocRows >= n_in) {
+      if (threadIdx.x == 0) P.blk_cnt[b] = 0;
+      continue;
+    }
     const u64 r0 = b * kLocRows + (u64)threadIdx.x * 4;
-    const bool full = r0 + 4 <= P.n_in;
+    const bool full = r0 + 4 <= n_in;
     u64 w[4];
     if (full && vec_in) {
       if (P.in_w64) {
@@ -406,7 +426,7 @@ __global__ void __launch_bounds__(256) k_pcount_loc(const __grid_constant__ PSte
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < 4; i++) w[i] = r0 + i < P.n_in ? load_word(P.in_words, P.in_w64, r0 + i) : invalid_in;
+      for (int i = 0; i < 4; i++) w[i] = r0 + i < n_in ? load_word(P.in_words, P.in_w64, r0 + i) : invalid_in;
     }
     u32 c[4], lo[4];
 #pragma unroll
@@ -443,14 +463,17 @@ __global__ void __launch_bounds__(256) k_pcount_loc(const __grid_constant__ PSte
           if (P.index_mode == INDEX_DENSE) {
             l = P.dense_offs[pv];
             h = P.dense_offs[pv + 1];
-          } else if (P.whole_view) {
-            l = 0;
-            h = P.v_n;
           } else {
-            const u64 klo = pv << P.rest_shift;
-            const u64 khi = klo + (1ull << P.rest_shift);
-            l = lower_bound_w(P.v_keys, P.v_key64, P.v_n, klo);
-            h = khi < klo ? P.v_n : lower_bound_w(P.v_keys, P.v_key64, P.v_n, khi);
+            const u64 vn = dev_size(P.v_n, P.v_n_dev);
+            if (P.whole_view) {
+              l = 0;
+              h = vn;
+            } else {
+              const u64 klo = pv << P.rest_shift;
+              const u64 khi = klo + (1ull << P.rest_shift);
+              l = lower_bound_w(P.v_keys, P.v_key64, vn, klo);
+              h = khi < klo ? vn : lower_bound_w(P.v_keys, P.v_key64, vn, khi);
+            }
           }
           c[i] = (u32)(h - l);
           lo[i] = (u32)l;
@@ -472,7 +495,7 @@ __global__ void __launch_bounds__(256) k_pcount_loc(const __grid_constant__ PSte
     } else {
 #pragma unroll
       for (int i = 0; i < 4; i++)
-        if (r0 + i < P.n_in) {
+        if (r0 + i < n_in) {
           P.loc[r0 + i] = lc[i];
           P.lo32[r0 + i] = lo[i];
         }
@@ -488,11 +511,17 @@ __global__ void __launch_bounds__(256) k_pcount_loc(const __grid_constant__ PSte
 // part[t] = the last row whose first output is at or before the tile's start
 __global__ void k_ppartition(const __grid_constant__ PStep P, u64 n_blk, u64 ntiles, u64* __restrict__ part) {
   const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  const u64 total = dev_size(P.total, P.total_dev);
+  const u64 n_in = dev_size(P.n_in, P.n_in_dev);
+  if (P.total_dev) {  // device-resident total: the tiles it needs, out of the launch's
+    if (!total) return;
+    ntiles = (total + kEmitTile - 1) / kEmitTile;
+  }
   if (t > ntiles) return;
-  const u64 j = t == ntiles ? P.j_begin + P.total - 1 : P.j_begin + t * (u64)kEmitTile;
+  const u64 j = t == ntiles ? P.j_begin + total - 1 : P.j_begin + t * (u64)kEmitTile;
   const u64 b = upper_bound_dev<u64>(P.blk_off, 0, n_blk, j) - 1;
   const u64 lo = b * kLocRows;
-  const u64 hi = lo + kLocRows < P.n_in ? lo + kLocRows : P.n_in;
+  const u64 hi = lo + kLocRows < n_in ? lo + kLocRows : n_in;
   part[t] = upper_bound_dev<u32>(P.loc, lo, hi, (u32)(j - P.blk_off[b])) - 1;
 }
 
@@ -709,7 +738,10 @@ bool try_fast(const PStep& P, const u64* part, unsigned tiles, cudaStream_t st) 
 }
 template <class Sem> struct PEmitL {
   static void go(const PStep& P, const u64* part, cudaStream_t st) {
-    const u64 tiles = (P.total + kEmitTile - 1) / kEmitTile;
+    // one block per tile; with a device-resident total, a fixed grid of
+    // blocks walks the tiles the total needs (P.total is then a capacity)
+    const u64 ntile = (P.total + kEmitTile - 1) / kEmitTile;
+    const u64 tiles = P.total_dev ? std::min<u64>(ntile, 152ull * 8) : ntile;
     // membership filter: 1 = new facts also written out, 2 = bitmap only;
     // 3 = dense (+)-accumulation of tagged outputs
     if (!std::is_same<Sem, SemUnit>::value && P.acc) {

@@ -48,7 +48,16 @@ struct PStep {
   // dense (+)-accumulation (tagged semirings): each output's tag is added into
   // acc[output word] and its bit set in `bitmap`; nothing else is written
   void* acc;
+  // device-resident sizes (a captured iteration): when set, the row count and
+  // the output count are read from device memory; n_in and total are then
+  // the capacities the launch grids and buffers were sized for
+  const u64* n_in_dev; const u64* total_dev;
+  const u64* v_n_dev;     // the probed view's row count (v_n its capacity)
+  const u64* stamp_dev;   // when set, the stamp filters compare with *stamp_dev + v_stamp_val
 };
+
+// size in device memory, capped by the capacity it was launched for
+LOB_DEV u64 dev_size(u64 cap, const u64* dev) { return dev ? (*dev < cap ? *dev : cap) : cap; }
 
 constexpr u64 kLocRows = 1024;  // rows per offset block: 256 threads x 4 consecutive rows
 constexpr u32 kErrLocOverflow = 1;  // a block's matches reached 2^32

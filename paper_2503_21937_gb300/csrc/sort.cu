@@ -36,8 +36,10 @@ struct SortCfg {
 
 template <class K, class P, int RB>
 __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const K* __restrict__ keys, u64 n, int shift,
-                                                                u32* __restrict__ hist, u64 ntiles) {
+                                                                u32* __restrict__ hist, u64 ntiles,
+                                                                const u64* __restrict__ n_dev) {
   constexpr int D = 1 << RB;
+  if (n_dev) n = *n_dev < n ? *n_dev : n;  // tiles past it count nothing
   constexpr int IT = SortCfg<K, P>::kItems;
   __shared__ u32 h[kSortWarps][D];
   for (int i = threadIdx.x; i < kSortWarps * D; i += kSortThreads) (&h[0][0])[i] = 0;
@@ -85,8 +87,11 @@ LOB_DEV u32 same_digit_lanes(u32 d, bool valid) {
 template <class K, class P, int RB>
 __global__ void __launch_bounds__(kSortThreads, 2) k_radix_scatter(const K* __restrict__ keys, const P* __restrict__ pay,
                                                                    K* __restrict__ okeys, P* __restrict__ opay, u64 n,
-                                                                   int shift, const u32* __restrict__ offs, u64 ntiles) {
+                                                                   int shift, const u32* __restrict__ offs, u64 ntiles,
+                                                                   const u64* __restrict__ n_dev) {
   constexpr int D = 1 << RB;
+  if (n_dev) n = *n_dev < n ? *n_dev : n;
+  if ((u64)blockIdx.x * SortCfg<K, P>::kTile >= n) return;  // a tile past a device-resident count
   constexpr int IT = SortCfg<K, P>::kItems;
   constexpr int TILE = SortCfg<K, P>::kTile;
   constexpr bool kPay = !std::is_same<P, NoPay>::value;
@@ -172,7 +177,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_radix_scatter(const K* __re
 }
 
 template <class K, class P, int RB>
-void sort_impl(void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits, void* scratch, cudaStream_t st) {
+void sort_impl(void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits, void* scratch, cudaStream_t st,
+               const u64* n_dev) {
   constexpr int D = 1 << RB;
   constexpr int TILE = SortCfg<K, P>::kTile;
   constexpr int SMEM = SortCfg<K, P>::kSmem;
@@ -189,7 +195,7 @@ void sort_impl(void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits,
   for (int shift = 0; shift < bits; shift += RB) {
     {
       ProfScope ps("radix_upsweep", n * kb + (double)D * ntiles * 4, st);
-      k_radix_upsweep<K, P, RB><<<(unsigned)ntiles, kSortThreads, 0, st>>>(src_k, n, shift, hist, ntiles);
+      k_radix_upsweep<K, P, RB><<<(unsigned)ntiles, kSortThreads, 0, st>>>(src_k, n, shift, hist, ntiles, n_dev);
     }
     {
       ProfScope ps("radix_digit_scan", (double)D * ntiles * 8, st);
@@ -198,7 +204,7 @@ void sort_impl(void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits,
     {
       ProfScope ps("radix_scatter", 2.0 * n * (kb + pb) + (double)D * ntiles * 4, st);
       k_radix_scatter<K, P, RB><<<(unsigned)ntiles, kSortThreads, SMEM, st>>>(src_k, src_p, dst_k, dst_p, n, shift, hist,
-                                                                               ntiles);
+                                                                               ntiles, n_dev);
     }
     std::swap(src_k, dst_k);
     std::swap(src_p, dst_p);
@@ -208,11 +214,12 @@ void sort_impl(void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits,
 }
 
 template <class K, class P>
-void sort_rb(int rb, void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits, void* scratch, cudaStream_t st) {
+void sort_rb(int rb, void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits, void* scratch, cudaStream_t st,
+             const u64* n_dev) {
   switch (rb) {
-    case 4: sort_impl<K, P, 4>(keys, pay, ktmp, ptmp, n, bits, scratch, st); break;
-    case 6: sort_impl<K, P, 6>(keys, pay, ktmp, ptmp, n, bits, scratch, st); break;
-    default: sort_impl<K, P, 8>(keys, pay, ktmp, ptmp, n, bits, scratch, st); break;
+    case 4: sort_impl<K, P, 4>(keys, pay, ktmp, ptmp, n, bits, scratch, st, n_dev); break;
+    case 6: sort_impl<K, P, 6>(keys, pay, ktmp, ptmp, n, bits, scratch, st, n_dev); break;
+    default: sort_impl<K, P, 8>(keys, pay, ktmp, ptmp, n, bits, scratch, st, n_dev); break;
   }
 }
 
@@ -479,16 +486,16 @@ size_t sort_scratch_bytes(u64 n, int rb) {
 }
 
 void sort_pairs(int key64, int pay_bytes, void** keys, void** pay, void* ktmp, void* ptmp, u64 n, int bits, int rb,
-                void* scratch, cudaStream_t st) {
+                void* scratch, cudaStream_t st, const u64* n_dev) {
   rb = sort_supported_radix_bits(rb);
   if (key64) {
-    if (pay_bytes == 0) sort_rb<u64, NoPay>(rb, keys, pay, ktmp, ptmp, n, bits, scratch, st);
-    else if (pay_bytes == 4) sort_rb<u64, u32>(rb, keys, pay, ktmp, ptmp, n, bits, scratch, st);
-    else sort_rb<u64, u64>(rb, keys, pay, ktmp, ptmp, n, bits, scratch, st);
+    if (pay_bytes == 0) sort_rb<u64, NoPay>(rb, keys, pay, ktmp, ptmp, n, bits, scratch, st, n_dev);
+    else if (pay_bytes == 4) sort_rb<u64, u32>(rb, keys, pay, ktmp, ptmp, n, bits, scratch, st, n_dev);
+    else sort_rb<u64, u64>(rb, keys, pay, ktmp, ptmp, n, bits, scratch, st, n_dev);
   } else {
-    if (pay_bytes == 0) sort_rb<u32, NoPay>(rb, keys, pay, ktmp, ptmp, n, bits, scratch, st);
-    else if (pay_bytes == 4) sort_rb<u32, u32>(rb, keys, pay, ktmp, ptmp, n, bits, scratch, st);
-    else sort_rb<u32, u64>(rb, keys, pay, ktmp, ptmp, n, bits, scratch, st);
+    if (pay_bytes == 0) sort_rb<u32, NoPay>(rb, keys, pay, ktmp, ptmp, n, bits, scratch, st, n_dev);
+    else if (pay_bytes == 4) sort_rb<u32, u32>(rb, keys, pay, ktmp, ptmp, n, bits, scratch, st, n_dev);
+    else sort_rb<u32, u64>(rb, keys, pay, ktmp, ptmp, n, bits, scratch, st, n_dev);
   }
 }
 

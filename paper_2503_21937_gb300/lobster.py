@@ -46,7 +46,8 @@ class LobsterError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_uint32), ("semiring", ctypes.c_uint32), ("derived", ctypes.c_uint64),
                 ("candidates", ctypes.c_uint64), ("new_facts", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
-                ("ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64)]
+                ("ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64), ("host_syncs", ctypes.c_uint64),
+                ("device_iterations", ctypes.c_uint32), ("graph_launches", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

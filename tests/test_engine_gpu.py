@@ -469,3 +469,97 @@ def test_runs_are_bitwise_repeatable():
             e.close()
         assert np.array_equal(outs[0].cols, outs[1].cols)
         assert np.array_equal(outs[0].tags, outs[1].tags)
+
+
+# ---------------------------------------------------------------------------
+# device-driven iteration loop (a CUDA graph after the first iteration) vs the
+# host-driven loop and the oracle
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("semiring", ["max_min", "add_mult", "diff_max_min", "diff_add_mult"])
+@pytest.mark.parametrize("opts", [{"driver": 2}, {"driver": 2, "loop_cap_floor": 256}, {"driver": 0}])
+def test_device_loop_matches_oracle(semiring, opts):
+    """Linear (grid reachability) and non-linear, filtered, batched (kinship)
+    programs; with a capacity floor of 256 rows the loop's buffers overflow and
+    grow several times mid-run, each time resuming from the last committed
+    iteration."""
+    g = W.grid_reach_instance(20, sub=78)
+    src, dst, p = g["edge"]
+    st, _ = compare(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, semiring, options=opts)
+    if opts["driver"]:
+        assert st["device_iterations"] > 0 and st["iterations"] > 30
+        if "loop_cap_floor" not in opts:
+            assert st["graph_launches"] == 1
+    B = W.batched_instance(8)
+    f, c = B["fact"], B["comp"]
+    inputs = {"fact": ((f[0], f[1], f[2]), f[3], f[4]), "comp": ((c[0], c[1], c[2]), None, c[4])}
+    st, _ = compare(W.KIN_PROGRAM, inputs, semiring, rels=["kin"], options=opts)
+    if opts["driver"]:
+        assert st["device_iterations"] > 0
+        if "loop_cap_floor" in opts:
+            assert st["graph_launches"] > 1
+
+
+@pytest.mark.parametrize("semiring", ["max_min", "add_mult"])
+def test_device_loop_max_iters(semiring):
+    """LOB_E_MAXITER inside the device loop leaves the same state as the host loop."""
+    from paper_2503_21937_gb300 import LobsterError
+    g = W.grid_reach_instance(16, sub=79)
+    src, dst, p = g["edge"]
+    inputs = {"edge": ((src, dst), p), "start": (g["start"],)}
+    got = []
+    for driver in (2, 0):
+        from paper_2503_21937_gb300 import Engine
+        e = Engine()
+        e.program(W.REACH_PROGRAM)
+        e.set_option("driver", driver)
+        e.load("edge", (src, dst), p)
+        e.load("start", g["start"])
+        with pytest.raises(LobsterError, match="MAXITER"):
+            e.run(semiring, max_iters=9)
+        got.append(e.read("reach"))
+        e.close()
+    assert np.array_equal(got[0].cols, got[1].cols)
+    assert np.array_equal(got[0].tags, got[1].tags)
+
+
+def test_device_loop_gradients_match_host_loop():
+    """Backward after a device-driven forward uses the iteration records the
+    loop kept on the device: gradients equal the host loop's."""
+    B = W.batched_instance(6)
+    e_ = B["edge"]
+    inputs = {"edge": ((e_[0], e_[1]), e_[2], e_[3]), "start": ((B["start"][0],), None, B["start"][2])}
+    grads = []
+    for driver in (2, 0):
+        e, st, got = engine_run(W.REACH_PROGRAM, inputs, "diff_add_mult", options={"driver": driver}, read=["reach"])
+        gin = {"edge": np.zeros(len(e_[0]), np.float32)}
+        e.backward("reach", np.linspace(-1, 1, got["reach"].cols.shape[1]).astype(np.float32), gin)
+        grads.append(gin["edge"])
+        e.close()
+    np.testing.assert_allclose(grads[0], grads[1], rtol=1e-5, atol=1e-6)
+
+
+def test_device_loop_takes_over_after_a_recorded_run():
+    """Default option (driver 1): the first run of an engine is host-driven and
+    records the sizes; a second run on the same engine plans the graph from
+    them, launches it once, and waits for the host a few times per run, not
+    per iteration; both runs match the oracle."""
+    from paper_2503_21937_gb300 import Engine
+    g = W.grid_reach_instance(24, sub=80)
+    src, dst, p = g["edge"]
+    want = compare(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, "max_min")[1].relation("reach")
+    e = Engine()
+    e.program(W.REACH_PROGRAM)
+    stats = []
+    for _ in range(2):
+        e.reset()
+        e.load("edge", (src, dst), p)
+        e.load("start", g["start"])
+        stats.append(e.run("max_min"))
+        got = e.read("reach")
+        assert np.array_equal(got.cols, want.cols)
+        assert np.array_equal(got.tags, want.tags.astype(np.float32))
+    e.close()
+    assert stats[0]["device_iterations"] == 0 and stats[1]["device_iterations"] == stats[1]["iterations"] - 1
+    assert stats[1]["graph_launches"] == 1
+    assert stats[1]["host_syncs"] < stats[0]["host_syncs"] / 5
