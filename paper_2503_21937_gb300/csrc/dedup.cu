@@ -99,9 +99,12 @@ constexpr int kMTile = kMThreads * kMItems;
 template <class K>
 __global__ void k_merge_path(const K* __restrict__ A, u64 na, const K* __restrict__ B, u64 nb, u64 nparts,
                              u64* __restrict__ apart, const u64* __restrict__ na_dev = nullptr,
-                             const u64* __restrict__ nb_dev = nullptr) {
+                             const u64* __restrict__ nb_dev = nullptr, void* const* a_pp = nullptr,
+                             int skip_empty = 0) {
   if (na_dev) na = *na_dev < na ? *na_dev : na;  // device-resident sizes, capped by the launch's capacities
   if (nb_dev) nb = *nb_dev < nb ? *nb_dev : nb;
+  if (skip_empty && nb == 0) return;
+  if (a_pp) A = reinterpret_cast<const K*>(a_pp[0]);
   const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nparts) return;
   const u64 d = min(t * (u64)kMTile, na + nb);
@@ -184,6 +187,8 @@ struct MergeCtx {
   const u64* nf_dev; const u64* nu_dev;  // device-resident sizes (nf, nu are then capacities)
   const u64* stamp_dev;                  // device-resident stamp base (stamp is then added to it)
   u64 rcap;                              // R entries past it are not written (0: no limit)
+  void* const* f_pp; void* const* o_pp; void* const* r_pp;  // device-resident buffer pointers
+  int skip_empty;
 };
 
 template <class K, class Sem>
@@ -191,6 +196,20 @@ LOB_DEV MergeCtx<K, Sem> resolve_sizes(MergeCtx<K, Sem> c) {
   if (c.nf_dev) c.nf = *c.nf_dev < c.nf ? *c.nf_dev : c.nf;
   if (c.nu_dev) c.nu = *c.nu_dev < c.nu ? *c.nu_dev : c.nu;
   if (c.stamp_dev) c.stamp = (u32)*c.stamp_dev + c.stamp;
+  if (c.f_pp) {
+    c.fk = reinterpret_cast<const K*>(c.f_pp[0]);
+    c.ft = reinterpret_cast<const typename Sem::Stored*>(c.f_pp[1]);
+    c.fs = reinterpret_cast<const u32*>(c.f_pp[2]);
+  }
+  if (c.o_pp) {
+    c.ok = reinterpret_cast<K*>(c.o_pp[0]);
+    c.ot = reinterpret_cast<typename Sem::Stored*>(c.o_pp[1]);
+    c.os = reinterpret_cast<u32*>(c.o_pp[2]);
+  }
+  if (c.r_pp) {
+    c.rk = reinterpret_cast<K*>(c.r_pp[0]);
+    c.rt = reinterpret_cast<typename Sem::Stored*>(c.r_pp[1]);
+  }
   return c;
 }
 
@@ -244,6 +263,13 @@ template <class K, class Sem>
 __global__ void __launch_bounds__(kMThreads) k_diffmerge_count(MergeCtx<K, Sem> c0, const u64* __restrict__ apart,
                                                                u64* __restrict__ tile_dup, u64* __restrict__ tile_r) {
   const MergeCtx<K, Sem> c = resolve_sizes(c0);
+  if (c.skip_empty && c.nu == 0) {  // nothing to merge: zero counts, so the totals read 0
+    if (threadIdx.x == 0) {
+      tile_dup[blockIdx.x] = 0;
+      tile_r[blockIdx.x] = 0;
+    }
+    return;
+  }
   __shared__ K sk[kMTile];
   __shared__ u64 sm[kMThreads / 32 + 1];
   MergeTile<K> t = load_merge_tile(c.fk, c.nf, c.uk, c.nu, apart, sk, c.err);
@@ -265,6 +291,7 @@ template <class K, class Sem>
 __global__ void __launch_bounds__(kMThreads) k_diffmerge_write(MergeCtx<K, Sem> c0, const u64* __restrict__ apart,
                                                                const u64* __restrict__ dup_off, const u64* __restrict__ r_off) {
   const MergeCtx<K, Sem> c = resolve_sizes(c0);
+  if (c.skip_empty && c.nu == 0) return;
   __shared__ K sk[kMTile];
   __shared__ u64 sm[kMThreads / 32 + 1];
   MergeTile<K> t = load_merge_tile(c.fk, c.nf, c.uk, c.nu, apart, sk, (u64*)nullptr);
@@ -553,12 +580,16 @@ void merge_impl(const MergeArgs& a, void* scratch, cudaStream_t st) {
   c.nu_dev = a.nu_dev;
   c.stamp_dev = a.stamp_dev;
   c.rcap = a.rcap;
+  c.f_pp = a.f_pp;
+  c.o_pp = a.o_pp;
+  c.r_pp = a.r_pp;
+  c.skip_empty = a.skip_empty;
   cudaMemsetAsync(c.err, 0, sizeof(u64), st);
   const double kb = sizeof(K), sb = Sem::kTags ? sizeof(typename Sem::Stored) : 0, ub = a.u_stored ? sb : (Sem::kTags ? sizeof(typename Sem::Cand) : 0);
   const double fsb = a.fstamp ? 4 : 0;
   { ProfScope ps("merge_path", (tiles + 1) * 8.0, st);
     k_merge_path<K><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, st>>>(c.fk, a.nf, c.uk, a.nu, tiles + 1, apart,
-                                                                          a.nf_dev, a.nu_dev); }
+                                                                          a.nf_dev, a.nu_dev, a.f_pp, a.skip_empty); }
   { ProfScope ps("diffmerge_count", (a.nf + a.nu) * kb, st);
     k_diffmerge_count<K, Sem><<<(unsigned)tiles, kMThreads, 0, st>>>(c, apart, tdup, tr); }
   { ProfScope ps("diffmerge_scan", tiles * 32.0, st);

@@ -3,20 +3,20 @@
 //
 // After the first iteration (run by the host loop, which fires the rules whose
 // delta atom is an input relation), the remaining iterations of a tagged run
-// run as one instantiated CUDA graph:
-//
-//   WHILE (not stopped):
-//     iteration on buffer set 0 -> 1     (begin, index rebuilds, join arms,
-//                                          dense read-out, difference+merge,
-//                                          secondary views, end)
-//     IF (not stopped):
-//       iteration on buffer set 1 -> 0
+// run as one instantiated CUDA graph: a conditional WHILE node whose body is
+// one iteration -- begin, index rebuilds, join arms, dense read-out,
+// difference+merge, secondary views, end -- and whose condition the body's
+// last kernel sets from the device state.
 //
 // Every size -- rows of a recent set, outputs of a join step, unique
 // candidates, |F| -- lives in a device state block; kernels read it there and
-// their grids are sized from capacities.  The begin kernel decides which arms
-// run (the host loop's skip rules), the end kernel commits the iteration's
-// sizes, flips the buffer parity and decides whether to stop (no new facts,
+// their grids are sized from capacities.  Each relation's views and recent
+// set are double-buffered with their own parity: the begin kernel resolves
+// this iteration's current and next buffers into a device pointer table that
+// the kernels read, the merges of a relation that received no candidates do
+// nothing, and the end kernel flips only what was written.  The begin kernel
+// also decides which arms run (the host loop's skip rules); the end kernel
+// commits the iteration's sizes and decides whether to stop (no new facts,
 // max_iters, or a capacity overflow).  A guard kernel after each
 // size-producing step records an overflow; the iteration then ends without
 // committing, so the last committed state stays intact in its buffers, and
@@ -35,13 +35,14 @@ constexpr int kGMaxRels = 16, kGMaxArms = 32, kGMaxSteps = 8, kGMaxViews = 4, kG
 constexpr int kRelSlots = 8 + 4 * kGMaxViews;
 constexpr int kArmSlots = 1 + kGMaxSteps;
 // header slots of the state block
-enum : int { S_K = 0, S_STOP, S_PARITY, S_OVERFLOW, S_EMITTED, S_NEW, S_ERR, S_ITERS, S_HDR = 8 };
+enum : int { S_K = 0, S_STOP, S_UNUSED, S_OVERFLOW, S_EMITTED, S_NEW, S_ERR, S_ITERS, S_HDR = 8 };
 enum : u64 { STOP_NONE = 0, STOP_FIXPOINT = 1, STOP_MAXITER = 2, STOP_OVERFLOW = 3, STOP_RECORD = 4 };
 // relation slots: |F|, |recent|, unique candidates, then the merge's counts
 // (duplicates, new or improved, error word); view j >= 1 at 8 + 4 (j - 1):
 // rows, duplicates, new, error word
 enum : int { R_FULL = 0, R_RECENT, R_NU, R_DUPS, R_NR, R_MERR };
 
+constexpr int kGMaxGroups = kGMaxRels * (2 + kGMaxViews);
 struct GDesc {
   int nrel, narm;
   u32 max_iters, rec_cap;
@@ -49,7 +50,21 @@ struct GDesc {
   int rel_nviews[kGMaxRels];
   int arm_delta[kGMaxArms], arm_last[kGMaxArms], arm_nbefore[kGMaxArms];
   int arm_before[kGMaxArms][kGMaxBefore];
+  // double-buffered groups: per dense relation its primary view, its
+  // maintained views (in view-slot order) and its recent set
+  int ngroups, par_base;  // group g's parity is state slot par_base + g
+  int rel_group[kGMaxRels];  // first group of the relation (primary view); views follow, then the recent set
+  // capacities the iteration's buffers were planned with, and the state slots
+  // that record what an overflowing iteration needed
+  u64 cap_full[kGMaxRels], cap_u[kGMaxRels], cap_r[kGMaxRels], cap_view[kGMaxRels][kGMaxViews];
+  u64 cap_bind, cap_outputs;
+  int need_full[kGMaxRels], need_u[kGMaxRels], need_r[kGMaxRels], need_view[kGMaxRels][kGMaxViews];
+  int need_bind, need_tiles;
 };
+static_assert(sizeof(GDesc) <= 4096, "loop descriptor must fit the kernel parameter space");
+// pointer table entries: tab / res [(g * 2 + b) * 3 + field], field 0 keys,
+// 1 tags, 2 stamps; tab's b is the buffer, res's b is 0 = current, 1 = next
+LOB_HD int ptr_slot(int g, int b) { return (g * 2 + b) * 3; }
 
 LOB_HD int rel_base(int r) { return S_HDR + r * kRelSlots; }
 LOB_HD int view_base(int r, int j) { return rel_base(r) + 8 + 4 * (j - 1); }
@@ -58,8 +73,15 @@ LOB_HD int arm_base(int nrel, int a) { return S_HDR + nrel * kRelSlots + a * kAr
 // Which arms run in the coming iteration (a recent delta relation, and old
 // facts in every derived atom before the delta atom), and the iteration's
 // record of (|F|, |recent|) per relation for the backward pass.
-__global__ void k_iter_begin(const __grid_constant__ GDesc d, u64* s, u64* rec) {
+__global__ void k_iter_begin(const __grid_constant__ GDesc d, u64* s, u64* rec, void* const* tab, void** res) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int g = 0; g < d.ngroups; g++) {  // this iteration's current and next buffers of every group
+    const int p = (int)(s[d.par_base + g] & 1);
+    for (int f = 0; f < 3; f++) {
+      res[ptr_slot(g, 0) + f] = tab[ptr_slot(g, p) + f];
+      res[ptr_slot(g, 1) + f] = tab[ptr_slot(g, p ^ 1) + f];
+    }
+  }
   const u64 k = s[S_K] + 1;
   for (int a = 0; a < d.narm; a++) {
     const u64* D = s + rel_base(d.arm_delta[a]);
@@ -77,9 +99,33 @@ __global__ void k_iter_begin(const __grid_constant__ GDesc d, u64* s, u64* rec) 
     }
 }
 
-// Commit the iteration (or stop without committing after an overflow).
+LOB_DEV void need_at_most(u64* s, u64 v, u64 cap, int need) {
+  if (v > cap) {
+    s[S_OVERFLOW] = 1;
+    if (v > s[need]) s[need] = v;
+  }
+}
+
+// Commit the iteration, or stop without committing when a size outgrew its
+// buffer (every kernel clamped its writes to the capacities, so the committed
+// state in the current buffers is intact).
 __global__ void k_iter_end(const __grid_constant__ GDesc d, u64* s) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int a = 0; a < d.narm; a++)
+    for (int st = 1; st <= d.arm_last[a]; st++) {
+      const u64 t = s[arm_base(d.nrel, a) + 1 + st];
+      need_at_most(s, t, d.cap_outputs, d.need_tiles);
+      if (st < d.arm_last[a]) need_at_most(s, t, d.cap_bind, d.need_bind);
+    }
+  for (int r = 0; r < d.nrel; r++) {
+    if (!d.rel_dense[r]) continue;
+    const u64* R = s + rel_base(r);
+    need_at_most(s, R[R_NU], d.cap_u[r], d.need_u[r]);
+    need_at_most(s, R[R_FULL] + R[R_NU], d.cap_full[r], d.need_full[r]);
+    need_at_most(s, R[R_NR], d.cap_r[r], d.need_r[r]);
+    for (int j = 1; j <= d.rel_nviews[r]; j++)
+      need_at_most(s, s[view_base(r, j)] + R[R_NR], d.cap_view[r][j - 1], d.need_view[r][j - 1]);
+  }
   if (s[S_OVERFLOW]) {
     s[S_STOP] = STOP_OVERFLOW;
     return;
@@ -88,33 +134,30 @@ __global__ void k_iter_end(const __grid_constant__ GDesc d, u64* s) {
   for (int r = 0; r < d.nrel; r++) {
     if (!d.rel_dense[r]) continue;
     u64* R = s + rel_base(r);
+    const int g0 = d.rel_group[r], grec = g0 + 1 + d.rel_nviews[r];
+    if (R[R_NU] == 0) {  // no candidates: nothing was merged or written
+      R[R_RECENT] = 0;
+      continue;
+    }
     R[R_FULL] = R[R_FULL] + R[R_NU] - R[R_DUPS];
     R[R_RECENT] = R[R_NR];
     total_new += R[R_NR];
+    s[d.par_base + g0] ^= 1ull;    // F and the recent set were written to their next buffers
+    s[d.par_base + grec] ^= 1ull;
+    if (R[R_NR] == 0) continue;    // the secondary views merged nothing
     for (int j = 1; j <= d.rel_nviews[r]; j++) {
       u64* V = s + view_base(r, j);
       V[0] = V[0] + R[R_NR] - V[1];
+      s[d.par_base + g0 + j] ^= 1ull;
     }
   }
   for (int a = 0; a < d.narm; a++) s[S_EMITTED] += s[arm_base(d.nrel, a) + 1 + d.arm_last[a]];
   s[S_K] += 1;
-  s[S_PARITY] ^= 1ull;
   s[S_NEW] += total_new;
   s[S_ITERS] += 1;
   if (total_new == 0) s[S_STOP] = STOP_FIXPOINT;
   else if (s[S_K] >= d.max_iters) s[S_STOP] = STOP_MAXITER;
   else if (s[S_K] >= d.rec_cap) s[S_STOP] = STOP_RECORD;
-}
-
-// s[a] (+ s[b]) must fit `cap`; otherwise the iteration is marked overflowed
-// and s[need] keeps the largest size seen
-__global__ void k_guard(u64* s, int a, int b, u64 cap, int need) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const u64 v = s[a] + (b >= 0 ? s[b] : 0ull);
-  if (v > cap) {
-    s[S_OVERFLOW] = 1;
-    if (v > s[need]) s[need] = v;
-  }
 }
 
 // In-graph phase timing (engine option "profile"): each call adds the time
@@ -163,7 +206,7 @@ struct GLoop {
   std::vector<int> need_full, need_u, need_r;
   std::vector<std::vector<int>> need_view;
   int need_bind = 0, need_tiles = 0;
-  DevBuf state, rec;
+  DevBuf state, rec, tab, res;
   // in-graph phase timing (profiling only): phase names and their totals
   bool timing = false;
   std::vector<std::string> phases;
@@ -262,7 +305,37 @@ void plan_loop(lob_engine& e, GLoop& G, u32 max_iters) {
   }
   G.need_bind = n++;
   G.need_tiles = n++;
+  // buffer groups and their parity slots
+  int g = 0;
+  for (int r = 0; r < nrel; r++) {
+    G.d.rel_group[r] = g;
+    if (G.d.rel_dense[r]) g += 2 + (int)G.views[r].size();
+  }
+  G.d.ngroups = g;
+  G.d.par_base = n;
+  n += g;
   G.n_slots = n;
+}
+
+// the current (b = 0) and twin (b = 1) buffers of group g, as the host holds them
+void group_buffers(lob_engine& e, const GLoop& G, int g, int b, void** out3) {
+  for (int r = 0; r < G.d.nrel; r++) {
+    if (!G.d.rel_dense[r]) continue;
+    const int g0 = G.d.rel_group[r], nv = (int)G.views[r].size();
+    if (g < g0 || g > g0 + 1 + nv) continue;
+    RelSt& R = e.rels[r];
+    if (g == g0 + 1 + nv) {  // recent set
+      out3[0] = (b ? R.nkeys : R.rkeys).p;
+      out3[1] = (b ? R.ntags : R.rtags).p;
+      out3[2] = nullptr;
+      return;
+    }
+    ViewSt& W = R.views[g == g0 ? 0 : G.views[r][g - g0 - 1].view];
+    out3[0] = (b ? W.keys2 : W.keys).p;
+    out3[1] = (b ? W.tags2 : W.tags).p;
+    out3[2] = (b ? W.stamps2 : W.stamps).p;
+    return;
+  }
 }
 
 // Capacities: what the engine remembers from earlier runs of this program, or
@@ -365,26 +438,31 @@ void allocate(lob_engine& e, GLoop& G) {
   e.ensure(G.state, (size_t)G.n_slots * 8);
 }
 
-// One iteration on buffer set `half` (0: the host's current buffers -> their
-// twins; 1: the twins -> the current buffers), captured into the stream.
-void capture_iteration(lob_engine& e, GLoop& G, int half, u64* st_dev, u64* rec_dev, cudaStream_t st) {
+// One iteration, captured into the stream.  Buffers of derived relations are
+// reached through the pointer table the begin kernel resolves.
+void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaStream_t st) {
   const int sem = e.semiring, ks = sem_kernel(sem);
   const int sb = stored_bytes(sem), cb = cand_bytes(sem);
   const bool stamps = sem_stamps(sem);
-  auto cur = [half](DevBuf& a, DevBuf& b) -> DevBuf& { return half == 0 ? a : b; };
-  auto nxt = [half](DevBuf& a, DevBuf& b) -> DevBuf& { return half == 0 ? b : a; };
   auto slot = [st_dev](int i) { return st_dev + i; };
-  auto guard = [&](int a, int b, u64 cap, int need) {
-    k_guard<<<1, 32, 0, st>>>(st_dev, a, b, cap, need);
-    e.check(cudaGetLastError(), "guard");
+  void** res = G.res.as<void*>();
+  // groups: primary view of r, its maintained view slot j, its recent set
+  auto gview = [&](int r, int view) -> int {
+    if (view == 0) return G.d.rel_group[r];
+    for (auto& gv : G.views[r])
+      if (gv.view == view) return G.d.rel_group[r] + gv.slot;
+    return -1;
   };
+  auto grecent = [&](int r) { return G.d.rel_group[r] + 1 + (int)G.views[r].size(); };
+  auto cur = [&](int g) { return res + ptr_slot(g, 0); };
+  auto nxt = [&](int g) { return res + ptr_slot(g, 1); };
   auto mark = [&](const char* name) {  // closes the phase that just ran
     if (!G.timing) return;
     k_phase_mark<<<1, 32, 0, st>>>(G.times.as<u64>(), name ? phase_id(G, name) : -1);
     e.check(cudaGetLastError(), "phase mark");
   };
   mark(nullptr);
-  k_iter_begin<<<1, 32, 0, st>>>(G.d, st_dev, rec_dev);
+  k_iter_begin<<<1, 32, 0, st>>>(G.d, st_dev, rec_dev, G.tab.as<void*>(), res);
   e.check(cudaGetLastError(), "iteration begin");
   for (auto& gi : G.indexes) {
     RelSt& R = e.rels[gi.rel];
@@ -395,8 +473,8 @@ void capture_iteration(lob_engine& e, GLoop& G, int half, u64* st_dev, u64* rec_
     for (size_t j = 0; j < G.views[gi.rel].size(); j++)
       if (G.views[gi.rel][j].view == gi.view) capw = G.cap_view[gi.rel][j] + G.cap_r[gi.rel];
     // rebuilt only when the relation gained facts in the previous iteration
-    build_dense_index(W.lay, gi.prefix, cur(W.keys, W.keys2).p, capw, I.offs.as<u64>(), I.domain, st, slot(gi.size_slot),
-                      slot(rel_base(gi.rel) + R_RECENT));
+    build_dense_index(W.lay, gi.prefix, W.keys.p, capw, I.offs.as<u64>(), I.domain, st, slot(gi.size_slot),
+                      slot(rel_base(gi.rel) + R_RECENT), cur(gview(gi.rel, gi.view)));
     e.check(cudaGetLastError(), "index");
   }
   mark("loop_begin_index");
@@ -408,8 +486,9 @@ void capture_iteration(lob_engine& e, GLoop& G, int half, u64* st_dev, u64* rec_
     RelSt& D = e.rels[drel];
     RelSt& H = e.rels[R.head.rel];
     const int ab = arm_base(G.d.nrel, (int)a);
-    const void* in_words = cur(D.rkeys, D.nkeys).p;
-    const void* in_tags = cur(D.rtags, D.ntags).p;
+    const void* in_words = D.rkeys.p;
+    const void* in_tags = D.rtags.p;
+    void* const* in_pp = cur(grecent(drel));
     u64 n_cap = G.cap_r[drel];
     const u64* n_dev = slot(ab);
     int in_packed = 1, side = 0;
@@ -422,14 +501,16 @@ void capture_iteration(lob_engine& e, GLoop& G, int half, u64* st_dev, u64* rec_
       PStep P = A.packed.steps[s - 1];
       P.in_words = in_words;
       P.in_tags = in_tags;
+      P.in_pp = in_pp;
       P.n_in = n_cap;
       P.n_in_dev = n_dev;
       (void)in_packed;
       const bool derived = VR.idb;
-      P.v_keys = derived ? cur(W.keys, W.keys2).p : W.keys.p;
+      P.v_keys = W.keys.p;
       P.v_key64 = W.lay.key64;
-      P.v_tags = derived ? cur(W.tags, W.tags2).p : W.tags.p;
-      P.v_stamp = (derived ? cur(W.stamps, W.stamps2) : W.stamps).as<u32>();
+      P.v_tags = W.tags.p;
+      P.v_stamp = W.stamps.as<u32>();
+      P.v_pp = derived ? cur(gview(vrel, S.view)) : nullptr;
       P.v_n = W.n;
       P.v_n_dev = nullptr;
       if (derived) {
@@ -464,7 +545,6 @@ void capture_iteration(lob_engine& e, GLoop& G, int half, u64* st_dev, u64* rec_
       e.check(cudaGetLastError(), "join scan");
       const std::string tag = "loop_arm" + std::to_string(a) + "_step" + std::to_string(s);
       mark((tag + "_count").c_str());
-      guard(tslot, -1, G.cap_tiles * (u64)kEmitTile, G.need_tiles);
       P.total_dev = slot(tslot);
       P.j_begin = 0;
       if (last) {
@@ -476,7 +556,6 @@ void capture_iteration(lob_engine& e, GLoop& G, int half, u64* st_dev, u64* rec_
         P.acc = H.dacc.p;
         P.total = G.cap_tiles * (u64)kEmitTile;
       } else {
-        guard(tslot, -1, G.cap_bind, G.need_bind);
         const int out_side = side ^ 1;
         P.out_words = e.bind[out_side][0].p;
         P.out_tags = e.bind[out_side][kMaxSlots + 1].p;
@@ -493,6 +572,7 @@ void capture_iteration(lob_engine& e, GLoop& G, int half, u64* st_dev, u64* rec_
       mark((tag + "_emit").c_str());
       in_words = e.bind[side][0].p;
       in_tags = e.bind[side][kMaxSlots + 1].p;
+      in_pp = nullptr;
       n_cap = G.cap_bind;
       n_dev = slot(tslot);
       in_packed = 0;
@@ -509,8 +589,6 @@ void capture_iteration(lob_engine& e, GLoop& G, int half, u64* st_dev, u64* rec_
     const u64 nbits = 1ull << L.bits;
     bits_count(H.dtouched.as<u32>(), nullptr, nbits, e.scratch.p, slot(rb + R_NU), st);
     e.check(cudaGetLastError(), "dense count");
-    guard(rb + R_NU, -1, G.cap_u[r], G.need_u[r]);
-    guard(rb + R_FULL, rb + R_NU, G.cap_full[r], G.need_full[r]);
     dense_extract(ks, L.key64, H.dtouched.as<u32>(), H.dacc.p, nbits, H.akeys.p, H.atags.p, G.cap_u[r], e.scratch.p, st,
                   G.cap_u[r]);
     e.check(cudaGetLastError(), "dense extract");
@@ -519,9 +597,13 @@ void capture_iteration(lob_engine& e, GLoop& G, int half, u64* st_dev, u64* rec_
     MergeArgs M{};
     M.sem = ks;
     M.key64 = L.key64;
-    M.fkeys = cur(V.keys, V.keys2).p;
-    M.ftags = cur(V.tags, V.tags2).p;
-    M.fstamp = stamps ? cur(V.stamps, V.stamps2).as<u32>() : nullptr;
+    M.fkeys = V.keys.p;
+    M.ftags = V.tags.p;
+    M.fstamp = stamps ? V.stamps.as<u32>() : nullptr;
+    M.f_pp = cur(gview(r, 0));
+    M.o_pp = nxt(gview(r, 0));
+    M.r_pp = nxt(grecent(r));
+    M.skip_empty = 1;
     M.nf = G.cap_full[r];
     M.nf_dev = slot(rb + R_FULL);
     M.ukeys = H.akeys.p;
@@ -529,26 +611,24 @@ void capture_iteration(lob_engine& e, GLoop& G, int half, u64* st_dev, u64* rec_
     M.nu = G.cap_u[r];
     M.nu_dev = slot(rb + R_NU);
     M.u_stored = 0;
-    M.okeys = nxt(V.keys, V.keys2).p;
-    M.otags = nxt(V.tags, V.tags2).p;
-    M.ostamp = stamps ? nxt(V.stamps, V.stamps2).as<u32>() : nullptr;
-    M.rkeys = nxt(H.rkeys, H.nkeys).p;
-    M.rtags = nxt(H.rtags, H.ntags).p;
+    M.okeys = V.keys2.p;
+    M.otags = V.tags2.p;
+    M.ostamp = stamps ? V.stamps2.as<u32>() : nullptr;
+    M.rkeys = H.nkeys.p;
+    M.rtags = H.ntags.p;
     M.stamp = 1;
     M.stamp_dev = slot(S_K);
     M.counts_dev = slot(rb + R_DUPS);
     M.rcap = G.cap_r[r];
     diff_merge(M, e.scratch.p, st);
     e.check(cudaGetLastError(), "difference+merge");
-    guard(rb + R_NR, -1, G.cap_r[r], G.need_r[r]);
     mark((rtag + "_merge").c_str());
     for (size_t j = 0; j < G.views[r].size(); j++) {
       ViewSt& W = H.views[G.views[r][j].view];
       const int vb = view_base(r, G.views[r][j].slot);
       const u64 nu = G.cap_r[r];
-      guard(vb, rb + R_NR, G.cap_view[r][j], G.need_view[r][j]);
-      repack_keys(L, V.perm, W.lay, W.perm, nxt(H.rkeys, H.nkeys).p, e.tmp_keys.p, nu, st, slot(rb + R_NR));
-      if (sb) copy_elems(e.tmp_tags.p, nxt(H.rtags, H.ntags).p, nu, sb, slot(rb + R_NR), st);
+      repack_keys(L, V.perm, W.lay, W.perm, H.nkeys.p, e.tmp_keys.p, nu, st, slot(rb + R_NR), nxt(grecent(r)));
+      if (sb) copy_elems(e.tmp_tags.p, H.ntags.p, nu, sb, slot(rb + R_NR), st, nxt(grecent(r)) + 1);
       void* k = e.tmp_keys.p;
       void* t = e.tmp_tags.p;
       sort_pairs(W.lay.key64, sb, &k, &t, e.tmp_keys2.p, e.tmp_tags2.p, nu, W.lay.bits, e.opt_radix_bits, e.scratch.p,
@@ -558,9 +638,12 @@ void capture_iteration(lob_engine& e, GLoop& G, int half, u64* st_dev, u64* rec_
       MergeArgs M2{};
       M2.sem = ks;
       M2.key64 = W.lay.key64;
-      M2.fkeys = cur(W.keys, W.keys2).p;
-      M2.ftags = cur(W.tags, W.tags2).p;
-      M2.fstamp = stamps ? cur(W.stamps, W.stamps2).as<u32>() : nullptr;
+      M2.fkeys = W.keys.p;
+      M2.ftags = W.tags.p;
+      M2.fstamp = stamps ? W.stamps.as<u32>() : nullptr;
+      M2.f_pp = cur(gview(r, G.views[r][j].view));
+      M2.o_pp = nxt(gview(r, G.views[r][j].view));
+      M2.skip_empty = 1;
       M2.nf = G.cap_view[r][j];
       M2.nf_dev = slot(vb);
       M2.ukeys = k;
@@ -568,9 +651,9 @@ void capture_iteration(lob_engine& e, GLoop& G, int half, u64* st_dev, u64* rec_
       M2.nu = nu;
       M2.nu_dev = slot(rb + R_NR);
       M2.u_stored = 1;
-      M2.okeys = nxt(W.keys, W.keys2).p;
-      M2.otags = nxt(W.tags, W.tags2).p;
-      M2.ostamp = stamps ? nxt(W.stamps, W.stamps2).as<u32>() : nullptr;
+      M2.okeys = W.keys2.p;
+      M2.otags = W.tags2.p;
+      M2.ostamp = stamps ? W.stamps2.as<u32>() : nullptr;
       M2.stamp = 1;
       M2.stamp_dev = slot(S_K);
       M2.counts_dev = slot(vb + 1);
@@ -648,6 +731,22 @@ int run_device_loop(lob_engine& e, u32& k, u32 max_iters, lob_stats& s, bool* ta
     if (round > 64) throw LobError(LOB_E_CUDA, "internal error: device loop capacities did not settle");
     G.d.rec_cap = rec_cap;
     allocate(e, G);
+    for (int r = 0; r < G.d.nrel; r++) {
+      G.d.cap_full[r] = G.cap_full[r];
+      G.d.cap_u[r] = G.cap_u[r];
+      G.d.cap_r[r] = G.cap_r[r];
+      G.d.need_full[r] = G.need_full[r];
+      G.d.need_u[r] = G.need_u[r];
+      G.d.need_r[r] = G.need_r[r];
+      for (size_t j = 0; j < G.views[r].size(); j++) {
+        G.d.cap_view[r][j] = G.cap_view[r][j];
+        G.d.need_view[r][j] = G.need_view[r][j];
+      }
+    }
+    G.d.cap_bind = G.cap_bind;
+    G.d.cap_outputs = G.cap_tiles * (u64)kEmitTile;
+    G.d.need_bind = G.need_bind;
+    G.d.need_tiles = G.need_tiles;
     e.ensure(G.rec, (size_t)rec_cap * G.d.nrel * 16);
     // state block: sizes as the host holds them after iteration k
     std::vector<u64> h(G.n_slots, 0);
@@ -658,16 +757,26 @@ int run_device_loop(lob_engine& e, u32& k, u32 max_iters, lob_stats& s, bool* ta
       h[rel_base(r) + R_RECENT] = R.n_recent;
       for (auto& gv : G.views[r]) h[view_base(r, gv.slot)] = R.views[gv.view].n;
     }
+    for (int g = 0; g < G.d.ngroups; g++) h[G.d.par_base + g] = 0;
     e.check(cudaMemcpyAsync(G.state.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, e.stream), "loop state");
+    // pointer table: both buffers of every group
+    std::vector<void*> tab((size_t)ptr_slot(G.d.ngroups, 0), nullptr);
+    for (int g = 0; g < G.d.ngroups; g++)
+      for (int b = 0; b < 2; b++) group_buffers(e, G, g, b, &tab[ptr_slot(g, b)]);
+    e.ensure(G.tab, std::max<size_t>(tab.size(), 1) * sizeof(void*));
+    e.ensure(G.res, std::max<size_t>(tab.size(), 1) * sizeof(void*));
+    if (!tab.empty())
+      e.check(cudaMemcpyAsync(G.tab.p, tab.data(), tab.size() * sizeof(void*), cudaMemcpyHostToDevice, e.stream),
+              "pointer table");
     u64* st_dev = G.state.as<u64>();
     u64* rec_dev = G.rec.as<u64>();
-    // WHILE { iteration 0 -> 1; IF { iteration 1 -> 0 } }
-    // The WHILE handle starts at 0 and a kernel ahead of the node sets it from
-    // the state block, as the body's last kernel does after every pass: if a
-    // value were never set, the loop would not start, rather than not end.
+    // WHILE { one iteration }.  The WHILE handle starts at 0 and a kernel ahead
+    // of the node sets it from the state block, as the body's last kernel does
+    // after every pass: if a value were never set, the loop would not start,
+    // rather than not end.
     GraphHolder gh;
     e.check(cudaGraphCreate(&gh.g, 0), "graph");
-    cudaGraphConditionalHandle hw, hi;
+    cudaGraphConditionalHandle hw;
     e.check(cudaGraphConditionalHandleCreate(&hw, gh.g, 0, cudaGraphCondAssignDefault), "while handle");
     cudaGraphNodeParams wp = {};
     wp.type = cudaGraphNodeTypeConditional;
@@ -697,29 +806,9 @@ int run_device_loop(lob_engine& e, u32& k, u32 max_iters, lob_stats& s, bool* ta
       e.check(cudaStreamEndCapture(cap, &top), "end capture");
     }
     cudaGraph_t body = wp.conditional.phGraph_out[0];
-    e.check(cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault), "if handle");
-    e.check(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
-            "capture");
-    cudaGraph_t ibody = nullptr;
+    e.check(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "capture");
     try {
-      capture_iteration(e, G, 0, st_dev, rec_dev, cap);
-      k_set_cond<<<1, 32, 0, cap>>>(st_dev, hi);
-      e.check(cudaGetLastError(), "condition");
-      cudaStreamCaptureStatus cstat;
-      const cudaGraphNode_t* deps = nullptr;
-      const cudaGraphEdgeData* edata = nullptr;
-      size_t ndeps = 0;
-      e.check(cudaStreamGetCaptureInfo(cap, &cstat, nullptr, nullptr, &deps, &edata, &ndeps), "capture info");
-      cudaGraphNodeParams ip = {};
-      ip.type = cudaGraphNodeTypeConditional;
-      ip.conditional.handle = hi;
-      ip.conditional.type = cudaGraphCondTypeIf;
-      ip.conditional.size = 1;
-      cudaGraphNode_t inode;
-      e.check(cudaGraphAddNode(&inode, body, deps, edata, ndeps, &ip), "if node");
-      ibody = ip.conditional.phGraph_out[0];
-      e.check(cudaStreamUpdateCaptureDependencies(cap, &inode, nullptr, 1, cudaStreamSetCaptureDependencies),
-              "capture dependencies");
+      capture_iteration(e, G, st_dev, rec_dev, cap);
       k_set_cond<<<1, 32, 0, cap>>>(st_dev, hw);
       e.check(cudaGetLastError(), "condition");
     } catch (...) {
@@ -730,17 +819,7 @@ int run_device_loop(lob_engine& e, u32& k, u32 max_iters, lob_stats& s, bool* ta
     }
     cudaGraph_t captured = nullptr;
     e.check(cudaStreamEndCapture(cap, &captured), "end capture");
-    e.check(cudaStreamBeginCaptureToGraph(cap, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "capture");
-    try {
-      capture_iteration(e, G, 1, st_dev, rec_dev, cap);
-    } catch (...) {
-      cudaGraph_t dummy;
-      cudaStreamEndCapture(cap, &dummy);
-      cudaGetLastError();
-      throw;
-    }
-    e.check(cudaStreamEndCapture(cap, &captured), "end capture");
-    const u64 per_iter = count_kernels(ibody);
+    const u64 per_iter = count_kernels(body);
     e.check(cudaGraphInstantiate(&gh.x, gh.g, 0), "instantiate");
     e.check(cudaGraphLaunch(gh.x, e.stream), "graph launch");
     std::vector<u64> out(G.n_slots);
@@ -748,7 +827,7 @@ int run_device_loop(lob_engine& e, u32& k, u32 max_iters, lob_stats& s, bool* ta
     e.sync();
     s.graph_launches++;
     const u64 ran = out[S_ITERS];
-    e.launches += ran * per_iter + 2 * ((ran + 1) / 2);
+    e.launches += ran * per_iter;
     if (out[S_ERR] & kErrLocOverflow)
       throw LobError(LOB_E_ARG, "join step: 1024 consecutive input rows have 2^32 or more matches");
     // the iterations' records for the backward pass
@@ -764,18 +843,20 @@ int run_device_loop(lob_engine& e, u32& k, u32 max_iters, lob_stats& s, bool* ta
           e.iter_counts.back().emplace_back(rec[2 * (it * G.d.nrel + r)], rec[2 * (it * G.d.nrel + r) + 1]);
       }
     }
-    // the committed state is in buffer set `parity`
-    if (out[S_PARITY] & 1) {
-      for (int r = 0; r < G.d.nrel; r++) {
-        if (!G.d.rel_dense[r]) continue;
-        RelSt& R = e.rels[r];
-        auto flip = [](ViewSt& W) {
-          std::swap(W.keys, W.keys2);
-          std::swap(W.tags, W.tags2);
-          std::swap(W.stamps, W.stamps2);
-        };
-        flip(R.views[0]);
-        for (auto& gv : G.views[r]) flip(R.views[gv.view]);
+    // each group's committed state is in the buffer its parity names
+    for (int r = 0; r < G.d.nrel; r++) {
+      if (!G.d.rel_dense[r]) continue;
+      RelSt& R = e.rels[r];
+      const int g0 = G.d.rel_group[r], nv = (int)G.views[r].size();
+      auto flip = [](ViewSt& W) {
+        std::swap(W.keys, W.keys2);
+        std::swap(W.tags, W.tags2);
+        std::swap(W.stamps, W.stamps2);
+      };
+      if (out[G.d.par_base + g0] & 1) flip(R.views[0]);
+      for (int j = 0; j < nv; j++)
+        if (out[G.d.par_base + g0 + 1 + j] & 1) flip(R.views[G.views[r][j].view]);
+      if (out[G.d.par_base + g0 + 1 + nv] & 1) {
         std::swap(R.rkeys, R.nkeys);
         std::swap(R.rtags, R.ntags);
       }
@@ -838,5 +919,7 @@ int run_device_loop(lob_engine& e, u32& k, u32 max_iters, lob_stats& s, bool* ta
   }
   e.release(G.state);
   e.release(G.rec);
+  e.release(G.tab);
+  e.release(G.res);
   return rc;
 }

@@ -191,9 +191,11 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ StepPar
 }
 
 __global__ void k_dense_index(const void* __restrict__ keys, int key64, u64 n, int rs, u64* __restrict__ offs, u64 domain,
-                              const u64* __restrict__ n_dev, const u64* __restrict__ changed_dev) {
+                              const u64* __restrict__ n_dev, const u64* __restrict__ changed_dev,
+                              void* const* __restrict__ keys_pp) {
   if (changed_dev && *changed_dev == 0) return;  // the view did not change: its index still holds
   if (n_dev) n = *n_dev < n ? *n_dev : n;
+  if (keys_pp) keys = keys_pp[0];
   const u64 stride = (u64)gridDim.x * blockDim.x;
   for (u64 p = (u64)blockIdx.x * blockDim.x + threadIdx.x; p <= domain; p += stride)
     offs[p] = p == domain ? n : lower_bound_any(keys, key64, n, p << rs);
@@ -204,8 +206,9 @@ struct Perm {
 };
 
 __global__ void k_repack(Layout from, Perm pf, Layout to, Perm pt, const void* __restrict__ in, void* __restrict__ out, u64 n,
-                         const u64* __restrict__ n_dev) {
+                         const u64* __restrict__ n_dev, void* const* __restrict__ in_pp) {
   if (n_dev) n = *n_dev < n ? *n_dev : n;
+  if (in_pp) in = in_pp[0];
   const u64 stride = (u64)gridDim.x * blockDim.x;
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const u64 k = load_key(in, from.key64, i);
@@ -332,28 +335,29 @@ void project_rows(int sem, const StepParams& P, cudaStream_t st) {
 }
 
 void build_dense_index(const Layout& L, int prefix_len, const void* keys, u64 n, u64* offs, u64 domain, cudaStream_t st,
-                       const u64* n_dev, const u64* changed_dev) {
+                       const u64* n_dev, const u64* changed_dev, void* const* keys_pp) {
   ProfScope ps("index_build", (domain + 1) * 8.0 + n * (L.key64 ? 8.0 : 4.0), st);
   k_dense_index<<<grid_for(domain + 1), 256, 0, st>>>(keys, L.key64, n, rest_shift(L, prefix_len), offs, domain, n_dev,
-                                                     changed_dev);
+                                                     changed_dev, keys_pp);
 }
 
 __global__ void k_copy_words(const u32* __restrict__ in, u32* __restrict__ out, u64 n_words, const u64* __restrict__ n_dev,
-                             u32 words_per_elem) {
+                             u32 words_per_elem, void* const* __restrict__ in_pp) {
   if (n_dev) n_words = (*n_dev * words_per_elem < n_words) ? *n_dev * words_per_elem : n_words;
+  if (in_pp) in = reinterpret_cast<const u32*>(in_pp[0]);
   const u64 stride = (u64)gridDim.x * blockDim.x;
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n_words; i += stride) out[i] = in[i];
 }
 
-void copy_elems(void* dst, const void* src, u64 n, int elem_bytes, const u64* n_dev, cudaStream_t st) {
+void copy_elems(void* dst, const void* src, u64 n, int elem_bytes, const u64* n_dev, cudaStream_t st, void* const* src_pp) {
   const u64 w = n * (u64)(elem_bytes / 4);
   if (!w) return;
   k_copy_words<<<grid_for(w), 256, 0, st>>>(reinterpret_cast<const u32*>(src), reinterpret_cast<u32*>(dst), w, n_dev,
-                                            (u32)(elem_bytes / 4));
+                                            (u32)(elem_bytes / 4), src_pp);
 }
 
 void repack_keys(const Layout& from, const int* perm_from, const Layout& to, const int* perm_to, const void* in, void* out,
-                 u64 n, cudaStream_t st, const u64* n_dev) {
+                 u64 n, cudaStream_t st, const u64* n_dev, void* const* in_pp) {
   if (!n) return;
   ProfScope ps("view_repack", n * ((from.key64 ? 8.0 : 4.0) + (to.key64 ? 8.0 : 4.0)), st);
   Perm a, b;
@@ -361,7 +365,7 @@ void repack_keys(const Layout& from, const int* perm_from, const Layout& to, con
     a.p[j] = j < from.arity ? perm_from[j] : 0;
     b.p[j] = j < to.arity ? perm_to[j] : 0;
   }
-  k_repack<<<grid_for(n), 256, 0, st>>>(from, a, to, b, in, out, n, n_dev);
+  k_repack<<<grid_for(n), 256, 0, st>>>(from, a, to, b, in, out, n, n_dev, in_pp);
 }
 
 void pack_rows(const Layout& L, const u32* cols, u64 stride, const u32* samples, u64 n, void* keys, u32* rows,

@@ -68,6 +68,10 @@ struct MergeArgs {
   const u64* nf_dev; const u64* nu_dev;
   const u64* stamp_dev;  // when set, new / improved facts get the stamp *stamp_dev + stamp
   u64 rcap;              // when non-zero, R entries past it are not written (the caller checks |R| against it)
+  // device-resident buffer pointers: when set, f_pp[0..2] replace fkeys / ftags /
+  // fstamp, o_pp[0..2] okeys / otags / ostamp and r_pp[0..1] rkeys / rtags
+  void* const* f_pp; void* const* o_pp; void* const* r_pp;
+  int skip_empty;        // with U empty, F and U are not read and nothing is written but counts_dev (all 0)
 };
 size_t merge_scratch_bytes(u64 nf, u64 nu);
 void diff_merge(const MergeArgs& a, void* scratch, cudaStream_t st);
@@ -178,14 +182,17 @@ void merge_nodup(int key64, const void* a, u64 na, const void* b, u64 nb, void* 
 
 // n_dev (optional): the key count in device memory, n its capacity;
 // changed_dev (optional): when it holds 0 the view is unchanged and the index is kept
+// keys_pp (optional): device slot holding the keys pointer (replaces keys)
 void build_dense_index(const Layout& L, int prefix_len, const void* keys, u64 n, u64* offs, u64 domain, cudaStream_t st,
-                       const u64* n_dev = nullptr, const u64* changed_dev = nullptr);
-// copy n elements of elem_bytes (a multiple of 4); n_dev as above
-void copy_elems(void* dst, const void* src, u64 n, int elem_bytes, const u64* n_dev, cudaStream_t st);
+                       const u64* n_dev = nullptr, const u64* changed_dev = nullptr, void* const* keys_pp = nullptr);
+// copy n elements of elem_bytes (a multiple of 4); n_dev as above; src_pp
+// (optional): device slot holding the source pointer
+void copy_elems(void* dst, const void* src, u64 n, int elem_bytes, const u64* n_dev, cudaStream_t st,
+                void* const* src_pp = nullptr);
 // re-encode keys of layout `from` into layout `to`; view column j of `to` is
 // relation column perm_to[j], view column j of `from` is relation column perm_from[j]
 void repack_keys(const Layout& from, const int* perm_from, const Layout& to, const int* perm_to, const void* in, void* out,
-                 u64 n, cudaStream_t st, const u64* n_dev = nullptr);
+                 u64 n, cudaStream_t st, const u64* n_dev = nullptr, void* const* in_pp = nullptr);
 void pack_rows(const Layout& L, const u32* cols, u64 stride, const u32* samples, u64 n, void* keys, u32* rows,
                cudaStream_t st);
 void read_rows(int sem, const Layout& L, const int* perm, const void* keys, const void* tags, u64 n, u32* cols,

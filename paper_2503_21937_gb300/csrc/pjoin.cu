@@ -40,17 +40,17 @@ LOB_DEV u64 compose(const PField* f, int n, u64 wi, u64 wv) {
 
 // input row r: its word, or false when the row is dropped / filtered
 template <class Sem>
-LOB_DEV bool input_row(const PStep& P, u64 r, u64& wi, typename Sem::Cand& tag) {
+LOB_DEV bool input_row(const PStep& P, const PPtrs& Q, u64 r, u64& wi, typename Sem::Cand& tag) {
   if (P.in_stamp_mode != STAMP_NONE) {
     u32 s = P.in_stamp[r] & 0x7FFFFFFFu;
     if (P.in_stamp_mode == STAMP_LT ? !(s < P.in_stamp_val) : s != P.in_stamp_val) return false;
   }
-  wi = load_word(P.in_words, P.in_w64, r);
+  wi = load_word(Q.in_words, P.in_w64, r);
   if (wi == (P.in_w64 ? ~0ull : 0xFFFFFFFFull)) return false;
   if (!checks_ok(P.in_checks, P.n_in_checks, wi, 0)) return false;
   if constexpr (Sem::kTags) {
-    if (P.in_packed) tag = Sem::from_stored(reinterpret_cast<const typename Sem::Stored*>(P.in_tags)[r]);
-    else tag = reinterpret_cast<const typename Sem::Cand*>(P.in_tags)[r];
+    if (P.in_packed) tag = Sem::from_stored(reinterpret_cast<const typename Sem::Stored*>(Q.in_tags)[r]);
+    else tag = reinterpret_cast<const typename Sem::Cand*>(Q.in_tags)[r];
   } else {
     tag = Sem::one();
   }
@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
   // tiles of kEmitTile outputs; a block takes tiles blockIdx.x, + gridDim.x, ...
   // (one tile per block when the grid has one block per tile)
   const u64 j_end = P.j_begin + dev_size(P.total, P.total_dev);
+  const PPtrs Q = resolve_ptrs(P);
   for (u64 tile = blockIdx.x;; tile += gridDim.x) {
   const u64 j0 = P.j_begin + tile * kEmitTile;
   if (j0 >= j_end) break;
@@ -124,15 +125,15 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
     const u64 v = (u64)P.lo32[r] + (j - row_off(P, r));
     u64 wi;
     C tag;
-    input_row<Sem>(P, r, wi, tag);
-    const u64 wv = load_word(P.v_keys, P.v_key64, v);
+    input_row<Sem>(P, Q, r, wi, tag);
+    const u64 wv = load_word(Q.v_keys, P.v_key64, v);
     bool ok = P.v_stamp_mode == STAMP_NONE ||
-              (P.v_stamp_mode == STAMP_LT ? (P.v_stamp[v] & 0x7FFFFFFFu) < vsv : (P.v_stamp[v] & 0x7FFFFFFFu) == vsv);
+              (P.v_stamp_mode == STAMP_LT ? (Q.v_stamp[v] & 0x7FFFFFFFu) < vsv : (Q.v_stamp[v] & 0x7FFFFFFFu) == vsv);
     ok = ok && checks_ok(P.checks, P.n_checks, wi, wv);
     const u64 w = ok ? compose(P.out, P.n_out, wi, wv) : invalid_out;
     if constexpr (kFilter == 3) {
       if (!ok) continue;
-      dense_add<Sem>(P.acc, w, Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v])));
+      dense_add<Sem>(P.acc, w, Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(Q.v_tags)[v])));
       touch_bit(P.bitmap, w);
     } else if constexpr (kFilter) {
       if (!ok) continue;
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(256) k_pemit(const __grid_constant__ PStep P, 
       const u64 o = P.out_base + (j - P.j_begin);
       if (P.out_w64) reinterpret_cast<u64*>(P.out_words)[o] = w;
       else reinterpret_cast<u32*>(P.out_words)[o] = (u32)w;
-      if constexpr (Sem::kTags) reinterpret_cast<C*>(P.out_tags)[o] = Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v]));
+      if constexpr (Sem::kTags) reinterpret_cast<C*>(P.out_tags)[o] = Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(Q.v_tags)[v]));
     }
   }
   if constexpr (kFilter == 1) {
@@ -187,10 +188,11 @@ __global__ void __launch_bounds__(256) k_pproject(const __grid_constant__ PStep 
   typedef typename Sem::Cand C;
   const u64 stride = (u64)gridDim.x * blockDim.x;
   const u64 invalid_out = P.out_w64 ? ~0ull : 0xFFFFFFFFull;
+  const PPtrs Q = resolve_ptrs(P);
   for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < P.n_in; r += stride) {
     u64 wi;
     C tag = Sem::one();
-    const bool ok = input_row<Sem>(P, r, wi, tag);
+    const bool ok = input_row<Sem>(P, Q, r, wi, tag);
     const u64 w = ok ? compose(P.out, P.n_out, wi, 0) : invalid_out;
     const u64 o = P.out_base + r;
     if (P.out_w64) reinterpret_cast<u64*>(P.out_words)[o] = w;
@@ -238,6 +240,7 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
   // tiles of kEmitTile outputs; a block takes tiles blockIdx.x, + gridDim.x, ...
   // (one tile per block when the grid has one block per tile)
   const u64 j_end = P.j_begin + dev_size(P.total, P.total_dev);
+  const PPtrs Q = resolve_ptrs(P);
   for (u64 tile = blockIdx.x;; tile += gridDim.x) {
   const u64 j0 = P.j_begin + tile * kEmitTile;
   if (j0 >= j_end) break;
@@ -303,12 +306,12 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
       const u64 r = r0 + rr[b];
       offv[b] = row_off(P, r);
       lov[b] = P.lo32[r];
-      wi[b] = load_word(P.in_words, P.in_w64, r);
+      wi[b] = load_word(Q.in_words, P.in_w64, r);
     }
 #pragma unroll
     for (int b = 0; b < B; b++) {
       const u64 j = j0 + (u64)(i0 + b) * 256 + threadIdx.x;
-      wv[b] = j < j_end ? load_word(P.v_keys, P.v_key64, (u64)lov[b] + (j - offv[b])) : 0ull;
+      wv[b] = j < j_end ? load_word(Q.v_keys, P.v_key64, (u64)lov[b] + (j - offv[b])) : 0ull;
     }
 #pragma unroll
     for (int b = 0; b < B; b++) {
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
       if (P.n_in_checks) ok = ok && checks_ok(P.in_checks, P.n_in_checks, wi[b], 0);
       const u64 v = (u64)lov[b] + (j - offv[b]);
       if (P.v_stamp_mode != STAMP_NONE) {
-        const u32 st = P.v_stamp[v] & 0x7FFFFFFFu;
+        const u32 st = Q.v_stamp[v] & 0x7FFFFFFFu;
         ok = ok && (P.v_stamp_mode == STAMP_LT ? st < vsv : st == vsv);
       }
 #pragma unroll
@@ -329,9 +332,9 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
       if constexpr (kFilter == 3) {
         if (!ok) continue;
         const u64 r = r0 + rr[b];
-        const C tag = P.in_packed ? Sem::from_stored(reinterpret_cast<const S*>(P.in_tags)[r])
-                                  : reinterpret_cast<const C*>(P.in_tags)[r];
-        dense_add<Sem>(P.acc, w, Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v])));
+        const C tag = P.in_packed ? Sem::from_stored(reinterpret_cast<const S*>(Q.in_tags)[r])
+                                  : reinterpret_cast<const C*>(Q.in_tags)[r];
+        dense_add<Sem>(P.acc, w, Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(Q.v_tags)[v])));
         touch_bit(P.bitmap, w);
       } else if constexpr (kFilter) {
         if (!ok) continue;
@@ -351,9 +354,9 @@ __global__ void __launch_bounds__(256) k_pemit_fast(const __grid_constant__ PSte
         else reinterpret_cast<u32*>(P.out_words)[o] = (u32)w;
         if constexpr (Sem::kTags) {
           const u64 r = r0 + rr[b];
-          C tag = P.in_packed ? Sem::from_stored(reinterpret_cast<const S*>(P.in_tags)[r])
-                              : reinterpret_cast<const C*>(P.in_tags)[r];
-          reinterpret_cast<C*>(P.out_tags)[o] = Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v]));
+          C tag = P.in_packed ? Sem::from_stored(reinterpret_cast<const S*>(Q.in_tags)[r])
+                              : reinterpret_cast<const C*>(Q.in_tags)[r];
+          reinterpret_cast<C*>(P.out_tags)[o] = Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(Q.v_tags)[v]));
         }
       }
     }
@@ -405,7 +408,8 @@ __global__ void __launch_bounds__(256) k_pcount_loc(const __grid_constant__ PSte
     plim[q] = P.prefix[q].limit_bits;
   }
   const u64 invalid_in = P.in_w64 ? ~0ull : 0xFFFFFFFFull;
-  const bool vec_in = (reinterpret_cast<uintptr_t>(P.in_words) & 15) == 0;
+  const PPtrs Q = resolve_ptrs(P);
+  const bool vec_in = (reinterpret_cast<uintptr_t>(Q.in_words) & 15) == 0;
   const u64 n_in = dev_size(P.n_in, P.n_in_dev);  // blocks past it get count 0
   for (u64 b = blockIdx.x; b < n_blk; b += gridDim.x) {
     if (b * kLocRows >= n_in) {
@@ -417,16 +421,16 @@ __global__ void __launch_bounds__(256) k_pcount_loc(const __grid_constant__ PSte
     u64 w[4];
     if (full && vec_in) {
       if (P.in_w64) {
-        const ulonglong2 x = reinterpret_cast<const ulonglong2*>(P.in_words)[r0 / 2];
-        const ulonglong2 y = reinterpret_cast<const ulonglong2*>(P.in_words)[r0 / 2 + 1];
+        const ulonglong2 x = reinterpret_cast<const ulonglong2*>(Q.in_words)[r0 / 2];
+        const ulonglong2 y = reinterpret_cast<const ulonglong2*>(Q.in_words)[r0 / 2 + 1];
         w[0] = x.x; w[1] = x.y; w[2] = y.x; w[3] = y.y;
       } else {
-        const uint4 x = reinterpret_cast<const uint4*>(P.in_words)[r0 / 4];
+        const uint4 x = reinterpret_cast<const uint4*>(Q.in_words)[r0 / 4];
         w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < 4; i++) w[i] = r0 + i < n_in ? load_word(P.in_words, P.in_w64, r0 + i) : invalid_in;
+      for (int i = 0; i < 4; i++) w[i] = r0 + i < n_in ? load_word(Q.in_words, P.in_w64, r0 + i) : invalid_in;
     }
     u32 c[4], lo[4];
 #pragma unroll
@@ -471,8 +475,8 @@ __global__ void __launch_bounds__(256) k_pcount_loc(const __grid_constant__ PSte
             } else {
               const u64 klo = pv << P.rest_shift;
               const u64 khi = klo + (1ull << P.rest_shift);
-              l = lower_bound_w(P.v_keys, P.v_key64, vn, klo);
-              h = khi < klo ? vn : lower_bound_w(P.v_keys, P.v_key64, vn, khi);
+              l = lower_bound_w(Q.v_keys, P.v_key64, vn, klo);
+              h = khi < klo ? vn : lower_bound_w(Q.v_keys, P.v_key64, vn, khi);
             }
           }
           c[i] = (u32)(h - l);

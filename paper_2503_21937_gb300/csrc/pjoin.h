@@ -54,7 +54,21 @@ struct PStep {
   const u64* n_in_dev; const u64* total_dev;
   const u64* v_n_dev;     // the probed view's row count (v_n its capacity)
   const u64* stamp_dev;   // when set, the stamp filters compare with *stamp_dev + v_stamp_val
+  // device-resident buffer pointers: when set, in_pp[0..1] replace in_words /
+  // in_tags and v_pp[0..2] replace v_keys / v_tags / v_stamp (read at kernel start)
+  void* const* in_pp; void* const* v_pp;
 };
+
+// the input and probed-view pointers of a step, resolved on the device
+struct PPtrs {
+  const void* in_words; const void* in_tags; const void* v_keys; const void* v_tags; const u32* v_stamp;
+};
+LOB_DEV PPtrs resolve_ptrs(const PStep& P) {
+  PPtrs q{P.in_words, P.in_tags, P.v_keys, P.v_tags, P.v_stamp};
+  if (P.in_pp) { q.in_words = P.in_pp[0]; q.in_tags = P.in_pp[1]; }
+  if (P.v_pp) { q.v_keys = P.v_pp[0]; q.v_tags = P.v_pp[1]; q.v_stamp = reinterpret_cast<const u32*>(P.v_pp[2]); }
+  return q;
+}
 
 // size in device memory, capped by the capacity it was launched for
 LOB_DEV u64 dev_size(u64 cap, const u64* dev) { return dev ? (*dev < cap ? *dev : cap) : cap; }

@@ -39,7 +39,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const K* __restr
                                                                 u32* __restrict__ hist, u64 ntiles,
                                                                 const u64* __restrict__ n_dev) {
   constexpr int D = 1 << RB;
-  if (n_dev) n = *n_dev < n ? *n_dev : n;  // tiles past it count nothing
+  if (n_dev) {
+    n = *n_dev < n ? *n_dev : n;  // tiles past it count nothing
+    if (n == 0) return;           // nothing to sort: the scatter will not read the histograms
+  }
   constexpr int IT = SortCfg<K, P>::kItems;
   __shared__ u32 h[kSortWarps][D];
   for (int i = threadIdx.x; i < kSortWarps * D; i += kSortThreads) (&h[0][0])[i] = 0;
