@@ -237,6 +237,10 @@ int lob_reset(lob_engine* e);
  *   "loop_cap_floor" smallest row capacity the device-driven loop plans its
  *                  buffers with before they grow (256..2^24, default 65536;
  *                  small values exercise the regrowth path)
+ *   "packed_backward" 1: the diff-add-mult backward pass replays packed join
+ *                  pipelines on the packed kernels (binding words plus the
+ *                  rows of the facts matched so far); 0: every arm on the
+ *                  general kernels                                   (default 1)
  * LOB_E_ARG for an unknown key or a value out of range. */
 int lob_set_option(lob_engine* e, const char* key, int64_t value);
 

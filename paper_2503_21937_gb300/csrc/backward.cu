@@ -21,6 +21,7 @@
 #include <cstring>
 
 #include "engine.h"
+#include "pjoin.h"
 #include "join_common.cuh"
 #include "scan.cuh"
 
@@ -449,6 +450,123 @@ void replay_arm(lob_engine& e, BwdState& S, const RulePlan& rp, const ArmPlan& A
   }
 }
 
+// The same replay on the packed kernels (pjoin.cu): returns false when the arm
+// is not a packed pipeline of at least one probe, or its head has no dense
+// key map, and the general replay runs instead.
+bool replay_arm_packed(lob_engine& e, BwdState& S, const RulePlan& rp, const ArmPlan& A, u32 k) {
+  if (!e.opt_packed_backward || !A.packed.ok || A.steps.size() < 2) return false;
+  for (const PStep& T : A.packed.steps)
+    if (!pjoin_backward_supported(T)) return false;
+  const RuleAst& R = rp.ast;
+  const u32 hrel = R.head.rel;
+  if (!S.hnew[hrel].p || !S.hrow[hrel].p) return false;
+  RelSt& D = e.rels[R.body[A.delta].rel];
+  ViewSt& DV = D.views[0];
+  RelSt& H = e.rels[hrel];
+  auto adj_of = [&](u32 rel) -> double* {
+    const RelSt& q = e.rels[rel];
+    return q.idb || q.in_has_tags ? S.adj[rel].as<double>() : nullptr;
+  };
+  PBwd B;
+  std::memset(&B, 0, sizeof(B));
+  B.packed_source = 1;
+  B.h_new = S.hnew[hrel].as<u32>();
+  B.h_row = S.hrow[hrel].as<u32>();
+  B.h_keys = H.views[0].keys.p;
+  B.h_key64 = H.views[0].lay.key64;
+  B.h_n = H.views[0].n;
+  B.h_adj = S.adj[hrel].as<double>();
+  B.fact_tags[0] = DV.tags.as<float>();
+  B.fact_adj[0] = adj_of(R.body[A.delta].rel);
+  for (size_t s = 1; s < A.steps.size(); s++) {
+    const u32 rel = R.body[A.steps[s].atom].rel;
+    B.fact_tags[s] = e.rels[rel].views[0].tags.as<float>();
+    B.fact_adj[s] = adj_of(rel);
+  }
+  const void* in_words = DV.keys.p;
+  u64 n_in = DV.n;
+  int side = 0;
+  for (size_t s = 1; s < A.steps.size(); s++) {
+    const StepPlan& SP = A.steps[s];
+    const bool last = s + 1 == A.steps.size();
+    const u32 vrel = R.body[SP.atom].rel;
+    ViewSt& W = e.rels[vrel].views[SP.view];
+    if (!W.n || !n_in) return true;
+    engine_ensure_index(e, W, SP.prefix_len);
+    PStep P = A.packed.steps[s - 1];
+    P.in_words = in_words;
+    P.in_tags = nullptr;
+    P.n_in = n_in;
+    if (s == 1) {  // the delta atom: facts first derived in iteration k - 1
+      P.in_stamp = DV.stamps.as<u32>();
+      P.in_stamp_mode = STAMP_EQ;
+      P.in_stamp_val = k - 1;
+    } else {
+      P.in_stamp_mode = STAMP_NONE;
+    }
+    P.v_keys = W.keys.p;
+    P.v_key64 = W.lay.key64;
+    P.v_tags = W.tags.p;
+    P.v_stamp = W.stamps.as<u32>();
+    P.v_n = W.n;
+    P.v_stamp_mode = STAMP_LT;
+    P.v_stamp_val = SP.probe_old ? k - 1 : k;
+    const IndexSt& I = W.index[SP.prefix_len];
+    P.index_mode = I.mode;
+    P.dense_offs = I.offs.as<u64>();
+    const u64 n_blk = pjoin_loc_blocks(n_in);
+    e.ensure(e.cnt, n_in * 4);
+    e.ensure(e.lo, n_in * 4);
+    e.ensure(e.off, n_blk * 16);
+    P.loc = e.cnt.as<u32>();
+    P.lo32 = e.lo.as<u32>();
+    P.blk_cnt = e.off.as<u64>() + n_blk;
+    P.blk_off = e.off.as<u64>();
+    P.err = reinterpret_cast<u32*>(e.counts.as<u64>() + 1);
+    e.check(cudaMemsetAsync(P.err, 0, sizeof(u64), e.stream), "join error word");
+    pjoin_count(SR_ADD_MULT, P, e.stream);
+    e.after_launch("backward count");
+    e.ensure(e.scratch, scan_scratch_elems(n_blk) * 8 + 64);
+    exclusive_scan<u64, u64>(P.blk_cnt, e.off.as<u64>(), n_blk, e.counts.as<u64>(), e.scratch.as<u64>(), e.stream);
+    e.after_launch("backward scan");
+    e.launches += 1 + scan_launches(n_blk);
+    e.check(cudaMemcpyAsync(e.pinned, e.counts.as<u64>(), 16, cudaMemcpyDeviceToHost, e.stream), "join total");
+    e.sync();
+    if (e.pinned[1] & kErrLocOverflow)
+      throw LobError(LOB_E_ARG, "join step: 1024 consecutive input rows have 2^32 or more matches");
+    const u64 total = e.pinned[0];
+    if (!total) return true;
+    B.last = last;
+    B.v_prow = SP.view ? S.prow[vrel][SP.view].as<u32>() : nullptr;
+    const int nf_in = B.packed_source ? 1 : B.n_in_facts;
+    const int out_side = side ^ 1;
+    if (!last) {
+      e.ensure(e.bind[out_side][0], total * (P.out_w64 ? 8 : 4));
+      P.out_words = e.bind[out_side][0].p;
+      for (int q = 0; q <= nf_in; q++) {
+        e.ensure(e.bfact[out_side][q], total * 4);
+        B.out_rows[q] = e.bfact[out_side][q].as<u32>();
+      }
+    }
+    const u64 ntiles = (total + kEmitTile - 1) / kEmitTile;
+    e.ensure(e.part, (ntiles + 1) * 8);
+    P.total = total;
+    P.j_begin = 0;
+    pjoin_partition(P, ntiles, e.part.as<u64>(), e.stream);
+    pjoin_backward_emit(P, B, e.part.as<u64>(), e.stream);
+    e.after_launch("backward emit");
+    e.launches += 2;
+    if (last) return true;
+    side = out_side;
+    in_words = e.bind[side][0].p;
+    n_in = total;
+    B.packed_source = 0;
+    B.n_in_facts = nf_in + 1;
+    for (int q = 0; q < B.n_in_facts; q++) B.in_rows[q] = e.bfact[side][q].as<u32>();
+  }
+  return true;
+}
+
 }  // namespace
 
 int backward_impl(lob_engine* e, u32 out_rel, const float* grad_tags, float* const* grad_inputs, int mem) {
@@ -536,9 +654,24 @@ int backward_impl(lob_engine* e, u32 out_rel, const float* grad_tags, float* con
         k_f32_to_f64<<<grid_for_n(n_out), 256, 0, e->stream>>>(gdev, n_out, S.adj[out_rel].as<double>());
         e->after_launch("adjoint seed");
       }
+      // Only relations out_rel depends on carry adjoints: rules with another
+      // head contribute nothing and are not replayed.
+      std::vector<char> needed(nrel, 0);
+      needed[out_rel] = 1;
+      for (bool grew = true; grew;) {
+        grew = false;
+        for (auto& p : e->plans)
+          if (needed[p.ast.head.rel])
+            for (auto& a : p.ast.body)
+              if (!needed[a.rel]) needed[a.rel] = grew = true;
+      }
+      // facts first derived in iteration k (the recent set at the start of k + 1)
+      auto new_in = [&](u32 k, u32 rel) -> u64 {
+        return k < e->iter_counts.size() ? e->iter_counts[k][rel].second : e->rels[rel].n_recent;
+      };
       for (u32 k = e->last_iter; k >= 1; k--) {
         for (size_t q = 0; q < nrel; q++) {  // the heads new in iteration k
-          if (!S.hnew[q].p) continue;
+          if (!S.hnew[q].p || !needed[q] || !new_in(k, (u32)q)) continue;
           RelSt& r = e->rels[q];
           e->check(cudaMemsetAsync(S.hnew[q].p, 0, S.hnew[q].cap, e->stream), "new heads");
           k_mark_new<<<grid_for_n(r.views[0].n), 256, 0, e->stream>>>(r.views[0].keys.p, r.views[0].lay.key64,
@@ -548,13 +681,14 @@ int backward_impl(lob_engine* e, u32 out_rel, const float* grad_tags, float* con
         }
         for (auto& p : e->plans)
           for (auto& A : p.arms) {
+            if (!needed[p.ast.head.rel] || !new_in(k, p.ast.head.rel)) continue;  // no adjoint can flow here
             const auto& cnt = e->iter_counts[k - 1];  // (total, recent) per relation at the start of iteration k
             if (!cnt[p.ast.body[A.delta].rel].second) continue;
             bool skip = false;
             for (u32 b : A.before_rels)
               if (cnt[b].first == cnt[b].second) { skip = true; break; }
             if (skip) continue;
-            replay_arm(*e, S, p, A, k);
+            if (!replay_arm_packed(*e, S, p, A, k)) replay_arm(*e, S, p, A, k);
           }
       }
       for (size_t k = 0; k < nrel; k++) {

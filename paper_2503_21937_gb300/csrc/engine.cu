@@ -2188,6 +2188,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "acc_bits" && value >= 1 && value <= 30) e->opt_acc_bits = (int)value;
     else if (k == "driver" && value >= 0 && value <= 2) e->opt_driver = (int)value;
     else if (k == "loop_cap_floor" && value >= 256 && value <= (1 << 24)) e->opt_loop_cap_floor = (int)value;
+    else if (k == "packed_backward" && (value == 0 || value == 1)) e->opt_packed_backward = (int)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

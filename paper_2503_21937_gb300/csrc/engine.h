@@ -191,6 +191,7 @@ struct lob_engine {
   int opt_driver = 1;             // iterations after the first as a device-driven graph when the run qualifies:
                                   // 1 once a host-driven run of the program recorded its sizes, 2 always, 0 never
   int opt_loop_cap_floor = 1 << 16;  // smallest buffer capacity (rows) the device loop plans with
+  int opt_packed_backward = 1;    // diff-add-mult backward replays packed arms on the packed kernels
   std::map<std::string, u64> loop_caps;  // buffer capacities the device loop needed, kept across runs
   u64 host_syncs = 0;             // host waits for the GPU (statistics)
   cudaStream_t capture_stream = nullptr;  // private stream the device loop's graph is captured on (created on first use)

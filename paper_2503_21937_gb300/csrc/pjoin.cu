@@ -707,6 +707,124 @@ __global__ void __launch_bounds__(256) k_pwarp_emit(const __grid_constant__ PSte
   }
 }
 
+// Backward emission (see pjoin.h): one tile of kEmitTile outputs per block,
+// located like the forward emission's.
+template <int NOUT, int NCHK>
+__global__ void __launch_bounds__(256) k_pbwd_emit(const __grid_constant__ PStep P, const __grid_constant__ PBwd B,
+                                                   const u64* __restrict__ part) {
+  constexpr int kItems = kEmitTile / 256;
+  __shared__ __align__(16) u32 row_of[kEmitTile];
+  __shared__ u32 sm[256 / 32 + 1];
+  __shared__ u32 th_inc[256];
+  const u64 j0 = P.j_begin + (u64)blockIdx.x * kEmitTile;
+  const u64 j_end = P.j_begin + P.total;
+  if (j0 >= j_end) return;
+  const u64 r0 = part[blockIdx.x];
+  const u64 r_end = part[blockIdx.x + 1];
+  for (int i = threadIdx.x; i < kEmitTile; i += 256) row_of[i] = 0;
+  __syncthreads();
+  for (u64 r = r0 + 1 + threadIdx.x; r <= r_end; r += 256) {
+    const u64 o = row_off(P, r);
+    if (o < j0 + kEmitTile) atomicMax(&row_of[o - j0], (u32)(r - r0));
+  }
+  __syncthreads();
+  {
+    u32 loc[kItems];
+    u32 m = 0;
+#pragma unroll
+    for (int i = 0; i < kItems; i++) {
+      const u32 x = row_of[threadIdx.x * kItems + i];
+      m = x > m ? x : m;
+      loc[i] = m;
+    }
+    const u32 inc = block_inclusive_max<u32>(m, sm);
+    th_inc[threadIdx.x] = inc;
+    __syncthreads();
+    const u32 ex = threadIdx.x ? th_inc[threadIdx.x - 1] : 0u;
+#pragma unroll
+    for (int i = 0; i < kItems; i++) row_of[threadIdx.x * kItems + i] = loc[i] > ex ? loc[i] : ex;
+  }
+  __syncthreads();
+  RegOp out_op[NOUT];
+  u32 out_sh[NOUT];
+#pragma unroll
+  for (int q = 0; q < NOUT; q++) {
+    out_op[q] = reg_op(P.out[q].op);
+    out_sh[q] = P.out[q].shift;
+  }
+  RegOp ca[NCHK > 0 ? NCHK : 1], cb[NCHK > 0 ? NCHK : 1];
+  bool ceq[NCHK > 0 ? NCHK : 1];
+#pragma unroll
+  for (int q = 0; q < NCHK; q++) {
+    ca[q] = reg_op(P.checks[q].a);
+    cb[q] = reg_op(P.checks[q].b);
+    ceq[q] = P.checks[q].eq != 0;
+  }
+  const u64 invalid_in = P.in_w64 ? ~0ull : 0xFFFFFFFFull;
+  const u64 invalid_out = P.out_w64 ? ~0ull : 0xFFFFFFFFull;
+  const int nf_in = B.packed_source ? 1 : B.n_in_facts;
+#pragma unroll 1
+  for (int i = 0; i < kItems; i++) {
+    const u64 j = j0 + (u64)i * 256 + threadIdx.x;
+    if (j >= j_end) break;
+    const u64 r = r0 + row_of[j - j0];
+    const u64 v = (u64)P.lo32[r] + (j - row_off(P, r));
+    const u64 wi = load_word(P.in_words, P.in_w64, r);
+    const u64 wv = load_word(P.v_keys, P.v_key64, v);
+    bool ok = wi != invalid_in;
+    if (P.n_in_checks) ok = ok && checks_ok(P.in_checks, P.n_in_checks, wi, 0);
+    if (P.v_stamp_mode != STAMP_NONE) {
+      const u32 st = P.v_stamp[v] & 0x7FFFFFFFu;
+      ok = ok && (P.v_stamp_mode == STAMP_LT ? st < P.v_stamp_val : st == P.v_stamp_val);
+    }
+#pragma unroll
+    for (int q = 0; q < NCHK; q++) ok = ok && ((reg_pick(ca[q], wi, wv) == reg_pick(cb[q], wi, wv)) == ceq[q]);
+    u64 w = 0;
+#pragma unroll
+    for (int q = 0; q < NOUT; q++) w |= reg_pick(out_op[q], wi, wv) << out_sh[q];
+    const u32 vrow = B.v_prow ? B.v_prow[v] : (u32)v;
+    if (!B.last) {  // the binding word (dropped: all ones) and the rows of the facts so far
+      const u64 o = j - P.j_begin;
+      if (P.out_w64) reinterpret_cast<u64*>(P.out_words)[o] = ok ? w : invalid_out;
+      else reinterpret_cast<u32*>(P.out_words)[o] = (u32)(ok ? w : invalid_out);
+      for (int q = 0; q < nf_in; q++) B.out_rows[q][o] = B.packed_source ? (u32)r : B.in_rows[q][r];
+      B.out_rows[nf_in][o] = vrow;
+      continue;
+    }
+    if (!ok) continue;
+    if (!((B.h_new[w >> 5] >> (w & 31)) & 1u)) continue;  // the head was not new (or was clamped) in this iteration
+    u64 hj;
+    if (B.h_row) {
+      hj = B.h_row[w];
+    } else {
+      u64 lo = 0, hi = B.h_n;
+      if (B.h_key64) {
+        const u64* a = reinterpret_cast<const u64*>(B.h_keys);
+        while (lo < hi) { const u64 m = (lo + hi) >> 1; if (a[m] < w) lo = m + 1; else hi = m; }
+      } else {
+        const u32* a = reinterpret_cast<const u32*>(B.h_keys);
+        while (lo < hi) { const u64 m = (lo + hi) >> 1; if (a[m] < (u32)w) lo = m + 1; else hi = m; }
+      }
+      hj = lo;
+    }
+    const double adj = B.h_adj[hj];
+    if (adj == 0.0) continue;
+    u32 rows[kMaxArity + 1];
+    float tags[kMaxArity + 1];
+    for (int q = 0; q < nf_in; q++) rows[q] = B.packed_source ? (u32)r : B.in_rows[q][r];
+    rows[nf_in] = vrow;
+    const int nf = nf_in + 1;
+    for (int q = 0; q < nf; q++) tags[q] = B.fact_tags[q][rows[q]];
+    for (int q = 0; q < nf; q++) {
+      if (!B.fact_adj[q]) continue;
+      double c = adj;
+      for (int l = 0; l < nf; l++)
+        if (l != q) c *= (double)tags[l];
+      atomicAdd(B.fact_adj[q] + rows[q], c);
+    }
+  }
+}
+
 unsigned grid_n(u64 n) {
   u64 b = (n + 255) / 256;
   if (b > 152ull * 16) b = 152ull * 16;
@@ -804,6 +922,25 @@ void pjoin_emit(int sem, const PStep& P, const u64* part, cudaStream_t st) {
   ProfScope ps("join_emit", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + 8.0) + P.total * (vb + ob), st);
   if (P.total) by_sem_p<PEmitL>(sem, P, part, st);
 }
+
+void pjoin_backward_emit(const PStep& P, const PBwd& B, const u64* part, cudaStream_t st) {
+  if (!P.total) return;
+  const u64 tiles = (P.total + kEmitTile - 1) / kEmitTile;
+  const int nf = (B.packed_source ? 1 : B.n_in_facts) + 1;
+  const double vb = (P.v_key64 ? 8 : 4) + 4.0;
+  // per output: the matched key and stamp; an intermediate step writes its word
+  // and carried rows, the last step probes the new-head bitmap
+  ProfScope ps("bwd_emit", P.n_in * ((P.in_w64 ? 8.0 : 4.0) + 8.0) +
+                               P.total * (vb + (B.last ? 4.0 : (P.out_w64 ? 8.0 : 4.0) + 4.0 * nf)), st);
+  const int no = P.n_out, nc = P.n_checks;
+#define LOB_BWD(NO, NC) if (no == NO && nc == NC) { k_pbwd_emit<NO, NC><<<(unsigned)tiles, 256, 0, st>>>(P, B, part); return; }
+  LOB_BWD(1, 0) LOB_BWD(2, 0) LOB_BWD(3, 0) LOB_BWD(4, 0) LOB_BWD(5, 0)
+  LOB_BWD(1, 1) LOB_BWD(2, 1) LOB_BWD(3, 1) LOB_BWD(4, 1) LOB_BWD(5, 1)
+  LOB_BWD(1, 2) LOB_BWD(2, 2) LOB_BWD(3, 2) LOB_BWD(4, 2) LOB_BWD(5, 2)
+#undef LOB_BWD
+}
+
+bool pjoin_backward_supported(const PStep& P) { return P.n_out >= 1 && P.n_out <= 5 && P.n_checks <= 2; }
 
 void pjoin_project(int sem, const PStep& P, cudaStream_t st) {
   ProfScope ps("project", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + row_bytes(sem, P.out_w64, false)), st);

@@ -84,6 +84,29 @@ void pjoin_partition(const PStep& P, u64 ntiles, u64* part, cudaStream_t st);
 void pjoin_emit(int sem, const PStep& P, const u64* part, cudaStream_t st);
 void pjoin_project(int sem, const PStep& P, cudaStream_t st);
 
+// Backward replay of a packed arm (diff-add-mult): the same count / partition
+// as the forward steps, then an emission that carries, per binding row, the
+// primary-view rows of the body facts matched so far; the last step forms the
+// head key, keeps groundings whose head was first derived (unclamped) in the
+// replayed iteration, and adds adjoint(head) * (product of the other facts'
+// tags) to each body fact's adjoint.
+struct PBwd {
+  int packed_source;                    // input rows are rows of the delta relation's primary view (fact 0 = row)
+  int n_in_facts;                       // facts carried by a binding-row input
+  const u32* in_rows[kMaxArity];        // their rows
+  u32* out_rows[kMaxArity + 1];         // intermediate step: the rows carried forward (n_in_facts + 1)
+  const u32* v_prow;                    // probed view row -> primary row (null: primary view)
+  const float* fact_tags[kMaxArity + 1];  // per body fact of the grounding: its relation's tags, by primary row
+  double* fact_adj[kMaxArity + 1];      // per body fact: adjoint array (null: no adjoint needed)
+  int last;
+  const u32* h_new;                     // bitmap of the head keys new (unclamped) in the replayed iteration
+  const u32* h_row;                     // dense head key -> primary row (null: binary search of h_keys)
+  const void* h_keys; int h_key64; u64 h_n;
+  const double* h_adj;
+};
+void pjoin_backward_emit(const PStep& P, const PBwd& B, const u64* part, cudaStream_t st);
+bool pjoin_backward_supported(const PStep& P);  // the emission has a kernel for the step's shape
+
 // Warp-balanced steps (unit semiring).  pjoin_warp_supported: the step has a
 // specialised warp kernel.  pjoin_warp_count: outputs per block of 1024 input
 // rows (pjoin_warp_blocks(n_in) entries); after an exclusive scan of them into

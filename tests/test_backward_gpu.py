@@ -98,3 +98,31 @@ def test_autograd_function():
     res = oracle_run(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, "diff_add_mult")
     want = res.vjp({"reach": gout.cpu().numpy().astype(np.float64)})["edge"]
     np.testing.assert_allclose(probs.grad.cpu().numpy(), want, rtol=1e-4, atol=1e-4)
+
+
+@pytest.mark.parametrize("packed", [1, 0])
+def test_packed_and_general_backward_replays(packed):
+    """The diff-add-mult backward on the packed kernels (binding words plus the
+    rows of the facts matched so far) and on the general kernels, each against
+    the oracle: a linear rule (grid reachability) and the three-atom kinship
+    rule with a filter, batched."""
+    def grads(program, inputs, out, seed):
+        res = oracle_run(program, inputs, "diff_add_mult")
+        rel = res.relation(out)
+        gout = W.stream(seed).normal(rel.cols.shape[1])
+        want = res.vjp({out: gout})
+        e, st, got = engine_run(program, inputs, "diff_add_mult", read=[out], options={"packed_backward": packed})
+        gin = {k: np.zeros(len(v[1]), np.float32) for k, v in inputs.items() if len(v) > 1 and v[1] is not None}
+        e.backward(out, gout.astype(np.float32), gin)
+        e.close()
+        assert np.array_equal(got[out].cols, rel.cols)
+        for k, g in gin.items():
+            np.testing.assert_allclose(g, want[k], rtol=1e-4, atol=1e-4, err_msg=k)
+    g = W.grid_reach_instance(14, sub=95)
+    src, dst, p = g["edge"]
+    grads(W.REACH_PROGRAM, {"edge": ((src, dst), (p * 0.5).astype(np.float32)), "start": (g["start"],)}, "reach", 96)
+    B = W.batched_instance(5)
+    f, c = B["fact"], B["comp"]
+    inputs = {"fact": ((f[0], f[1], f[2]), (f[3] * 0.6).astype(np.float32), f[4]),
+              "comp": ((c[0], c[1], c[2]), None, c[4])}
+    grads(W.KIN_PROGRAM, inputs, "kin", 97)
