@@ -131,27 +131,99 @@ def make_inputs(sg_nodes=SG_NODES, tc_nodes=TC_NODES, tc_edges=TC_EDGES):
             "tc": (W.TC_PROGRAM, {"edge": np.stack([s, d])})}
 
 
-def cpu_oracle_sample(budget_s: float = 20.0):
-    """Time the oracle on reduced instances of the same generators."""
+def cpu_info() -> dict:
+    """Host cores and CPU model of the machine the CPU baselines run on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and model is None:
+                    model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
+def cpu_oracle_sample():
+    """The oracle (single thread) on the reduced instances of the benchmark's
+    generators: same generation on a 5,000-node tree and transitive closure on a
+    2,000-node / 10,000-edge power-law graph, one run each."""
     import oracle
     oracle.build()
-    inputs = make_inputs(sg_nodes=2000, tc_nodes=600, tc_edges=3000)
+    inputs = make_inputs(sg_nodes=5000, tc_nodes=2000, tc_edges=10000)
     t0 = time.perf_counter()
     derived = 0
-    reps = 0
-    while True:
-        for name, (prog, rels) in inputs.items():
-            res = oracle.run(prog, {k: (v,) for k, v in rels.items()})
-            head = "sg" if name == "sg" else "path"
-            derived += res.relation(head).cols.shape[1]
-        reps += 1
-        if time.perf_counter() - t0 > budget_s / 2 or reps >= 5:
-            break
+    for name, (prog, rels) in inputs.items():
+        res = oracle.run(prog, {k: (v,) for k, v in rels.items()})
+        derived += res.relation("sg" if name == "sg" else "path").cols.shape[1]
     dt = time.perf_counter() - t0
-    return {"value": derived / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} x (same generation on a 2,000-node random tree + transitive closure on a "
-                      f"600-node/3,000-edge power-law graph), naive FP64 std::map oracle, single thread, "
-                      f"{dt:.1f} s"}
+    return {"value": derived / dt, "unit": UNIT, "cores": 1, "kind": "oracle", **cpu_info(),
+            "sample": f"same generation on a 5,000-node random tree + transitive closure on a 2,000-node/10,000-edge "
+                      f"power-law graph (reduced instances of the benchmark's generators), naive FP64 std::map oracle, "
+                      f"single thread, {derived} derived tuples in {dt:.1f} s"}
+
+
+def _bfs_count(args):
+    """Reachable (source, target) pairs from a range of sources (one BFS each)."""
+    lo, hi, s, d, n = args
+    import numpy as np
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import breadth_first_order
+    g = csr_matrix((np.ones(len(s)), (s, d)), shape=(n, n))
+    gt = g.T.tocsr()
+    tot = 0
+    for src in range(lo, hi):
+        order = breadth_first_order(g, src, directed=True, return_predecessors=False)
+        tot += len(order) - 1
+        preds = gt.indices[gt.indptr[src]:gt.indptr[src + 1]]
+        if np.isin(preds, order).any():  # a cycle leads back to the source
+            tot += 1
+    return tot
+
+
+def cpu_checkers(andersen: bool = False) -> dict:
+    """Full-size textbook computations of the benchmark's relations on the host:
+    the same-generation closed form (sum over tree levels of n_d (n_d - 1)), the
+    transitive closure by one BFS per source on every host core, the oracle on
+    the 1,000-node / 3,000-edge Erdos-Renyi closure, and (optionally, about two
+    minutes) Andersen points-to as a boolean sparse-matrix fixpoint."""
+    import multiprocessing as mp
+    import numpy as np
+    out = {}
+    parent, child, depth = W.random_tree(SG_NODES)
+    t0 = time.perf_counter()
+    counts = np.bincount(depth)
+    n_sg = int(sum(int(c) * (int(c) - 1) for c in counts[1:]))
+    dt = time.perf_counter() - t0
+    out["sg_50k_closed_form"] = {"tuples": n_sg, "s": dt, "cores": 1}
+    s, d = W.chung_lu_power_law(TC_NODES, TC_EDGES)
+    cores = os.cpu_count() or 1
+    step = (TC_NODES + 4 * cores - 1) // (4 * cores)
+    jobs = [(lo, min(lo + step, TC_NODES), s, d, TC_NODES) for lo in range(0, TC_NODES, step)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        n_tc = sum(pool.map(_bfs_count, jobs))
+    dt = time.perf_counter() - t0
+    out["tc_20k_parallel_bfs"] = {"tuples": n_tc, "s": dt, "cores": cores, "tuples_per_s": n_tc / dt}
+    import oracle
+    oracle.build()
+    a, b = W.erdos_renyi(1000, 3000)
+    t0 = time.perf_counter()
+    n_er = oracle.run(W.TC_PROGRAM, {"edge": ((a, b),)}).relation("path").cols.shape[1]
+    dt = time.perf_counter() - t0
+    out["er_tc_1k_oracle"] = {"tuples": n_er, "s": dt, "cores": 1, "tuples_per_s": n_er / dt}
+    if andersen:
+        sys.path.insert(0, ROOT)
+        from tests import pins
+        A = W.andersen_program(200_000, 1_000_000)
+        t0 = time.perf_counter()
+        n_pt = pins.andersen_sparse(A["addr"], A["assign"], A["load"], A["store"], 200_000).nnz
+        dt = time.perf_counter() - t0
+        out["andersen_200k_sparse_fixpoint"] = {"tuples": int(n_pt), "s": dt, "cores": 1, "tuples_per_s": n_pt / dt}
+    return out
 
 
 def max_over_ranks(ms: float, dist=None, device: str = "cuda") -> float:
@@ -204,7 +276,8 @@ def reference_arm(args):
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                       "data": "synthetic", "config": base_config(),
-                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                                       **cpu_info()},
                       "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -232,46 +305,135 @@ def _batched_tensors(B, sel=None):
             "comp": (T(np.stack([c[0][mc], c[1][mc], c[2][mc]])), None, T(c[4][mc]))}
 
 
-def batched_fwd_bwd(n_samples=512, loop_samples=32, reps=3):
+def batched_fwd_bwd(n_samples=512, reps=3):
     """Forward + backward (torch.autograd) samples/s of the batched workload in
-    one engine launch, against the same API called once per sample."""
+    one engine run, with the device-driven and the host-driven iteration loop,
+    against the same API called once per sample for every sample.  Engines are
+    reused across calls (the binding keeps idle engines per program and size
+    class); the first call of each setting is an untimed warm-up."""
     import torch
-    from paper_2503_21937_gb300.autograd import fixpoint
+    from paper_2503_21937_gb300.autograd import LAST_STATS, fixpoint
     B = W.batched_instance(n_samples)
     full = _batched_tensors(B)
-    singles = [_batched_tensors(B, i) for i in range(loop_samples)]
+    singles = [_batched_tensors(B, i) for i in range(n_samples)]
 
-    def fwd_bwd(inp, semiring):
+    def fwd_bwd(inp, semiring, options):
         ins = {k: (v[0], v[1].clone().requires_grad_(True) if v[1] is not None else None, v[2]) for k, v in inp.items()}
-        out = fixpoint(BATCH_PROGRAM, ins, semiring, outputs=["reach", "kin"])
+        out = fixpoint(BATCH_PROGRAM, ins, semiring, outputs=["reach", "kin"], options=options)
+        stats = dict(LAST_STATS)
         loss = out["reach"][1].sum() + out["kin"][1].sum()
         loss.backward()
-        return out
+        return stats
 
     res = {}
     for semiring in ("diff_add_mult", "diff_max_min"):
-        fwd_bwd(full, semiring)
-        torch.cuda.synchronize()
-        t = []
-        for _ in range(reps):
-            t0 = time.perf_counter()
-            fwd_bwd(full, semiring)
+        r = {}
+        for name, opts in (("device_driven", {"driver": 1}), ("host_driven", {"driver": 0})):
+            fwd_bwd(full, semiring, opts)
             torch.cuda.synchronize()
-            t.append(time.perf_counter() - t0)
-        batched = n_samples / min(t)
-        fwd_bwd(singles[0], semiring)
+            t, st = [], None
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                st = fwd_bwd(full, semiring, opts)
+                torch.cuda.synchronize()
+                t.append(time.perf_counter() - t0)
+            r[name] = {"samples_per_s": round(n_samples / min(t), 1), "ms": round(1e3 * min(t), 2),
+                       "iterations": st["iterations"], "device_iterations": st["device_iterations"],
+                       "graph_launches": st["graph_launches"], "host_syncs_per_run": st["host_syncs"],
+                       "host_syncs_per_device_iteration": round(st["graph_launches"] / st["device_iterations"], 4)
+                       if st["device_iterations"] else None}
+        fwd_bwd(singles[0], semiring, {})
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for s in singles:
-            fwd_bwd(s, semiring)
+        for sgl in singles:
+            fwd_bwd(sgl, semiring, {})
         torch.cuda.synchronize()
-        loop = loop_samples / (time.perf_counter() - t0)
-        res[semiring] = {"batched_samples_per_s": round(batched, 1), "per_sample_loop_samples_per_s": round(loop, 1),
-                         "speedup": round(batched / loop, 1), "batched_ms": round(1e3 * min(t), 2)}
+        loop = n_samples / (time.perf_counter() - t0)
+        best = max(r.values(), key=lambda x: x["samples_per_s"])["samples_per_s"]
+        res[semiring] = {**r, "per_sample_loop_samples_per_s": round(loop, 1),
+                         "speedup_device_driven_vs_loop": round(r["device_driven"]["samples_per_s"] / loop, 1),
+                         "speedup_best_vs_loop": round(best / loop, 1)}
     return {"metric": "batched fwd+bwd samples/s vs per-sample (same GB300)", "samples": n_samples,
-            "loop_sample_subset": loop_samples,
+            "per_sample_loop": f"all {n_samples} samples, one fixpoint + backward call each, engines reused",
             "workload": "512 samples: grid reachability (side U{8..48}) + 20-relation kinship composition, f32 tags, "
                         "torch.autograd backward of sum(tags)", "results": res}
+
+
+# ---------------------------------------------------------------------------
+# the other configurations: throughput lines (device time, median of 5 runs
+# after a warm-up run on the same engine) with the dominant kernel's roofline
+# ---------------------------------------------------------------------------
+def _roofline(prof: dict, peak: float, peak_kind: str):
+    # phases of the device-driven loop carry no bytes; kernels timed one by one do
+    kern = {k: v for k, v in prof.items() if v["bytes"] > 0 and v["ms"] > 0}
+    if not kern:
+        return None
+    name, v = max(kern.items(), key=lambda kv: kv[1]["ms"])
+    ach = (v["bytes"] / v["launches"]) / (v["ms"] / v["launches"] / 1e3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "peak_source": peak_kind, "share": round(v["ms"] / sum(x["ms"] for x in kern.values()), 3)}
+
+
+def config_legs(runs: int = 5) -> dict:
+    import torch
+    from paper_2503_21937_gb300 import Engine
+    peak, peak_kind = load_peaks()
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a).astype(np.int32)).cuda()
+    F = lambda a: torch.from_numpy(np.ascontiguousarray(a).astype(np.float32)).cuda()
+    a, b = W.erdos_renyi(1000, 3000)
+    g = W.grid_reach_instance(64)
+    gs, gd, gp = g["edge"]
+    A = W.andersen_program(200_000, 1_000_000)
+    cases = {
+        "er_tc_1k_3k_unit": (W.TC_PROGRAM, {"edge": (T(np.stack([a, b])), None)}, "unit", ["path"], None),
+        "grid_64_diff_max_min_fwd_bwd": (W.REACH_PROGRAM, {"edge": (T(np.stack([gs, gd])), F(gp)),
+                                                           "start": (T(np.zeros((1, 1))), None)},
+                                         "diff_max_min", ["reach"], "edge"),
+        "grid_64_diff_add_mult_fwd_bwd": (W.REACH_PROGRAM, {"edge": (T(np.stack([gs, gd])), F(gp)),
+                                                            "start": (T(np.zeros((1, 1))), None)},
+                                          "diff_add_mult", ["reach"], "edge"),
+        "andersen_200k_1m_unit": (W.ANDERSEN_PROGRAM, {k: (T(np.stack([v[0], v[1]])), None) for k, v in A.items()},
+                                  "unit", ["pt"], None),
+    }
+    out = {}
+    for name, (prog, ins, sr, heads, grad_rel) in cases.items():
+        e = Engine()
+        e.program(prog)
+
+        def one(profile=False, driver=1):
+            e.reset()
+            e.set_option("profile", 1 if profile else 0)
+            e.set_option("driver", driver)
+            for rel, (c, p) in ins.items():
+                e.load(rel, c, p)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            st = e.run(sr)
+            if grad_rel:
+                n = e.size(heads[0])
+                gin = {grad_rel: torch.zeros(ins[grad_rel][0].shape[1], device="cuda")}
+                e.backward(heads[0], torch.ones(n, device="cuda"), gin)
+            ev1.record()
+            ev1.synchronize()
+            return st, ev0.elapsed_time(ev1)
+
+        one()
+        times, st = [], None
+        for _ in range(runs):
+            st, ms = one()
+            times.append(ms)
+        ms = statistics.median(times)
+        e.profile_reset()
+        one(profile=True, driver=0)  # per-kernel timing on the host-driven loop
+        prof = e.profile()
+        e.close()
+        out[name] = {"semiring": sr, "derived": st["derived"], "candidates": st["candidates"],
+                     "iterations": st["iterations"], "device_iterations": st["device_iterations"],
+                     "ms": round(ms, 3), "derived_tuples_per_s": st["derived"] / (ms / 1e3),
+                     "candidate_tuples_per_s": st["candidates"] / (ms / 1e3),
+                     "timed": "fixpoint + backward" if grad_rel else "fixpoint",
+                     "roofline": _roofline(prof, peak, peak_kind)}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -326,6 +488,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=1, help="extra steps with per-kernel CUDA-event timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched fwd+bwd measurement")
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-configuration throughput lines")
+    ap.add_argument("--cpu-andersen", action="store_true",
+                    help="also time the full-size Andersen sparse-matrix checker on the host (about two minutes)")
     ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
                     help="engine option applied to every engine (repeatable)")
     ap.add_argument("--profile-case", choices=["sort_u32_2e26", "tc_8k", "sg_20k"],
@@ -467,12 +632,16 @@ def main():
         e2e = {"value": derived[0] / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)}
 
+    configs = None
+    if not args.no_configs:
+        configs = config_legs()
     batched = None
     if not args.no_batched:
         batched = batched_fwd_bwd()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample()
+        cpu["checkers"] = cpu_checkers(andersen=args.cpu_andersen)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -480,7 +649,8 @@ def main():
                 "config": {**base_config(world), "derived_per_step": derived[0], "iterations": iters,
                            "join_outputs": cands, "engine_options": args.option},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "kernels": kernels, "kernels_by_workload": by_workload, "batched": batched}
+                "clocks": clk, "kernels": kernels, "kernels_by_workload": by_workload, "configs": configs,
+                "batched": batched}
         print(json.dumps(line))
     for e in engines.values():
         e.close()

@@ -24,14 +24,14 @@ _IDLE: dict = {}
 _MAX_IDLE = 4
 
 
-def _engine_key(program, names, cols):
+def _engine_key(program, names, cols, options):
     rows = sum(int(c.shape[1]) for c in cols)
     stream = torch.cuda.current_stream().cuda_stream
     return (program, tuple(names), tuple(int(c.shape[0]) for c in cols), stream, torch.cuda.current_device(),
-            max(rows, 1).bit_length())
+            max(rows, 1).bit_length(), tuple(sorted(options.items())))
 
 
-def _take_engine(key, program):
+def _take_engine(key, program, options):
     idle = _IDLE.get(key)
     if idle:
         e = idle.pop()
@@ -39,6 +39,8 @@ def _take_engine(key, program):
         return e
     e = Engine()
     e.program(program)
+    for k, v in options.items():
+        e.set_option(k, v)
     return e
 
 
@@ -53,14 +55,17 @@ def _give_back(key, e):
 class _FixpointFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, spec, *probs):
-        program, names, cols, samples, semiring, outputs = spec
-        key = _engine_key(program, names, cols)
-        e = _take_engine(key, program)
+        program, names, cols, samples, semiring, outputs, options = spec
+        key = _engine_key(program, names, cols, options)
+        e = _take_engine(key, program, options)
+        ctx.stats = None
         for name, c, p, s in zip(names, cols, probs, samples):
             if name not in e.ids:
                 e.declare(name, c.shape[0])
             e.load(name, c, p.detach() if p is not None else None, s)
-        e.run(semiring)
+        ctx.stats = e.run(semiring)
+        LAST_STATS.clear()
+        LAST_STATS.update(ctx.stats)
         rels = [e.read(o, device=True) for o in outputs]
         ctx.engine = e
         ctx.key = key
@@ -78,7 +83,7 @@ class _FixpointFn(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, *grads):
-        program, names, cols, samples, semiring, outputs = ctx.spec
+        program, names, cols, samples, semiring, outputs, options = ctx.spec
         e = ctx.engine
         if semiring not in _DIFF or e is None:
             raise RuntimeError("gradients need a diff_* semiring")
@@ -93,10 +98,15 @@ class _FixpointFn(torch.autograd.Function):
         return (None, *[gin.get(n) if hp else None for n, hp in zip(names, ctx.has_prob)])
 
 
-def fixpoint(program: str, inputs: dict, semiring: str = "diff_add_mult", outputs=None):
+# statistics (lob_stats) of the most recent forward run, for benchmarks
+LAST_STATS: dict = {}
+
+
+def fixpoint(program: str, inputs: dict, semiring: str = "diff_add_mult", outputs=None, options=None):
     """inputs: name -> (cols (arity, n) int tensor, probs (n,) float tensor or None,
     sample ids (n,) int tensor or None), all on CUDA.  Returns name -> (cols,
-    tags, sample ids) for each output relation (default: every rule head)."""
+    tags, sample ids) for each output relation (default: every rule head).
+    options: engine options (lob_set_option keys) for the engines that run it."""
     if outputs is None:
         heads = []
         for line in program.split("."):
@@ -110,7 +120,7 @@ def fixpoint(program: str, inputs: dict, semiring: str = "diff_add_mult", output
     cols = [inputs[n][0] for n in names]
     probs = [inputs[n][1] if len(inputs[n]) > 1 else None for n in names]
     samples = [inputs[n][2] if len(inputs[n]) > 2 else None for n in names]
-    spec = (program, names, cols, samples, semiring, list(outputs))
+    spec = (program, names, cols, samples, semiring, list(outputs), dict(options or {}))
     res = _FixpointFn.apply(spec, *probs)
     m = len(outputs)
     return {o: (res[m + i], res[i], res[2 * m + i]) for i, o in enumerate(outputs)}
