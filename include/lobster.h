@@ -237,6 +237,10 @@ int lob_reset(lob_engine* e);
  *   "loop_cap_floor" smallest row capacity the device-driven loop plans its
  *                  buffers with before they grow (256..2^24, default 65536;
  *                  small values exercise the regrowth path)
+ *   "cross_join"   1: under LOB_UNIT, an arm with two probes keyed by the
+ *                  delta row alone (same generation: children(a) x
+ *                  children(b)) whose new facts only set bitmap bits runs
+ *                  as one fused cross-product step; 0: two steps    (default 1)
  *   "packed_backward" 1: the diff-add-mult backward pass replays packed join
  *                  pipelines on the packed kernels (binding words plus the
  *                  rows of the facts matched so far); 0: every arm on the

@@ -467,6 +467,96 @@ static PackedArm compile_packed(lob_engine& e, const RuleAst& R, const ArmPlan& 
   return out;
 }
 
+// The fused cross-product form of a two-probe arm whose second probe's prefix
+// is bound by the delta atom alone (see pjoin_warp_cross_bitmap).
+static void compile_cross(lob_engine& e, const RuleAst& R, const ArmPlan& A, PackedArm& out) {
+  if (!out.ok || A.steps.size() != 3) return;
+  const int nv = (int)R.var_names.size();
+  std::vector<POperand> loc(nv, op_const(0));
+  std::vector<char> src(nv, 0);
+  const Layout& L0 = e.rels[R.body[A.delta].rel].views[0].lay;
+  for (size_t c = 0; c < R.body[A.delta].args.size(); c++) {
+    const Term& t = R.body[A.delta].args[c];
+    if (t.var && !src[t.v]) {
+      loc[t.v] = op_field(0, L0.shift[c], L0.width[c]);
+      src[t.v] = 1;
+    }
+  }
+  const POperand sample = L0.swidth ? op_field(0, L0.sshift, L0.swidth) : op_const(0);
+  const StepPlan& S1 = A.steps[1];
+  const ViewSt& W1 = e.rels[R.body[S1.atom].rel].views[S1.view];
+  for (int j = S1.prefix_len; j < (int)R.body[S1.atom].args.size(); j++)
+    if (S1.act[j].op == OP_BIND) loc[R.body[S1.atom].args[W1.perm[j]].v] = op_field(1, W1.lay.shift[j], W1.lay.width[j]);
+  const StepPlan& S2 = A.steps[2];
+  const AtomAst& atom = R.body[S2.atom];
+  const ViewSt& W2 = e.rels[atom.rel].views[S2.view];
+  const Layout& WL = W2.lay;
+  for (int j = 0; j < S2.prefix_len; j++) {
+    const Term& t = atom.args[W2.perm[j]];
+    if (t.var && !src[t.v]) return;  // keyed by a variable the first probe binds: no cross product
+  }
+  PStep P;
+  std::memset(&P, 0, sizeof(P));
+  const int rs = rest_shift(WL, S2.prefix_len);
+  auto term_op = [&](const Term& t) { return t.var ? loc[t.v] : op_const(t.v); };
+  if (WL.swidth) {
+    PField f{};
+    f.op = sample;
+    f.shift = (uint8_t)(WL.sshift - rs);
+    f.limit_bits = (uint8_t)WL.swidth;
+    P.prefix[P.n_prefix++] = f;
+  }
+  for (int j = 0; j < S2.prefix_len; j++) {
+    PField f{};
+    f.op = term_op(atom.args[W2.perm[j]]);
+    f.shift = (uint8_t)(WL.shift[j] - rs);
+    f.limit_bits = (uint8_t)WL.width[j];
+    P.prefix[P.n_prefix++] = f;
+  }
+  P.rest_shift = rs >= 64 ? 0 : rs;
+  P.whole_view = S2.prefix_len == 0 && WL.swidth == 0;
+  for (int j = S2.prefix_len; j < (int)atom.args.size(); j++) {
+    const Term& t = atom.args[W2.perm[j]];
+    const POperand f = op_field(3, WL.shift[j], WL.width[j]);
+    const ColAct& act = S2.act[j];
+    if (act.op == OP_BIND) {
+      loc[t.v] = f;
+    } else {
+      if (P.n_checks >= kMaxPChecks) return;
+      PCheck c{};
+      c.a = f;
+      c.b = act.op == OP_CHECK_CONST ? op_const(act.cnst) : loc[t.v];
+      c.eq = 1;
+      P.checks[P.n_checks++] = c;
+    }
+  }
+  for (int f : S2.filters) {
+    if (P.n_checks >= kMaxPChecks) return;
+    PCheck c{};
+    c.a = term_op(R.filters[f].a);
+    c.b = term_op(R.filters[f].b);
+    c.eq = R.filters[f].eq ? 1 : 0;
+    P.checks[P.n_checks++] = c;
+  }
+  const Layout& HL = e.rels[R.head.rel].views[0].lay;
+  for (size_t c = 0; c < R.head.args.size(); c++) {
+    PField f{};
+    f.op = term_op(R.head.args[c]);
+    f.shift = (uint8_t)HL.shift[c];
+    P.out[P.n_out++] = f;
+  }
+  if (HL.swidth) {
+    PField f{};
+    f.op = sample;
+    f.shift = (uint8_t)HL.sshift;
+    P.out[P.n_out++] = f;
+  }
+  P.out_w64 = HL.key64;
+  if (!pjoin_cross_supported(out.steps[0], P)) return;
+  out.cross = P;
+  out.cross_ok = true;
+}
+
 static void prepare(lob_engine& e, int sem) {
   release_derived(e);
   e.semiring = sem;
@@ -538,7 +628,10 @@ static void prepare(lob_engine& e, int sem) {
         }
     }
   for (auto& p : e.plans)
-    for (auto& A : p.arms) A.packed = e.opt_packed_join ? compile_packed(e, p.ast, A) : PackedArm{};
+    for (auto& A : p.arms) {
+      A.packed = e.opt_packed_join ? compile_packed(e, p.ast, A) : PackedArm{};
+      if (sem == SR_UNIT) compile_cross(e, p.ast, A, A.packed);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1050,6 +1143,49 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
       e.cand_emitted += sub;
     }
     return;
+  }
+  if (A.packed.cross_ok && e.opt_cross_join && e.opt_warp_join && H.extract) {
+    // both probes keyed by the delta row: one pass over the products
+    const StepPlan& S1 = A.steps[1];
+    const StepPlan& S2 = A.steps[2];
+    RelSt& V1 = e.rels[R.body[S1.atom].rel];
+    RelSt& V2 = e.rels[R.body[S2.atom].rel];
+    ViewSt& W1 = V1.views[S1.view];
+    ViewSt& W2 = V2.views[S2.view];
+    if (W1.stale) rebuild_view(e, V1, W1);
+    if (W2.stale) rebuild_view(e, V2, W2);
+    if (W1.n < (1ull << 27) && W2.n < (1ull << 27)) {
+      if (!W1.n || !W2.n) return;
+      ensure_index(e, W1, S1.prefix_len);
+      ensure_index(e, W2, S2.prefix_len);
+      PStep PA = A.packed.steps[0];
+      PA.in_words = D.rkeys.p;
+      PA.in_tags = nullptr;
+      PA.n_in = D.n_recent;
+      PA.v_keys = W1.keys.p;
+      PA.v_key64 = W1.lay.key64;
+      PA.v_n = W1.n;
+      PA.v_stamp_mode = STAMP_NONE;
+      PA.index_mode = W1.index[S1.prefix_len].mode;
+      PA.dense_offs = W1.index[S1.prefix_len].offs.as<u64>();
+      PStep PB = A.packed.cross;
+      PB.v_keys = W2.keys.p;
+      PB.v_key64 = W2.lay.key64;
+      PB.v_n = W2.n;
+      PB.index_mode = W2.index[S2.prefix_len].mode;
+      PB.dense_offs = W2.index[S2.prefix_len].offs.as<u64>();
+      PB.bitmap = H.bitmap.as<u32>();
+      H.touched = true;
+      const u64 before = g_prof ? e.read_u64(e.counts.as<u64>() + 13) : 0;
+      pjoin_warp_cross_bitmap(PA, PB, e.counts.as<u64>() + 13, e.stream);
+      e.after_launch("join emit");
+      e.launches++;
+      if (g_prof) {
+        const u64 outs = e.read_u64(e.counts.as<u64>() + 13) - before;
+        g_prof->add_last_bytes(outs * ((W1.lay.key64 ? 8.0 : 4.0) + (W2.lay.key64 ? 8.0 : 4.0) + 4.0));
+      }
+      return;
+    }
   }
   const void* in_words = D.rkeys.p;
   const void* in_tags = D.rtags.p;
@@ -2189,6 +2325,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "driver" && value >= 0 && value <= 2) e->opt_driver = (int)value;
     else if (k == "loop_cap_floor" && value >= 256 && value <= (1 << 24)) e->opt_loop_cap_floor = (int)value;
     else if (k == "packed_backward" && (value == 0 || value == 1)) e->opt_packed_backward = (int)value;
+    else if (k == "cross_join" && (value == 0 || value == 1)) e->opt_cross_join = (int)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

@@ -127,6 +127,11 @@ struct StepPlan {
 struct PackedArm {
   bool ok = false;
   std::vector<PStep> steps;
+  // two probes where the second is keyed by the delta row alone: the second
+  // probe compiled against the delta row (word 0), the first probe's key
+  // (word 1) and its own key (word 3), for the fused cross-product step
+  bool cross_ok = false;
+  PStep cross;
 };
 struct ArmPlan {
   int delta = 0;
@@ -192,6 +197,7 @@ struct lob_engine {
                                   // 1 once a host-driven run of the program recorded its sizes, 2 always, 0 never
   int opt_loop_cap_floor = 1 << 16;  // smallest buffer capacity (rows) the device loop plans with
   int opt_packed_backward = 1;    // diff-add-mult backward replays packed arms on the packed kernels
+  int opt_cross_join = 1;         // unit semiring: fused cross-product step for two probes keyed by the delta row
   std::map<std::string, u64> loop_caps;  // buffer capacities the device loop needed, kept across runs
   u64 host_syncs = 0;             // host waits for the GPU (statistics)
   cudaStream_t capture_stream = nullptr;  // private stream the device loop's graph is captured on (created on first use)

@@ -825,6 +825,120 @@ __global__ void __launch_bounds__(256) k_pbwd_emit(const __grid_constant__ PStep
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused cross-product step (unit semiring, bitmap-only last step).  When both
+// probes of a two-probe arm are keyed by the delta row alone -- same
+// generation's sg(x,y) :- parent(a,x), sg(a,b), parent(b,y), where children(a)
+// and children(b) depend only on (a, b) -- a warp probes both views for 32
+// delta rows, scans the lanes' product counts |A| * |B|, and expands the
+// products in rounds of 32 (lane l takes output t; its row is found by a
+// binary search over the scanned counts, its pair (i, j) by one division),
+// setting each output's membership bit.  No binding words, no count pass.
+// Operands: word 0 the delta row, 1 the key matched in view A, 3 the key
+// matched in view B, 2 a constant.
+// ---------------------------------------------------------------------------
+LOB_DEV u64 reg_pick3(const RegOp& o, u64 wi, u64 wa, u64 wb) {
+  if (o.word == 2) return (u64)o.cval;
+  const u64 w = o.word == 0 ? wi : (o.word == 1 ? wa : wb);
+  return (w >> o.shift) & o.mask;
+}
+
+// match range of view B for input word wi (B's prefix operands read wi only)
+LOB_DEV u32 probe_b(const PStep& B, u64 wi, u32& lo) {
+  u64 pv = 0;
+  lo = 0;
+  for (int q = 0; q < B.n_prefix; q++) {
+    const u64 x = pick(B.prefix[q].op, wi, 0);
+    if (B.prefix[q].limit_bits < 64 && (x >> B.prefix[q].limit_bits)) return 0;
+    pv |= x << B.prefix[q].shift;
+  }
+  u64 l, h;
+  if (B.index_mode == INDEX_DENSE) {
+    l = B.dense_offs[pv];
+    h = B.dense_offs[pv + 1];
+  } else if (B.whole_view) {
+    l = 0;
+    h = B.v_n;
+  } else {
+    const u64 klo = pv << B.rest_shift;
+    const u64 khi = klo + (1ull << B.rest_shift);
+    l = lower_bound_w(B.v_keys, B.v_key64, B.v_n, klo);
+    h = khi < klo ? B.v_n : lower_bound_w(B.v_keys, B.v_key64, B.v_n, khi);
+  }
+  lo = (u32)l;
+  return (u32)(h - l);
+}
+
+template <int NOUT, int NCHKA, int NCHKB>
+__global__ void __launch_bounds__(256) k_pwarp_cross(const __grid_constant__ PStep A, const __grid_constant__ PStep B,
+                                                     unsigned long long* emitted) {
+  RegOp out_op[NOUT];
+  u32 out_sh[NOUT];
+#pragma unroll
+  for (int q = 0; q < NOUT; q++) {
+    out_op[q] = reg_op(B.out[q].op);
+    out_sh[q] = B.out[q].shift;
+  }
+  RegOp aa[NCHKA > 0 ? NCHKA : 1], ab[NCHKA > 0 ? NCHKA : 1], ba[NCHKB > 0 ? NCHKB : 1], bb[NCHKB > 0 ? NCHKB : 1];
+  bool aeq[NCHKA > 0 ? NCHKA : 1], beq[NCHKB > 0 ? NCHKB : 1];
+#pragma unroll
+  for (int q = 0; q < NCHKA; q++) {
+    aa[q] = reg_op(A.checks[q].a);
+    ab[q] = reg_op(A.checks[q].b);
+    aeq[q] = A.checks[q].eq != 0;
+  }
+#pragma unroll
+  for (int q = 0; q < NCHKB; q++) {
+    ba[q] = reg_op(B.checks[q].a);
+    bb[q] = reg_op(B.checks[q].b);
+    beq[q] = B.checks[q].eq != 0;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u64 nwarps = (u64)gridDim.x * (blockDim.x / 32);
+  u64 mine = 0;
+  for (u64 g = (u64)blockIdx.x * (blockDim.x / 32) + warp; g * 32 < A.n_in; g += nwarps) {
+    u64 wi;
+    u32 loa, lob = 0, cb = 0;
+    const u32 ca = probe_row(A, g * 32 + lane, wi, loa);
+    if (ca) cb = probe_b(B, wi, lob);
+    const u64 c = (u64)ca * cb;
+    const u64 inc = warp_inclusive_sum(c);
+    const u64 ex = inc - c;
+    const u64 tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    if (!tot) continue;
+    mine += tot;
+    for (u64 t0 = 0; t0 < tot; t0 += 32) {
+      const u64 t = t0 + lane;
+      int src = 0;
+#pragma unroll
+      for (int step = 16; step; step >>= 1) {
+        const u64 e = __shfl_sync(0xFFFFFFFFu, ex, src + step);
+        if (e <= t) src += step;
+      }
+      const u64 wr = __shfl_sync(0xFFFFFFFFu, wi, src);
+      const u32 la = __shfl_sync(0xFFFFFFFFu, loa, src);
+      const u32 lb = __shfl_sync(0xFFFFFFFFu, lob, src);
+      const u32 nb = __shfl_sync(0xFFFFFFFFu, cb, src);
+      const u64 er = __shfl_sync(0xFFFFFFFFu, ex, src);
+      if (t >= tot) continue;
+      const u32 u = (u32)(t - er);
+      const u32 i = u / nb, j = u - i * nb;
+      const u64 wa = load_word(A.v_keys, A.v_key64, (u64)la + i);
+      const u64 wb = load_word(B.v_keys, B.v_key64, (u64)lb + j);
+      bool ok = true;
+#pragma unroll
+      for (int q = 0; q < NCHKA; q++) ok = ok && ((reg_pick3(aa[q], wr, wa, 0) == reg_pick3(ab[q], wr, wa, 0)) == aeq[q]);
+#pragma unroll
+      for (int q = 0; q < NCHKB; q++) ok = ok && ((reg_pick3(ba[q], wr, wa, wb) == reg_pick3(bb[q], wr, wa, wb)) == beq[q]);
+      u64 w = 0;
+#pragma unroll
+      for (int q = 0; q < NOUT; q++) w |= reg_pick3(out_op[q], wr, wa, wb) << out_sh[q];
+      if (ok) atomicOr(B.bitmap + (w >> 5), 1u << (u32)(w & 31u));
+    }
+  }
+  if (lane == 0 && mine) atomicAdd(emitted, (unsigned long long)mine);
+}
+
 unsigned grid_n(u64 n) {
   u64 b = (n + 255) / 256;
   if (b > 152ull * 16) b = 152ull * 16;
@@ -945,6 +1059,27 @@ bool pjoin_backward_supported(const PStep& P) { return P.n_out >= 1 && P.n_out <
 void pjoin_project(int sem, const PStep& P, cudaStream_t st) {
   ProfScope ps("project", P.n_in * (row_bytes(sem, P.in_w64, P.in_packed) + row_bytes(sem, P.out_w64, false)), st);
   if (P.n_in) by_sem_p<PProjL>(sem, P, st);
+}
+
+bool pjoin_cross_supported(const PStep& A, const PStep& B) {
+  return A.n_checks <= 1 && B.n_checks <= 1 && B.n_out >= 1 && B.n_out <= 4;
+}
+
+void pjoin_warp_cross_bitmap(const PStep& A, const PStep& B, u64* emitted_dev, cudaStream_t st) {
+  // the outputs' bytes (two matched keys and a bitmap word each) are added by
+  // the caller once their number is known
+  ProfScope ps("join_emit", A.n_in * (A.in_w64 ? 8.0 : 4.0), st);
+  if (!A.n_in) return;
+  auto* em = reinterpret_cast<unsigned long long*>(emitted_dev);
+  const unsigned g = grid_n(A.n_in);
+  const int no = B.n_out, ca = A.n_checks, cb = B.n_checks;
+#define LOB_CROSS(NO, CA, CB) \
+  if (no == NO && ca == CA && cb == CB) { k_pwarp_cross<NO, CA, CB><<<g, 256, 0, st>>>(A, B, em); return; }
+  LOB_CROSS(1, 0, 0) LOB_CROSS(2, 0, 0) LOB_CROSS(3, 0, 0) LOB_CROSS(4, 0, 0)
+  LOB_CROSS(1, 1, 0) LOB_CROSS(2, 1, 0) LOB_CROSS(3, 1, 0) LOB_CROSS(4, 1, 0)
+  LOB_CROSS(1, 0, 1) LOB_CROSS(2, 0, 1) LOB_CROSS(3, 0, 1) LOB_CROSS(4, 0, 1)
+  LOB_CROSS(1, 1, 1) LOB_CROSS(2, 1, 1) LOB_CROSS(3, 1, 1) LOB_CROSS(4, 1, 1)
+#undef LOB_CROSS
 }
 
 bool pjoin_warp_supported(int sem, const PStep& P) {

@@ -114,6 +114,13 @@ bool pjoin_backward_supported(const PStep& P);  // the emission has a kernel for
 // pjoin_warp_bitmap: last step, only sets the bits of P.bitmap and adds the
 // step's outputs to *emitted_dev.
 bool pjoin_warp_supported(int sem, const PStep& P);
+// Fused cross-product last step (see pjoin.cu): A = the first probe's step
+// (input rows, probe of view A, its checks on words 0 / 1), B = the second
+// probe keyed by the input word alone (its prefix on word 0, its checks and
+// the head fields on words 0 / 1 / 3, the bitmap).  Sets membership bits and
+// adds the outputs to *emitted_dev.
+bool pjoin_cross_supported(const PStep& A, const PStep& B);
+void pjoin_warp_cross_bitmap(const PStep& A, const PStep& B, u64* emitted_dev, cudaStream_t st);
 u64 pjoin_warp_blocks(u64 n_in);
 void pjoin_warp_count(const PStep& P, u64* blk_cnt, cudaStream_t st);
 void pjoin_warp_emit(const PStep& P, u64 total, const u64* blk_off, cudaStream_t st);

@@ -563,3 +563,21 @@ def test_device_loop_takes_over_after_a_recorded_run():
     assert stats[0]["device_iterations"] == 0 and stats[1]["device_iterations"] == stats[1]["iterations"] - 1
     assert stats[1]["graph_launches"] == 1
     assert stats[1]["host_syncs"] < stats[0]["host_syncs"] / 5
+
+
+@pytest.mark.parametrize("cross", [1, 0])
+def test_cross_product_step(cross):
+    """Same generation, whose recursive rule probes parent twice with keys from
+    the delta row alone: the fused cross-product step (children(a) x
+    children(b) straight into the membership bitmap) and the two-step
+    pipeline, against the oracle and the depth closed form; also on a
+    batched (sample-id) instance."""
+    from tests import pins
+    parent, child, depth = W.random_tree(5000, seed_index=31)
+    opts = {"cross_join": cross, "bitmap_delta": 2}
+    st, _ = compare(W.SG_PROGRAM, {"parent": ((parent, child),)}, options=opts)
+    assert st["derived"] == pins.same_generation_closed_form(depth)
+    p2, c2, _ = W.random_tree(800, seed_index=32)
+    samples = np.concatenate([np.zeros(len(parent), np.uint32), np.ones(len(p2), np.uint32)])
+    compare(W.SG_PROGRAM, {"parent": ((np.concatenate([parent, p2]), np.concatenate([child, c2])), None, samples)},
+            options=opts)
