@@ -15,6 +15,10 @@ Parity status per function (pins are in ``tests/test_oracle_pins.py``):
   * add-mult-prob / diff-add-mult -- pinned (layered DP, lattice-path closed form, trees)
   * forward-mode gradients        -- pinned (FP64 central finite differences)
   * batching by sample id         -- pinned (per-sample runs)
+  * top-1-proofs / diff-top-1     -- pinned (max-product paths by Dijkstra, the
+                                     paper's printed proof, union of shared
+                                     facts, brute-force two-hop maxima, the cap,
+                                     finite differences)
 """
 from __future__ import annotations
 
@@ -36,7 +40,8 @@ _LIB = os.path.join(_HERE, "liboracle.so" if _MUTANT == 0 else f"liboracle_mutan
 _lock = threading.Lock()
 _lib = None
 
-SEMIRINGS = {"unit": 0, "max_min": 1, "add_mult": 2, "diff_max_min": 3, "diff_add_mult": 4}
+SEMIRINGS = {"unit": 0, "max_min": 1, "add_mult": 2, "diff_max_min": 3, "diff_add_mult": 4,
+             "top1_proofs": 5, "diff_top1_proofs": 6}
 
 
 def build(force: bool = False) -> str:
@@ -70,6 +75,11 @@ def _load():
             lib.orc_read_ids.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p]
             lib.orc_vjp.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p, P(ctypes.c_void_p)]
             lib.orc_free.argtypes = [ctypes.c_void_p]
+            lib.orc_set_proof_cap.argtypes = [ctypes.c_uint32]
+            lib.orc_ties.argtypes = [ctypes.c_void_p]
+            lib.orc_ties.restype = ctypes.c_uint64
+            lib.orc_read_proofs.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p]
+            lib.orc_read_proofs.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -123,6 +133,23 @@ class Result:
         _load().orc_read_ids(self._h, name.encode(), out.ctypes.data)
         return out
 
+    @property
+    def ties(self) -> int:
+        """top-1-proofs: how often (+) met two different, equally likely proofs."""
+        return int(_load().orc_ties(self._h))
+
+    def proofs(self, name: str) -> list:
+        """top-1-proofs: per fact of ``relation(name)`` (same order) its proof,
+        an ascending array of input-fact ids (global row index over the inputs
+        in load order)."""
+        lib = _load()
+        n = lib.orc_size(self._h, name.encode())
+        total = lib.orc_read_proofs(self._h, name.encode(), None, None)
+        lens = np.zeros(max(n, 0), np.uint32)
+        ids = np.zeros(max(total, 0), np.uint32)
+        lib.orc_read_proofs(self._h, name.encode(), lens.ctypes.data, ids.ctypes.data)
+        return np.split(ids, np.cumsum(lens.astype(np.int64))[:-1]) if n > 0 else []
+
     def vjp(self, grads: dict) -> dict:
         """grads: relation -> upstream gradient aligned with ``relation(name)``.
         Returns input relation -> gradient aligned with its loaded rows."""
@@ -137,8 +164,9 @@ class Result:
         return outs
 
 
-def run(program: str, inputs: dict, semiring="unit", max_iters: int = 100000) -> Result:
-    """Run the naive fixpoint.
+def run(program: str, inputs: dict, semiring="unit", max_iters: int = 100000, proof_cap: int = 300) -> Result:
+    """Run the naive fixpoint.  ``proof_cap`` bounds the proofs of the
+    top-1-proofs semirings (a longer union is an error).
 
     inputs: name -> (cols, tags, samples) with cols an (arity, n) array (or a
     sequence of n-long columns), tags a length-n float array or None (tag 1,
@@ -176,6 +204,7 @@ def run(program: str, inputs: dict, semiring="unit", max_iters: int = 100000) ->
     c_tags = (ctypes.c_void_p * k)(*tag_ptrs)
     c_smp = (ctypes.c_void_p * k)(*smp_ptrs)
     h = ctypes.c_void_p()
+    lib.orc_set_proof_cap(int(proof_cap))
     rc = lib.orc_run(program.encode(), sr, k, c_names, c_ar, c_n, c_cols, c_tags, c_smp, max_iters,
                      ctypes.byref(h))
     if rc != 0:

@@ -33,6 +33,23 @@
 //   4 diff-add-mult  add-mult-prob carried with a forward-mode sparse gradient
 //                    (dual number): d(a+b) = da + db, zero when a + b > 1;
 //                    d(a*b) = a db + b da
+//   5 top-1-proofs   (Sec. 5.3 "Limitations"; Sec. 3.4) a tag is one proof: the
+//                    set of input facts of one derivation, at most `cap` of them
+//                    (300 by default, the paper's limit); its probability is the
+//                    product of its facts' probabilities.  (x) = union of the two
+//                    proofs (a fact used twice counts once); (+) keeps the more
+//                    likely proof.  Facts loaded without a probability have the
+//                    empty proof (probability 1).  A union longer than the cap
+//                    is an error.
+//   6 diff-top-1-proofs  top-1-proofs with d P / d p_i = product of the
+//                    proof's other facts' probabilities, for each fact i in it
+//
+// top-1-proofs details.  The probability of a proof is the product, in FP64,
+// of its facts' probabilities in ascending input-fact id order, rounded once to
+// f32 (the precision of every tag); (+) compares these f32 values.  When two
+// different proofs of one key are equally likely the oracle keeps the one whose
+// sorted id list is lexicographically smaller and counts the tie (orc_ties):
+// the engine may keep either, so parity is checked on instances without ties.
 //
 // Batched inputs (Sec. 4.3): facts carry a sample id and samples never join; the
 // oracle states that directly by running the fixpoint once per sample.
@@ -66,15 +83,29 @@ constexpr uint32_t kNoId = 0xFFFFFFFFu;
 using Tuple = std::array<uint32_t, kMaxArity>;
 using Dual = std::map<uint32_t, double>;  // input-fact id -> partial derivative
 
-enum Semiring { UNIT = 0, MAX_MIN = 1, ADD_MULT = 2, DIFF_MAX_MIN = 3, DIFF_ADD_MULT = 4 };
+enum Semiring { UNIT = 0, MAX_MIN = 1, ADD_MULT = 2, DIFF_MAX_MIN = 3, DIFF_ADD_MULT = 4, TOP1 = 5, DIFF_TOP1 = 6 };
+bool is_top1(int sr) { return sr == TOP1 || sr == DIFF_TOP1; }
 
 struct Tag {
   double v = 1.0;
   uint32_t id = kNoId;  // diff-max-min: the input fact that bounds v
   Dual d;               // diff-add-mult: d v / d p
+  std::vector<uint32_t> proof;  // top-1-proofs: ascending input-fact ids
 };
 
 std::string g_err;
+// top-1-proofs state of the current run
+std::vector<double> g_prob;  // input-fact id -> probability
+uint32_t g_proof_cap = 300;
+bool g_proof_overflow = false;
+uint64_t g_ties = 0;
+
+// probability of a proof: FP64 product in ascending id order, rounded to f32
+double proof_prob(const std::vector<uint32_t>& proof) {
+  double p = 1.0;
+  for (uint32_t id : proof) p *= g_prob[id];
+  return (double)(float)p;
+}
 
 // ---------------------------------------------------------------------------
 // program text
@@ -239,8 +270,34 @@ Tag otimes(int sr, const Tag& a, const Tag& b) {
       for (auto& kv : b.d) r.d[kv.first] += a.v * kv.second;
 #endif
       break;
+    case TOP1:
+    case DIFF_TOP1:
+#if ORACLE_MUTANT == 13  // mutant: the union keeps a fact used by both proofs twice
+      std::merge(a.proof.begin(), a.proof.end(), b.proof.begin(), b.proof.end(), std::back_inserter(r.proof));
+#else
+      std::set_union(a.proof.begin(), a.proof.end(), b.proof.begin(), b.proof.end(), std::back_inserter(r.proof));
+#endif
+      if (r.proof.size() > g_proof_cap) {
+        g_proof_overflow = true;
+        r.proof.resize(g_proof_cap);
+      }
+      r.v = proof_prob(r.proof);
+      break;
   }
   return r;
+}
+
+// top-1-proofs (+): the more likely proof; equally likely different proofs are
+// a tie, resolved to the lexicographically smaller id list
+bool top1_greater(const Tag& a, const Tag& b) {
+#if ORACLE_MUTANT == 14  // mutant: (+) keeps the less likely proof
+  if (a.v != b.v) return a.v < b.v;
+#else
+  if (a.v != b.v) return a.v > b.v;
+#endif
+  if (a.proof == b.proof) return false;
+  g_ties++;
+  return a.proof < b.proof;
 }
 
 // Accumulator for the (+) over the groundings of one head key.  For the
@@ -272,6 +329,10 @@ void acc_add(int sr, Acc& acc, const Tag& g) {
     case DIFF_MAX_MIN:
       if (dmm_greater(g, acc.t)) acc.t = g;
       break;
+    case TOP1:
+    case DIFF_TOP1:
+      if (top1_greater(g, acc.t)) acc.t = g;
+      break;
   }
 }
 
@@ -295,6 +356,7 @@ Tag acc_value(int sr, const Acc& acc) {
 
 bool tag_equal(int sr, const Tag& a, const Tag& b) {
   if (sr == DIFF_MAX_MIN) return a.v == b.v && a.id == b.id;
+  if (is_top1(sr)) return a.v == b.v && a.proof == b.proof;
   return a.v == b.v;
 }
 
@@ -467,6 +529,8 @@ struct orc_result {
   // relation -> sample -> sorted facts
   std::map<std::string, uint32_t> arity;
   std::map<std::string, std::map<uint32_t, Relation>> out;
+  std::vector<double> prob;  // top-1-proofs: input-fact id -> probability
+  uint64_t ties = 0;
 };
 
 extern "C" {
@@ -477,7 +541,7 @@ int orc_run(const char* program, int semiring, int n_inputs, const char* const* 
             const uint64_t* nrows, const uint32_t* const* cols, const double* const* tags,
             const uint32_t* const* samples, uint32_t max_iters, orc_result** result) {
   g_err.clear();
-  if (!program || !result || semiring < 0 || semiring > 4 || n_inputs < 0) {
+  if (!program || !result || semiring < 0 || semiring > 6 || n_inputs < 0) {
     g_err = "bad argument";
     return -3;
   }
@@ -496,6 +560,12 @@ int orc_run(const char* program, int semiring, int n_inputs, const char* const* 
   // split loaded facts by sample; duplicates merged with (+)
   std::map<uint32_t, std::map<std::string, std::map<Tuple, Acc>>> loaded;
   uint64_t base = 0;
+  g_prob.clear();
+  g_proof_overflow = false;
+  g_ties = 0;
+  for (int k = 0; k < n_inputs; k++) base += nrows[k];
+  if (is_top1(semiring)) g_prob.assign(base, 1.0);
+  base = 0;
   for (int k = 0; k < n_inputs; k++) {
     if (arities[k] < 1 || arities[k] > (uint32_t)kMaxArity) {
       delete res;
@@ -518,6 +588,11 @@ int orc_run(const char* program, int semiring, int n_inputs, const char* const* 
       const bool differentiable = tags && tags[k];
       if (semiring == DIFF_MAX_MIN && differentiable) g.id = (uint32_t)(base + r);
       if (semiring == DIFF_ADD_MULT && differentiable) g.d[(uint32_t)(base + r)] = 1.0;
+      if (is_top1(semiring) && differentiable) {
+        g_prob[base + r] = g.v;
+        g.proof.push_back((uint32_t)(base + r));
+        g.v = proof_prob(g.proof);
+      }
       acc_add(semiring, loaded[s][names[k]][t], g);
     }
     base += nrows[k];
@@ -529,6 +604,11 @@ int orc_run(const char* program, int semiring, int n_inputs, const char* const* 
     for (auto& rel : smp.second)
       for (auto& kv : rel.second) e.db[rel.first][kv.first] = acc_value(semiring, kv.second);
     int rc = e.run(max_iters);
+    if (g_proof_overflow) {
+      delete res;
+      g_err = "a proof is longer than the proof cap";
+      return -5;
+    }
     if (rc != 0) {
       delete res;
       g_err = "max_iters reached";
@@ -538,11 +618,38 @@ int orc_run(const char* program, int semiring, int n_inputs, const char* const* 
     for (auto& rel : e.db) res->out[rel.first][smp.first] = std::move(rel.second);
   }
   res->iterations = max_it;
+  res->prob = g_prob;
+  res->ties = g_ties;
   *result = res;
   return 0;
 }
 
 int orc_iterations(const orc_result* r) { return r ? r->iterations : -1; }
+
+// top-1-proofs: the proof cap of later runs (default 300)
+void orc_set_proof_cap(uint32_t cap) { g_proof_cap = cap; }
+
+// top-1-proofs: equally likely different proofs met by (+) during the run
+uint64_t orc_ties(const orc_result* r) { return r ? r->ties : 0; }
+
+// top-1-proofs: the proofs of `rel` in read order, as per-fact lengths and the
+// concatenated ascending input-fact ids; returns the total number of ids (call
+// with null pointers to size the buffers).
+int64_t orc_read_proofs(const orc_result* r, const char* rel, uint32_t* lens, uint32_t* ids) {
+  auto it = r->out.find(rel);
+  if (it == r->out.end()) return 0;
+  int64_t i = 0, w = 0;
+  for (auto& s : it->second)
+    for (auto& kv : s.second) {
+      if (lens) lens[i] = (uint32_t)kv.second.proof.size();
+      for (uint32_t id : kv.second.proof) {
+        if (ids) ids[w] = id;
+        w++;
+      }
+      i++;
+    }
+  return w;
+}
 
 int64_t orc_size(const orc_result* r, const char* rel) {
   auto it = r->out.find(rel);
@@ -588,7 +695,7 @@ int orc_read_ids(const orc_result* r, const char* rel, uint32_t* ids) {
 // Vector-Jacobian product: grad_in[k][row] += sum_o grad_out[o] * d tag_o / d p_(k,row)
 // with o running over `rel` in read order.  Only for the diff semirings.
 int orc_vjp(const orc_result* r, const char* rel, const double* grad_out, double* const* grad_in) {
-  if (r->semiring != DIFF_MAX_MIN && r->semiring != DIFF_ADD_MULT) return -4;
+  if (r->semiring != DIFF_MAX_MIN && r->semiring != DIFF_ADD_MULT && r->semiring != DIFF_TOP1) return -4;
   auto it = r->out.find(rel);
   if (it == r->out.end()) return 0;
   auto deposit = [&](uint32_t id, double g) {
@@ -606,6 +713,15 @@ int orc_vjp(const orc_result* r, const char* rel, const double* grad_out, double
       double g = grad_out[i++];
       if (r->semiring == DIFF_MAX_MIN) {
         if (kv.second.id != kNoId) deposit(kv.second.id, g);
+      } else if (r->semiring == DIFF_TOP1) {
+        // d prod_j p_j / d p_i = product of the other facts' probabilities
+        const std::vector<uint32_t>& P = kv.second.proof;
+        for (size_t a = 0; a < P.size(); a++) {
+          double others = 1.0;
+          for (size_t b = 0; b < P.size(); b++)
+            if (b != a) others *= r->prob[P[b]];
+          deposit(P[a], g * others);
+        }
       } else {
         for (auto& d : kv.second.d) deposit(d.first, g * d.second);
       }

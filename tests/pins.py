@@ -286,3 +286,46 @@ def possible_worlds_maxmin(facts, probs, closure):
             if k not in best or val > best[k]:
                 best[k] = val
     return {k: (v, -nid) for k, (v, nid) in best.items()}
+
+
+def max_product_path(src, dst, p, source):
+    """Most likely path from `source` to every reachable node (Dijkstra on the
+    product of edge probabilities, all in [0, 1], so extending a path never
+    makes it likelier): node -> (probability, edge indices of the path)."""
+    adj = defaultdict(list)
+    for e, (a, b, w) in enumerate(zip(src.tolist(), dst.tolist(), np.asarray(p, np.float64).tolist())):
+        adj[a].append((b, w, e))
+    best = {source: (1.0, [])}
+    heap = [(-1.0, source)]
+    done = set()
+    while heap:
+        negv, v = heapq.heappop(heap)
+        if v in done:
+            continue
+        done.add(v)
+        pv, path = best[v]
+        for w, pw, e in adj[v]:
+            c = pv * pw
+            if w not in done and c > best.get(w, (-1.0, None))[0]:
+                best[w] = (c, path + [e])
+                heapq.heappush(heap, (-c, w))
+    return best
+
+
+def proof_is_path(src, dst, edge_ids, source, target):
+    """The edges `edge_ids` form a simple path from source to target (in some order)."""
+    out = {}
+    for e in edge_ids:
+        a = int(src[e])
+        if a in out:
+            return False
+        out[a] = int(dst[e])
+    v, seen = source, {source}
+    for _ in range(len(edge_ids)):
+        if v not in out:
+            return False
+        v = out[v]
+        if v in seen:
+            return False
+        seen.add(v)
+    return v == target

@@ -23,6 +23,8 @@ MUTANTS = {
     10: "sample ids ignored (samples join)",
     11: "first two head columns transposed",
     12: "diff-max-min (x) keeps the greater operand",
+    13: "top-1-proofs union keeps a shared fact twice",
+    14: "top-1-proofs (+) keeps the less likely proof",
 }
 
 

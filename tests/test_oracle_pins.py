@@ -406,3 +406,151 @@ def test_kinship_maxmin_possible_worlds():
     for k, (v, i) in want.items():
         assert got[k][0] == v, k
         assert got[k][1] == i, k
+
+
+# ----------------------------------------------------------------------------
+# top-1-proofs (Sec. 5.3 "Limitations"; Sec. 3.4): one proof per fact, (x) =
+# union of proofs, (+) = the more likely proof
+# ----------------------------------------------------------------------------
+
+def _f32(x):
+    return float(np.float32(x))
+
+
+@pytest.mark.parametrize("g", range(3))
+def test_top1_reach_is_the_most_likely_path(g):
+    """On reachability every kept proof is a simple path, so the tag of reach(y)
+    is the probability of the most likely path (Dijkstra on products)."""
+    src, dst, p = small_graphs()[g]
+    inputs = {"edge": ((src, dst), p), "start": ((np.array([0], np.uint32),),)}
+    best = pins.max_product_path(src, dst, p, 0)
+    for sr in ("top1_proofs", "diff_top1_proofs"):
+        r = oracle.run(W.REACH_PROGRAM, inputs, sr)
+        assert r.ties == 0
+        rel = r.relation("reach")
+        proofs = r.proofs("reach")
+        assert set(rel.cols[0].tolist()) == set(best)
+        for y, t, pr in zip(rel.cols[0].tolist(), rel.tags.tolist(), proofs):
+            assert t == pytest.approx(best[y][0], rel=1e-6)
+            assert sorted(pr.tolist()) == sorted(best[y][1])  # edge rows come first in load order
+            assert pins.proof_is_path(src, dst, pr.tolist(), 0, y)
+            assert t == _f32(math.prod(np.asarray(p, np.float64)[pr].tolist()))
+
+
+def test_top1_grid_paths_against_dijkstra():
+    g = W.grid_reach_instance(10, sub=3)
+    src, dst, p = g["edge"]
+    r = oracle.run(W.REACH_PROGRAM, {"edge": ((src, dst), p), "start": (g["start"],)}, "top1_proofs")
+    best = pins.max_product_path(src, dst, p, 0)
+    rel = r.relation("reach")
+    proofs = r.proofs("reach")
+    assert len(rel.cols[0]) == len(best) == 100
+    for y, t, pr in zip(rel.cols[0].tolist(), rel.tags.tolist(), proofs):
+        assert t == pytest.approx(best[y][0], rel=1e-6)
+        assert pins.proof_is_path(src, dst, pr.tolist(), 0, y)
+
+
+def test_top1_a_fact_used_twice_counts_once():
+    """(x) is the union of proofs: a(x), a(x) has the probability of a(x)."""
+    pa = np.array([0.5, 0.25, 0.8])
+    pb = np.array([0.4, 0.9, 0.3])
+    x = np.array([0, 1, 2], np.uint32)
+    prog = "q(x) :- a(x), a(x).\nr(x) :- a(x), b(x), a(x).\n"
+    r = oracle.run(prog, {"a": ((x,), pa), "b": ((x,), pb)}, "top1_proofs")
+    q, rr = r.relation("q"), r.relation("r")
+    assert q.tags.tolist() == [_f32(v) for v in pa]
+    assert [p.tolist() for p in r.proofs("q")] == [[0], [1], [2]]
+    assert rr.tags.tolist() == [_f32(a * b) for a, b in zip(pa, pb)]
+    assert [p.tolist() for p in r.proofs("r")] == [[0, 3], [1, 4], [2, 5]]
+
+
+def test_top1_two_hop_is_the_best_middle_vertex():
+    """t(x,z) :- e(x,y), f(y,z): the most likely grounding over y (brute force)."""
+    s = W.stream(4242)
+    n, m = 6, 30
+    e = (s.below(m, n), s.below(m, n))
+    f = (s.below(m, n), s.below(m, n))
+    pe, pf = s.prob(m).astype(np.float64), s.prob(m).astype(np.float64)
+    r = oracle.run("t(x,z) :- e(x,y), f(y,z).\n", {"e": (e, pe), "f": (f, pf)}, "top1_proofs")
+    # distinct input rows (duplicates keep the likelier row)
+    def best_rows(cols, p):
+        d = {}
+        for i, k in enumerate(zip(*[c.tolist() for c in cols])):
+            if k not in d or p[i] > p[d[k]]:
+                d[k] = i
+        return d
+    de, df = best_rows(e, pe), best_rows(f, pf)
+    want = {}
+    for (x, y), i in de.items():
+        for (y2, z), j in df.items():
+            if y2 != y:
+                continue
+            v = _f32(pe[i] * pf[j])
+            if (x, z) not in want or v > want[(x, z)][0]:
+                want[(x, z)] = (v, [i, m + j])
+    assert r.ties == 0
+    rel = r.relation("t")
+    got = {k: (t, pr.tolist()) for k, t, pr in zip(map(tuple, rel.cols.T.tolist()), rel.tags.tolist(), r.proofs("t"))}
+    assert got == want
+
+
+def test_top1_pathfinder_example_proof_from_the_paper():
+    """The proof of connected(1,5) is the chain edge(1,2), ..., edge(4,5) that the
+    paper's Sec. 2 example prints; the endpoint facts carry no probability and
+    join the proof as the empty conjunction."""
+    from tests.golden.load import pathfinder_example
+    program, inputs = pathfinder_example()
+    chain = [0.9, 0.8, 0.95, 0.85]
+    r = oracle.run(program, inputs, "top1_proofs")
+    conn = r.relation("connected")
+    assert rel_set(conn) == {(1, 5)}
+    assert [p.tolist() for p in r.proofs("connected")] == [[1, 2, 3, 4]]  # edge rows 1..4 of the fixture
+    assert conn.tags.tolist() == [_f32(math.prod(chain))]
+    path = r.relation("path")
+    tag = dict(zip(map(tuple, path.cols.T.tolist()), path.tags.tolist()))
+    assert tag[(0, 1)] == _f32(0.97)
+
+
+def test_top1_proof_cap_is_enforced():
+    n = 9
+    a, b = W.ktree_chain(n)
+    p = np.full(n - 1, 0.5)
+    inputs = {"edge": ((a, b), p), "start": ((np.array([0], np.uint32),),)}
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.run(W.REACH_PROGRAM, inputs, "top1_proofs", proof_cap=5)
+    assert ei.value.code == -5
+    r = oracle.run(W.REACH_PROGRAM, inputs, "top1_proofs", proof_cap=8)
+    pr = r.proofs("reach")
+    assert [len(x) for x in pr] == list(range(n))
+    assert r.relation("reach").tags[-1] == 0.5 ** 8
+
+
+def test_top1_proofs_are_valid_derivations_on_kinship():
+    """Every kept proof derives its fact on its own (the unit fixpoint over the
+    proof's facts plus the facts without a probability contains it), and the tag
+    is the product of the proof's probabilities."""
+    n, rr, a, b, p = W.kinship_instance(W.stream(143))
+    comp = W.composition_table()
+    inputs = {"fact": ((rr, a, b), p), "comp": (comp,)}
+    r = oracle.run(W.KIN_PROGRAM, inputs, "top1_proofs")
+    kin = r.relation("kin")
+    proofs = r.proofs("kin")
+    s = W.stream(99)
+    picks = s.below(min(40, len(proofs)), len(proofs)).tolist()
+    for i in picks:
+        pr = proofs[i]
+        assert kin.tags[i] == _f32(math.prod(p.astype(np.float64)[pr].tolist()))
+        sub = {"fact": ((rr[pr], a[pr], b[pr]),), "comp": (comp,)}
+        got = rel_set(oracle.run(W.KIN_PROGRAM, sub, "unit").relation("kin"))
+        assert tuple(kin.cols[:, i].tolist()) in got
+
+
+def test_top1_gradient_matches_finite_differences():
+    src, dst, p = small_graphs()[2]
+    inputs = {"edge": ((src, dst), p), "start": ((np.array([0], np.uint32),),)}
+    n_out = oracle.run(W.REACH_PROGRAM, inputs, "top1_proofs").relation("reach").cols.shape[1]
+    gout = W.stream(56).normal(n_out)
+    # the tags are products rounded to f32: a wide step keeps the rounding
+    # error small, and a product is linear in each factor, so the central
+    # difference has no truncation error
+    _fd_check(W.REACH_PROGRAM, inputs, "reach", "diff_top1_proofs", gout, range(len(src)), h=1e-3)
