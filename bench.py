@@ -56,9 +56,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """dram bytes per launch for `kernel` from the committed ncu summary, or None
-    when the summary was taken on different kernel sources."""
+def ncu_traffic(kernel: str, outputs_per_launch: float):
+    """DRAM bytes per launch of `kernel` at the benchmark's size, from the
+    committed ncu summary: DRAM bytes per join output measured on the small
+    profile cases (one kernel, a few launches), times this workload's join
+    outputs per launch.  None when the summary was taken on other kernel sources."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -68,7 +70,9 @@ def ncu_traffic(kernel: str):
     if t.get("source_hash") != kernel_source_hash():
         return None
     k = t.get("kernels", {}).get(kernel)
-    return None if k is None else k.get("dram_bytes_per_launch_full_size")
+    if k is None or not outputs_per_launch:
+        return None
+    return k["dram_bytes_per_output"] * outputs_per_launch
 
 
 # ---------------------------------------------------------------------------
@@ -489,6 +493,8 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=1, help="extra steps with per-kernel CUDA-event timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched fwd+bwd measurement")
     ap.add_argument("--no-configs", action="store_true", help="skip the per-configuration throughput lines")
+    ap.add_argument("--no-pathfinder", action="store_true",
+                    help="skip the end-to-end training-step sweep over Pathfinder grid sides")
     ap.add_argument("--cpu-andersen", action="store_true",
                     help="also time the full-size Andersen sparse-matrix checker on the host (about two minutes)")
     ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
@@ -597,9 +603,10 @@ def main():
         per_launch_bytes = v["bytes"] / v["launches"]
         per_launch_s = v["ms"] / v["launches"] / 1e3
         ach = per_launch_bytes / per_launch_s / 1e9
+        outs = sum(cands.values()) / max(v["launches"], 1) if name == "join_emit" else 0
         roofline = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(ach / peak, 4), "peak_source": peak_kind,
-                    "algorithmic_bytes_per_launch": per_launch_bytes, "traffic": ncu_traffic(name)}
+                    "algorithmic_bytes_per_launch": per_launch_bytes, "traffic": ncu_traffic(name, outs)}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -638,6 +645,12 @@ def main():
     batched = None
     if not args.no_batched:
         batched = batched_fwd_bwd()
+    pathfinder = None
+    if not args.no_pathfinder:
+        from paper_2503_21937_gb300 import pathfinder as PF
+        pathfinder = {"metric": "training-step samples/s (CNN edge predictor -> batched diff-max-min fixpoint -> "
+                                "BCE -> backward -> Adam), synthetic Pathfinder-like grids",
+                      "by_side": PF.sweep()}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample()
@@ -650,7 +663,7 @@ def main():
                            "join_outputs": cands, "engine_options": args.option},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "kernels": kernels, "kernels_by_workload": by_workload, "configs": configs,
-                "batched": batched}
+                "batched": batched, "pathfinder": pathfinder}
         print(json.dumps(line))
     for e in engines.values():
         e.close()

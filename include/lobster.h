@@ -49,6 +49,16 @@ typedef struct lob_engine lob_engine;
 #define LOB_ADD_MULT 2       /* add-mult-prob: (+) = min(1, a+b), (x) = a*b on [0,1] */
 #define LOB_DIFF_MAX_MIN 3   /* differentiable max-min: gradient 1 to the bounding input fact */
 #define LOB_DIFF_ADD_MULT 4  /* differentiable add-mult: exact reverse-mode gradient */
+/* top-1-proofs (Sec. 5.3 "Limitations"): a tag is one proof, the set of input
+ * facts of one derivation (at most option "proof_cap" of them), with the
+ * product of their probabilities.  (x) = union of the proofs, (+) = the likelier
+ * proof; an input row loaded without a probability has the empty proof.  The
+ * product is taken in FP64 in ascending input-fact id order and rounded once to
+ * f32; (+) compares those f32 values, and a fact's proof is replaced only by a
+ * strictly likelier one.  Which of two equally likely proofs a key keeps is not
+ * fixed.  Proofs are read with lob_read_proofs. */
+#define LOB_TOP1_PROOFS 5
+#define LOB_DIFF_TOP1_PROOFS 6  /* gradient of each proof's product to the input facts in it */
 
 #define LOB_MEM_HOST 0
 #define LOB_MEM_DEVICE 1
@@ -74,6 +84,7 @@ typedef struct lob_stats {
   uint64_t host_syncs;      /* times the host waited for the GPU during the run */
   uint32_t device_iterations; /* iterations run by the device-driven loop (option "driver") */
   uint32_t graph_launches;  /* launches of that loop's graph (1 unless a buffer had to grow) */
+  uint64_t proof_words;     /* top-1-proofs: u32 words of the proof arena in use at the end */
 } lob_stats;
 
 /* Create an engine on the current CUDA device.  `alloc` may be NULL (stream-
@@ -137,6 +148,7 @@ typedef struct lob_tune_report {
   uint32_t trials;  /* fixpoint runs timed (warm-up excluded) */
   double first_ms;  /* median run time with the options in force when called */
   double best_ms;   /* median run time with the chosen options */
+  int32_t acc_dense, cross_join;
 } lob_tune_report;
 
 /* Autotuner for the loaded program (not part of the paper's method).  It picks
@@ -144,11 +156,16 @@ typedef struct lob_tune_report {
  * the fixpoint under candidate settings and timing each run on the engine's
  * stream (CUDA events).  The search is coordinate descent over these knobs:
  *   - packed_join: packed-word vs general join steps;
- *   - join_index: dense offset table vs binary search;
+ *   - join_index: dense offset table vs binary search vs hash table (the join
+ *     strategy: offset-table / hash probes vs sorted-merge search);
  *   - radix_bits: the sort's digit width;
+ *   - for the tagged semirings acc_dense (dense (+)-accumulation vs sorted
+ *     candidates);
  *   - for the unit semiring also warp_join (warp-balanced vs tile emission),
- *     bitmap_delta (bitmap read-out vs sorted candidates) and emit_filter
- *     (membership filter).
+ *     bitmap_delta (bitmap read-out vs sorted candidates), emit_filter
+ *     (membership filter) and cross_join (fused cross-product step).
+ * Tile sizes (emission, merge, unique, sort) are compile-time constants of the
+ * kernels and are not searched.
  * Each setting runs `repeats` times (0 = 1) and scores its median run time; a
  * change must win by 2 %.  All settings compute the same relations, so only
  * time decides.  The engine must be loaded and not yet run (LOB_E_STATE
@@ -170,6 +187,17 @@ int lob_relation_size(lob_engine* e, uint32_t rel, uint64_t* n);
 int lob_read_relation(lob_engine* e, uint32_t rel, uint32_t* cols, float* tags, uint32_t* sample_ids,
                       uint64_t capacity, uint64_t* n_out, int mem);
 
+/* The proofs of a top-1-proofs run (LOB_STATE otherwise): for fact i of `rel`
+ * in lob_read_relation order, lens[i] = the number of input facts in its proof
+ * and its ids follow those of facts 0..i-1 in `ids`, ascending.  The id of row
+ * q of relation k is q plus the rows loaded into relations 0..k-1 (declaration
+ * order).  lens holds lob_relation_size entries (or is NULL); ids holds
+ * id_capacity entries (or is NULL); *n_ids (may be NULL) receives the total id
+ * count.  When the ids exceed id_capacity nothing is written to ids and
+ * LOB_E_CAPACITY is returned.  `mem` says where lens and ids live. */
+int lob_read_proofs(lob_engine* e, uint32_t rel, uint32_t* lens, uint32_t* ids, uint64_t id_capacity, uint64_t* n_ids,
+                    int mem);
+
 /* Reverse-mode gradient after a LOB_DIFF_* run (Sec. 3.4: differentiable
  * versions of the probabilistic semirings).
  *   grad_tags   d loss / d tag for every fact of out_rel, in lob_read_relation order
@@ -177,7 +205,8 @@ int lob_read_relation(lob_engine* e, uint32_t rel, uint32_t* cols, float* tags, 
  *               relations); entry k is NULL or points to one float per loaded
  *               row of relation k, in load order; gradients are ADDED there.
  * diff-max-min: each output's gradient goes to the input row that bounds its
- * tag.  diff-add-mult: adjoints flow back through every recorded derivation
+ * tag.  diff-top-1-proofs: to every input row of its proof, times the product of
+ * the proof's other probabilities.  diff-add-mult: adjoints flow back through every recorded derivation
  * (recomputed per iteration), zero through a clamped (+).  May be called once
  * per output relation; LOB_E_STATE without a diff run. */
 int lob_backward(lob_engine* e, uint32_t out_rel, const float* grad_tags, float* const* grad_inputs, int mem);
@@ -187,7 +216,11 @@ int lob_reset(lob_engine* e);
 
 /* Engine options (key, value):
  *   "join_index"   0 dense offset table up to dense_bits, else binary
- *                  search; 1 dense up to 30 bits; 2 binary search  (default 0)
+ *                  search; 1 dense up to 30 bits; 2 binary search; 3 a hash
+ *                  table of the view's distinct join prefixes (open
+ *                  addressing, linear probing, each slot holding the
+ *                  prefix's first row and row count; 2 slots per row at
+ *                  most)                                             (default 0)
  *   "dense_bits"   largest join-prefix width, in bits, indexed densely (default 24)
  *   "radix_bits"   bits per radix-sort pass: 4, 6 or 8 (other values
  *                  in 4..11 select 8)                                (default 8)
@@ -237,6 +270,9 @@ int lob_reset(lob_engine* e);
  *   "loop_cap_floor" smallest row capacity the device-driven loop plans its
  *                  buffers with before they grow (256..2^24, default 65536;
  *                  small values exercise the regrowth path)
+ *   "proof_cap"    top-1-proofs: the most input facts a proof may hold; a
+ *                  union beyond it ends the run with LOB_E_CAPACITY
+ *                  (1 .. 2^20)                                       (default 300)
  *   "cross_join"   1: under LOB_UNIT, an arm with two probes keyed by the
  *                  delta row alone (same generation: children(a) x
  *                  children(b)) whose new facts only set bitmap bits runs

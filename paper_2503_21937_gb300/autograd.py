@@ -13,7 +13,7 @@ import torch
 
 from .lobster import Engine, relation_arities
 
-_DIFF = {"diff_max_min", "diff_add_mult"}
+_DIFF = {"diff_max_min", "diff_add_mult", "diff_top1_proofs"}
 
 # Idle engines per (program, relations, stream, device, input-size class).  An
 # engine is taken for one forward (+ backward) and returned afterwards, so a

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblobster.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["engine.cu", "rules.cu", "join.cu", "pjoin.cu", "sort.cu", "dedup.cu", "bitset.cu", "backward.cu", "noalloc.cu",
-           "driver.cu"]
+           "driver.cu", "top1.cu"]
 
 
 def nvcc() -> str:

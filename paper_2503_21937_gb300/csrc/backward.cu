@@ -374,6 +374,7 @@ void replay_arm(lob_engine& e, BwdState& S, const RulePlan& rp, const ArmPlan& A
     P.index_mode = I.mode;
     P.dense_offs = I.offs.as<u64>();
     P.dense_domain = I.domain;
+    P.hash_bits = I.hash_bits;
     fill_filters_b(R, SP.filters, P.filters, P.n_filters);
     B.v_prow = SP.view ? S.prow[R.body[SP.atom].rel][SP.view].as<u32>() : nullptr;
     e.ensure(e.cnt, P.n_in * 4);
@@ -514,6 +515,7 @@ bool replay_arm_packed(lob_engine& e, BwdState& S, const RulePlan& rp, const Arm
     const IndexSt& I = W.index[SP.prefix_len];
     P.index_mode = I.mode;
     P.dense_offs = I.offs.as<u64>();
+    P.hash_bits = I.hash_bits;
     const u64 n_blk = pjoin_loc_blocks(n_in);
     e.ensure(e.cnt, n_in * 4);
     e.ensure(e.lo, n_in * 4);
@@ -615,6 +617,19 @@ int backward_impl(lob_engine* e, u32 out_rel, const float* grad_tags, float* con
       k_dmm_scatter<<<grid_for_n(n_out), 256, 0, e->stream>>>(O.views[0].tags.as<u64>(), gdev, n_out, T);
       e->after_launch("max-min backward");
     }
+  } else if (e->semiring == LOB_DIFF_TOP1_PROOFS) {
+    // each output's probability is the product over its proof: its gradient
+    // goes to every input fact of the proof (top1.cu)
+    if (nrel > (size_t)kTop1GradRels) throw LobError(LOB_E_ARG, "more than 64 relations");
+    Top1GradTable T{};
+    T.n = (int)nrel;
+    for (size_t k = 0; k < nrel; k++) {
+      T.base[k] = e->rels[k].id_base;
+      T.count[k] = (u32)e->rels[k].n_in;
+      T.grad[k] = gin[k];
+    }
+    top1_grad_scatter(O.views[0].tags.as<u64>(), gdev, n_out, e->arena.as<u32>(), e->top1_prob.as<float>(), T, e->stream);
+    e->after_launch("top-1-proofs backward");
   } else {
     BwdState S;
     try {

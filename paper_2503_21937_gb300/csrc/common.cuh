@@ -71,7 +71,9 @@ LOB_DEV u64 invalid_of(int key64) { return key64 ? ~0ull : 0xFFFFFFFFull; }
 // semirings (Sec. 3.1 table; Sec. 3.4).  `Stored` is the tag kept with a fact;
 // `Cand` is the tag carried by candidates and join intermediates.
 // ---------------------------------------------------------------------------
-enum SemiringId { SR_UNIT = 0, SR_MAX_MIN = 1, SR_ADD_MULT = 2, SR_DIFF_MAX_MIN = 3, SR_DIFF_ADD_MULT = 4 };
+enum SemiringId {
+  SR_UNIT = 0, SR_MAX_MIN = 1, SR_ADD_MULT = 2, SR_DIFF_MAX_MIN = 3, SR_DIFF_ADD_MULT = 4, SR_TOP1 = 5, SR_DIFF_TOP1 = 6
+};
 
 struct SemUnit {
   typedef u32 Stored;
@@ -132,6 +134,74 @@ struct SemDiffMaxMin {
   LOB_DEV static Stored store(Cand c) { return c; }
   LOB_DEV static bool better(Stored a, Stored b) { return a > b; }
 };
+// top-1-proofs (Sec. 5.3 "Limitations"; Sec. 3.4): a tag is one proof, the
+// set of input facts of one derivation, kept in the engine's proof arena as
+// [length, ids ascending]; the tag packs (bits(P) << 32) | word offset of the
+// proof, where P is the proof's probability.  (+) keeps the likelier proof (u64
+// max: equally likely proofs go to the larger offset); a fact is improved only
+// when its probability grows.  (x) is the union of two proofs and needs the
+// arena, so the join kernels compute it with top1_union (no Sem::mul here).
+struct SemTop1 {
+  typedef u64 Stored;
+  typedef u64 Cand;
+  static constexpr bool kTags = true;
+  static constexpr bool kIdempotent = true;
+  LOB_DEV static Cand one() { return (u64)__float_as_uint(1.0f) << 32; }  // the empty proof, at offset 0
+  LOB_DEV static Cand from_stored(Stored s) { return s; }
+  LOB_DEV static Cand add(Cand a, Cand b) { return a > b ? a : b; }
+  LOB_DEV static Stored store(Cand c) { return c; }
+  LOB_DEV static bool better(Stored a, Stored b) { return (a >> 32) > (b >> 32); }
+};
+
+// The proof arena of a top-1-proofs run.  Word 0 is the empty proof; proofs
+// are appended by bump allocation; a union that does not fit leaves the tail
+// past `cap` (the host grows the arena and runs the step again).
+struct Top1Arena {
+  u32* words;
+  unsigned long long* tail;  // next free word
+  u64 cap;                   // words allocated (at most 2^32 - 1)
+  const float* prob;         // input-fact id -> probability
+  u32 proof_cap;             // longest proof allowed
+  u32* err;                  // bit 0: a union longer than proof_cap
+};
+
+// (x) of two top-1 tags: the union of their proofs, written to the arena, with
+// its probability = the FP64 product of its facts' probabilities in ascending
+// id order, rounded once to f32.
+LOB_DEV u64 top1_union(const Top1Arena& A, u64 a, u64 b) {
+  const u32 ra = (u32)a, rb = (u32)b;
+  const u32* pa = A.words + ra;
+  const u32* pb = A.words + rb;
+  const u32 la = pa[0], lb = pb[0];
+  if (la == 0 || ra == rb) return b;  // the empty proof is the identity; a proof with itself is itself
+  if (lb == 0) return a;
+  const u64 need = (u64)la + lb + 1;
+  const u64 at = atomicAdd(A.tail, (unsigned long long)need);
+  if (at + need > A.cap) return 0;
+  u32* out = A.words + at + 1;
+  u32 i = 0, j = 0, n = 0;
+  double p = 1.0;
+  while (i < la || j < lb) {
+    u32 x;
+    if (j >= lb) x = pa[1 + i++];
+    else if (i >= la) x = pb[1 + j++];
+    else {
+      const u32 xa = pa[1 + i], xb = pb[1 + j];
+      x = xa < xb ? xa : xb;
+      i += xa <= xb;
+      j += xb <= xa;
+    }
+    out[n++] = x;
+    p *= (double)A.prob[x];
+  }
+  if (n > A.proof_cap) {
+    atomicOr(A.err, 1u);
+    return 0;
+  }
+  out[-1] = n;
+  return ((u64)__float_as_uint((float)p) << 32) | at;
+}
+
 LOB_HD u64 dmm_pack(float v, u32 id) {
 #ifdef __CUDA_ARCH__
   u32 b = __float_as_uint(v);
@@ -167,6 +237,34 @@ LOB_DEV void touch_bit(u32* bm, u64 key) {
   const u32 bit = 1u << (u32)(key & 31u);
   u32* w = bm + (key >> 5);
   if (!(*reinterpret_cast<volatile u32*>(w) & bit)) atomicOr(w, bit);
+}
+
+// ---------------------------------------------------------------------------
+// Hash index of a sorted view's join prefixes (Sec. 5.1: a lock-free hash
+// table with open addressing and linear probing whose payload is row
+// indices).  A slot holds prefix + 1 (0: empty), the first row of the
+// prefix's run in the sorted view and the run's length; 2^bits slots.
+// ---------------------------------------------------------------------------
+struct HashSlot {
+  unsigned long long key;
+  u32 lo, cnt;
+};
+LOB_HD u64 hash_home(u64 pv, int bits) { return (pv * 0x9E3779B97F4A7C15ull) >> (64 - bits); }
+// the run [lo, hi) of prefix pv (empty when absent); at most 2^bits probes
+LOB_DEV void hash_find(const HashSlot* tab, int bits, u64 pv, u64& lo, u64& hi) {
+  const u64 mask = (1ull << bits) - 1;
+  u64 s = hash_home(pv, bits);
+  lo = hi = 0;
+  for (u64 n = 0; n <= mask; n++) {
+    const u64 k = tab[s].key;
+    if (k == pv + 1) {
+      lo = tab[s].lo;
+      hi = lo + tab[s].cnt;
+      return;
+    }
+    if (k == 0) return;
+    s = (s + 1) & mask;
+  }
 }
 
 // ---------------------------------------------------------------------------

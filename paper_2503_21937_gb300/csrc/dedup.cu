@@ -490,6 +490,11 @@ LOB_DEV typename Sem::Cand row_tag(const float* raw, u64 row, u32 id_base, int d
   if constexpr (std::is_same<Sem, SemDiffMaxMin>::value) {
     float v = raw ? raw[row] : 1.0f;
     return dmm_pack(v, differentiable ? id_base + (u32)row : 0xFFFFFFFFu);
+  } else if constexpr (std::is_same<Sem, SemTop1>::value) {
+    // a row with a probability is the proof {its id}, whose arena entry sits at
+    // word 1 + 2 id; a row without one has the empty proof (word 0, probability 1)
+    if (!raw || !differentiable) return SemTop1::one();
+    return ((u64)__float_as_uint(raw[row]) << 32) | (u64)(1u + 2u * (id_base + (u32)row));
   } else if constexpr (std::is_same<Sem, SemUnit>::value) {
     return 1u;
   } else {
@@ -630,6 +635,7 @@ void unique_run(int sem, int key64, const void* keys, const void* tags, u64 n, v
     case SR_UNIT: dispatch_unique<SemUnit>(key64, keys, tags, n, okeys, otags, count_dev, scratch, st); break;
     case SR_MAX_MIN: dispatch_unique<SemMaxMin>(key64, keys, tags, n, okeys, otags, count_dev, scratch, st); break;
     case SR_DIFF_MAX_MIN: dispatch_unique<SemDiffMaxMin>(key64, keys, tags, n, okeys, otags, count_dev, scratch, st); break;
+    case SR_TOP1: dispatch_unique<SemTop1>(key64, keys, tags, n, okeys, otags, count_dev, scratch, st); break;
     default: dispatch_unique<SemAddMult>(key64, keys, tags, n, okeys, otags, count_dev, scratch, st); break;
   }
 }
@@ -647,6 +653,7 @@ void diff_merge(const MergeArgs& a, void* scratch, cudaStream_t st) {
     case SR_UNIT: merge_impl<K, SemUnit>(a, scratch, st); break;                  \
     case SR_MAX_MIN: merge_impl<K, SemMaxMin>(a, scratch, st); break;             \
     case SR_DIFF_MAX_MIN: merge_impl<K, SemDiffMaxMin>(a, scratch, st); break;    \
+    case SR_TOP1: merge_impl<K, SemTop1>(a, scratch, st); break;                  \
     default: merge_impl<K, SemAddMult>(a, scratch, st); break;                    \
   }
   if (a.key64) { LOB_MERGE(u64) } else { LOB_MERGE(u32) }
@@ -683,6 +690,7 @@ void combine_merge(int sem, int key64, const void* akeys, const void* atags, u64
     case SR_UNIT: combine_impl<K, SemUnit>(akeys, atags, na, bkeys, btags, nb, okeys, otags, count_dev, scratch, st); break; \
     case SR_MAX_MIN: combine_impl<K, SemMaxMin>(akeys, atags, na, bkeys, btags, nb, okeys, otags, count_dev, scratch, st); break; \
     case SR_DIFF_MAX_MIN: combine_impl<K, SemDiffMaxMin>(akeys, atags, na, bkeys, btags, nb, okeys, otags, count_dev, scratch, st); break; \
+    case SR_TOP1: combine_impl<K, SemTop1>(akeys, atags, na, bkeys, btags, nb, okeys, otags, count_dev, scratch, st); break; \
     default: combine_impl<K, SemAddMult>(akeys, atags, na, bkeys, btags, nb, okeys, otags, count_dev, scratch, st); break; \
   }
   if (key64) { LOB_COMB(u64) } else { LOB_COMB(u32) }
@@ -699,6 +707,7 @@ void load_unique(const LoadUniqueArgs& a, void* scratch, cudaStream_t st) {
     case SR_UNIT: load_impl<K, SemUnit>(a, scratch, st); break;                \
     case SR_MAX_MIN: load_impl<K, SemMaxMin>(a, scratch, st); break;           \
     case SR_DIFF_MAX_MIN: load_impl<K, SemDiffMaxMin>(a, scratch, st); break;  \
+    case SR_TOP1: load_impl<K, SemTop1>(a, scratch, st); break;                \
     default: load_impl<K, SemAddMult>(a, scratch, st); break;                  \
   }
   if (a.key64) { LOB_LOAD(u64) } else { LOB_LOAD(u32) }

@@ -230,7 +230,9 @@ int key_bytes(const Layout& L) { return L.key64 ? 8 : 4; }
 // accumulation, and whose arms with a derived delta relation are packed join
 // pipelines of at least one probe.
 bool loop_eligible(const lob_engine& e) {
-  if (!e.opt_driver || e.semiring == SR_UNIT || e.opt_sort_algo != 0) return false;
+  // (hash indexes of derived relations are built on the host; the loop
+  // rebuilds only dense offset tables)
+  if (!e.opt_driver || e.semiring == SR_UNIT || e.opt_sort_algo != 0 || e.opt_join_index == 3) return false;
   if ((int)e.rels.size() > kGMaxRels) return false;
   int narm = 0;
   for (const auto& r : e.rels) {
@@ -532,6 +534,7 @@ void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaS
       const IndexSt& I = W.index[S.prefix_len];
       P.index_mode = I.mode;
       P.dense_offs = I.offs.as<u64>();
+      P.hash_bits = I.hash_bits;
       const u64 n_blk = pjoin_loc_blocks(n_cap);
       P.loc = e.cnt.as<u32>();
       P.lo32 = e.lo.as<u32>();

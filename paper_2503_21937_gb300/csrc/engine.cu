@@ -162,6 +162,8 @@ static void release_derived(lob_engine& e) {
     r.filter_on = false;
     r.last_cand = r.last_new = r.cand_iter = 0;
   }
+  for (DevBuf* b : {&e.arena, &e.top1_state, &e.top1_prob}) e.release(*b);
+  e.arena_tail = e.arena_cap = 0;
   e.plans.clear();
 }
 
@@ -629,7 +631,8 @@ static void prepare(lob_engine& e, int sem) {
     }
   for (auto& p : e.plans)
     for (auto& A : p.arms) {
-      A.packed = e.opt_packed_join ? compile_packed(e, p.ast, A) : PackedArm{};
+      // top-1-proofs joins form unions of proofs: general steps only
+      A.packed = e.opt_packed_join && !sem_top1(sem) ? compile_packed(e, p.ast, A) : PackedArm{};
       if (sem == SR_UNIT) compile_cross(e, p.ast, A, A.packed);
     }
 }
@@ -680,6 +683,71 @@ static std::pair<void*, void*> sort_view_rows(lob_engine& e, RelSt& r, ViewSt& v
   e.after_launch("view sort");
   e.launches += 1;
   return {k, t};
+}
+
+// top-1-proofs: the proof arena (empty proof + one singleton proof per
+// input-fact id) and the probability of every id
+constexpr u64 kArenaMaxWords = 0xFFFFFFFFull;  // tags address words with 32 bits
+static void top1_setup(lob_engine& e, u64 n_ids) {
+  const u64 base_words = 1 + 2 * n_ids;
+  if (base_words > kArenaMaxWords) throw LobError(LOB_E_ARG, "top-1-proofs: more than 2^31 - 1 loaded rows");
+  const u64 words = std::min(kArenaMaxWords, std::max<u64>(2 * base_words, base_words + (1ull << 22)));
+  e.ensure(e.arena, words * 4);
+  e.arena_cap = std::min<u64>(kArenaMaxWords, e.arena.cap / 4);
+  top1_init_arena(e.arena.as<u32>(), n_ids, e.stream);
+  e.after_launch("proof arena");
+  e.ensure(e.top1_prob, std::max<u64>(n_ids, 1) * 4);
+  for (auto& r : e.rels) {
+    if (!r.n_in) continue;
+    float* dst = e.top1_prob.as<float>() + r.id_base;
+    if (r.in_has_tags)
+      e.check(cudaMemcpyAsync(dst, r.in_tags.p, r.n_in * 4, cudaMemcpyDeviceToDevice, e.stream), "fact probabilities");
+    else
+      fill_f32(dst, r.n_in, 1.0f, e.stream);
+  }
+  e.ensure(e.top1_state, 16);
+  e.check(cudaMemsetAsync(e.top1_state.p, 0, 16, e.stream), "proof arena state");
+  set_u64_dev(e.top1_state.as<unsigned long long>(), base_words, e.stream);
+  e.arena_tail = base_words;
+  e.launches += 3;
+}
+
+static Top1Arena top1_desc(lob_engine& e) {
+  Top1Arena A{};
+  A.words = e.arena.as<u32>();
+  A.tail = e.top1_state.as<unsigned long long>();
+  A.cap = e.arena_cap;
+  A.prob = e.top1_prob.as<float>();
+  A.proof_cap = (u32)e.opt_proof_cap;
+  A.err = reinterpret_cast<u32*>(e.top1_state.as<u64>() + 1);
+  return A;
+}
+
+// After a top-1-proofs join emission: a union longer than the proof cap is an
+// error; when the arena ran out, it grows (keeping the proofs before this
+// step) and the step runs again from the same tail.  Emission is idempotent:
+// every output has a fixed position.
+static void top1_after_emit(lob_engine& e, int sem, StepParams& P, const u64* part) {
+  for (;;) {
+    e.check(cudaMemcpyAsync(e.pinned, e.top1_state.p, 16, cudaMemcpyDeviceToHost, e.stream), "proof arena state");
+    e.sync();
+    const u64 tail = e.pinned[0];
+    if (e.pinned[1] & 1)
+      throw LobError(LOB_E_CAPACITY, "top-1-proofs: a proof is longer than the proof cap (option proof_cap)");
+    if (tail <= e.arena_cap) {
+      e.arena_tail = tail;
+      return;
+    }
+    if (e.arena_cap >= kArenaMaxWords) throw LobError(LOB_E_CAPACITY, "top-1-proofs: the proof arena needs 2^32 words");
+    const u64 want = std::min(kArenaMaxWords, std::max(2 * e.arena_cap, tail + tail / 2));
+    e.ensure(e.arena, want * 4, true);
+    e.arena_cap = std::min<u64>(kArenaMaxWords, e.arena.cap / 4);
+    set_u64_dev(e.top1_state.as<unsigned long long>(), e.arena_tail, e.stream);
+    P.top1 = top1_desc(e);
+    join_emit(sem, P, part, e.stream);
+    e.after_launch("join emit (proof arena grown)");
+    e.launches += 2;
+  }
 }
 
 static void load_facts(lob_engine& e) {
@@ -762,6 +830,7 @@ static void load_facts(lob_engine& e) {
       }
     }
   }
+  if (sem_top1(sem)) top1_setup(e, id_base);
 }
 
 // ---------------------------------------------------------------------------
@@ -779,7 +848,22 @@ static void ensure_index(lob_engine& e, ViewSt& v, int prefix) {
   const int dbits = L.bits - rest_shift(L, prefix);
   bool dense = dbits <= e.opt_dense_bits;
   if (e.opt_join_index == 1) dense = dbits <= 30;
-  if (e.opt_join_index == 2) dense = false;
+  if (e.opt_join_index >= 2) dense = false;
+  if (e.opt_join_index == 3 && v.n < (1ull << 31)) {
+    // hash index of the view's distinct prefixes (Sec. 5.1), load factor <= 1/2
+    int bits = 4;
+    while ((1ull << bits) < 2 * std::max<u64>(v.n, 1)) bits++;
+    I.mode = INDEX_HASH;
+    I.hash_bits = bits;
+    I.domain = 1ull << bits;
+    e.ensure(I.offs, I.domain * sizeof(HashSlot));
+    e.check(cudaMemsetAsync(I.offs.p, 0, I.domain * sizeof(HashSlot), e.stream), "hash index");
+    build_hash_index(L, prefix, v.keys.p, v.n, I.offs.p, bits, e.stream);
+    e.after_launch("hash index");
+    e.launches++;
+    I.valid = true;
+    return;
+  }
   if (dense) {
     I.mode = INDEX_DENSE;
     I.domain = 1ull << dbits;
@@ -927,6 +1011,8 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
   if (!D.n_recent) return;
   StepParams P;
   std::memset(&P, 0, sizeof(P));
+  const bool top1 = sem_top1(e.semiring);
+  if (top1) P.top1 = top1_desc(e);
   P.in_packed = 1;
   P.in_keys = D.rkeys.p;
   P.in_lay = D.views[0].lay;
@@ -983,6 +1069,7 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
     P.index_mode = I.mode;
     P.dense_offs = I.offs.as<u64>();
     P.dense_domain = I.domain;
+    P.hash_bits = I.hash_bits;
     fill_filters(R, S.filters, P.filters, P.n_filters);
     // count -> scan
     e.ensure(e.cnt, P.n_in * 4);
@@ -1023,6 +1110,7 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
         join_emit(sem, P, e.part.as<u64>(), e.stream);
         e.after_launch("join emit");
         e.launches += 2;
+        if (top1) top1_after_emit(e, sem, P, e.part.as<u64>());
         const u64 written = H.filter_on ? e.read_u64(e.counts.as<u64>() + 14) : sub;
         P.bitmap = nullptr;
         P.out_count = nullptr;
@@ -1054,6 +1142,7 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
     join_emit(sem, P, e.part.as<u64>(), e.stream);
     e.after_launch("join emit");
     e.launches += 2;
+    if (top1) top1_after_emit(e, sem, P, e.part.as<u64>());
     // the binding table becomes the next step's input
     side = out_side;
     P.in_packed = 0;
@@ -1168,12 +1257,14 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
       PA.v_stamp_mode = STAMP_NONE;
       PA.index_mode = W1.index[S1.prefix_len].mode;
       PA.dense_offs = W1.index[S1.prefix_len].offs.as<u64>();
+      PA.hash_bits = W1.index[S1.prefix_len].hash_bits;
       PStep PB = A.packed.cross;
       PB.v_keys = W2.keys.p;
       PB.v_key64 = W2.lay.key64;
       PB.v_n = W2.n;
       PB.index_mode = W2.index[S2.prefix_len].mode;
       PB.dense_offs = W2.index[S2.prefix_len].offs.as<u64>();
+      PB.hash_bits = W2.index[S2.prefix_len].hash_bits;
       PB.bitmap = H.bitmap.as<u32>();
       H.touched = true;
       const u64 before = g_prof ? e.read_u64(e.counts.as<u64>() + 13) : 0;
@@ -1213,6 +1304,7 @@ static void run_arm_packed(lob_engine& e, const RulePlan& rp, const ArmPlan& A, 
     const IndexSt& I = W.index[S.prefix_len];
     P.index_mode = I.mode;
     P.dense_offs = I.offs.as<u64>();
+    P.hash_bits = I.hash_bits;
     // unit semiring: warp-balanced steps.  Views below 2^27 rows keep a 32-row
     // group's outputs, and views below 2^22 rows a 1024-row block's outputs,
     // under 2^32.
@@ -1688,7 +1780,7 @@ static void choose_dedup_mode(lob_engine& e, RelSt& r) {
 // Dense (+)-accumulation for every derived relation of a tagged run whose key
 // space has at most opt_acc_bits bits (accumulator: 2^bits candidate tags).
 static void enable_dense(lob_engine& e) {
-  if (!e.opt_acc_dense || e.semiring == SR_UNIT) return;
+  if (!e.opt_acc_dense || e.semiring == SR_UNIT || sem_top1(e.semiring)) return;
   const int cb = dense_cand_bytes(sem_kernel(e.semiring));
   for (auto& r : e.rels) {
     const Layout& L = r.views[0].lay;
@@ -1706,7 +1798,7 @@ static void enable_dense(lob_engine& e) {
 
 static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   if (e.state != 0) throw LobError(LOB_E_STATE, "run_to_fixpoint was already called; call lob_reset first");
-  if (sem < 0 || sem > 4) throw LobError(LOB_E_ARG, "unknown semiring id");
+  if (sem < 0 || sem > 6) throw LobError(LOB_E_ARG, "unknown semiring id");
   e.peak_bytes = e.live_bytes;
   e.launches = 0;
   const u64 syncs0 = e.host_syncs;
@@ -1793,10 +1885,11 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   s.peak_bytes = e.peak_bytes;
   s.kernel_launches = e.launches;
   s.host_syncs = e.host_syncs - syncs0;
+  s.proof_words = e.arena_tail;
   e.stats = s;
   e.last_iter = k;
   e.state = 1;
-  e.ran_diff = sem == SR_DIFF_MAX_MIN || sem == SR_DIFF_ADD_MULT;
+  e.ran_diff = sem == SR_DIFF_MAX_MIN || sem == SR_DIFF_ADD_MULT || sem == SR_DIFF_TOP1;
   if (st) *st = s;
   return rc;
 }
@@ -2033,13 +2126,17 @@ struct TuneKnob {
 
 static int autotune(lob_engine& e, int sem, u32 max_iters, u32 repeats, lob_tune_report* rep) {
   if (e.state != 0) throw LobError(LOB_E_STATE, "autotune a loaded engine before lob_run_to_fixpoint");
-  if (sem < 0 || sem > 4) throw LobError(LOB_E_ARG, "unknown semiring id");
+  if (sem < 0 || sem > 6) throw LobError(LOB_E_ARG, "unknown semiring id");
   if (!repeats) repeats = 1;
-  std::vector<TuneKnob> knobs = {{&e.opt_packed_join, {1, 0}}, {&e.opt_join_index, {0, 1, 2}}, {&e.opt_radix_bits, {8, 6}}};
+  std::vector<TuneKnob> knobs = {{&e.opt_packed_join, {1, 0}}, {&e.opt_join_index, {0, 1, 2, 3}},
+                                 {&e.opt_radix_bits, {8, 6}}};
   if (sem == SR_UNIT) {
     knobs.push_back({&e.opt_warp_join, {1, 2, 0}});
     knobs.push_back({&e.opt_bitmap_delta, {1, 2, 0}});
     knobs.push_back({&e.opt_emit_filter, {1, 2, 0}});
+    knobs.push_back({&e.opt_cross_join, {1, 0}});
+  } else {
+    knobs.push_back({&e.opt_acc_dense, {1, 0}});
   }
   std::vector<int> saved;
   for (auto& k : knobs) saved.push_back(*k.field);
@@ -2094,6 +2191,8 @@ static int autotune(lob_engine& e, int sem, u32 max_iters, u32 repeats, lob_tune
       rep->join_index = e.opt_join_index;
       rep->radix_bits = e.opt_radix_bits;
       rep->emit_filter = e.opt_emit_filter;
+      rep->acc_dense = e.opt_acc_dense;
+      rep->cross_join = e.opt_cross_join;
       rep->trials = trials;
       rep->first_ms = first;
       rep->best_ms = best;
@@ -2155,6 +2254,57 @@ int lob_read_relation(lob_engine* e, uint32_t rel, uint32_t* cols, float* tags, 
     e->release(c);
     e->release(t);
     e->release(s);
+    return LOB_OK;
+  });
+}
+
+int lob_read_proofs(lob_engine* e, uint32_t rel, uint32_t* lens, uint32_t* ids, uint64_t id_capacity, uint64_t* n_ids,
+                    int mem) {
+  return guarded(e, [&] {
+    if (rel >= e->rels.size()) throw LobError(LOB_E_UNKNOWN_REL, "unknown relation id");
+    if (e->state != 1) throw LobError(LOB_E_STATE, "read after lob_run_to_fixpoint");
+    if (!sem_top1(e->semiring)) throw LobError(LOB_E_STATE, "proofs exist after a top-1-proofs run only");
+    if (mem != LOB_MEM_HOST && mem != LOB_MEM_DEVICE) throw LobError(LOB_E_ARG, "bad mem");
+    ViewSt& V = e->rels[rel].views[0];
+    const u64 n = V.n;
+    if (n_ids) *n_ids = 0;
+    if (!n) return LOB_OK;
+    DevBuf l, off, out;
+    e->ensure(l, n * 4);
+    e->ensure(off, (n + 1) * 8);
+    const u64* tags = V.tags.as<u64>();
+    top1_proof_lengths(tags, n, e->arena.as<u32>(), l.as<u32>(), e->stream);
+    e->after_launch("proof lengths");
+    scratch_at_least(*e, scan_scratch_elems(n) * 8 + 64);
+    exclusive_scan<u32, u64>(l.as<u32>(), off.as<u64>(), n, e->counts.as<u64>(), e->scratch.as<u64>(), e->stream);
+    e->after_launch("proof offsets");
+    const u64 total = e->read_u64(e->counts.as<u64>());
+    if (n_ids) *n_ids = total;
+    if (lens) {
+      e->check(cudaMemcpyAsync(lens, l.p, n * 4, mem == LOB_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                               e->stream), "proof lengths out");
+    }
+    if (ids && total > id_capacity) {
+      e->sync();
+      e->release(l);
+      e->release(off);
+      throw LobError(LOB_E_CAPACITY, "id capacity " + std::to_string(id_capacity) + " < " + std::to_string(total));
+    }
+    if (ids && total) {
+      u32* dst = ids;
+      if (mem == LOB_MEM_HOST) {
+        e->ensure(out, total * 4);
+        dst = out.as<u32>();
+      }
+      top1_copy_proofs(tags, n, e->arena.as<u32>(), off.as<u64>(), dst, e->stream);
+      e->after_launch("proof ids");
+      if (mem == LOB_MEM_HOST)
+        e->check(cudaMemcpyAsync(ids, out.p, total * 4, cudaMemcpyDeviceToHost, e->stream), "proof ids out");
+    }
+    e->sync();
+    e->release(l);
+    e->release(off);
+    e->release(out);
     return LOB_OK;
   });
 }
@@ -2309,7 +2459,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
   return guarded(e, [&] {
     if (!key) throw LobError(LOB_E_ARG, "null key");
     std::string k = key;
-    if (k == "join_index" && value >= 0 && value <= 2) e->opt_join_index = (int)value;
+    if (k == "join_index" && value >= 0 && value <= 3) e->opt_join_index = (int)value;
     else if (k == "dense_bits" && value >= 1 && value <= 30) e->opt_dense_bits = (int)value;
     else if (k == "radix_bits" && value >= 4 && value <= 11) e->opt_radix_bits = sort_supported_radix_bits((int)value);
     else if (k == "sync_check" && (value == 0 || value == 1)) e->opt_sync_check = (int)value;
@@ -2326,6 +2476,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "loop_cap_floor" && value >= 256 && value <= (1 << 24)) e->opt_loop_cap_floor = (int)value;
     else if (k == "packed_backward" && (value == 0 || value == 1)) e->opt_packed_backward = (int)value;
     else if (k == "cross_join" && (value == 0 || value == 1)) e->opt_cross_join = (int)value;
+    else if (k == "proof_cap" && value >= 1 && value <= (1 << 20)) e->opt_proof_cap = (int)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

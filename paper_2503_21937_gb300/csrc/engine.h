@@ -49,8 +49,9 @@ struct DevBuf {
 };
 
 struct IndexSt {
-  int mode = 0;  // INDEX_DENSE / INDEX_BSEARCH
+  int mode = 0;  // INDEX_DENSE / INDEX_BSEARCH / INDEX_HASH
   u64 domain = 0;
+  int hash_bits = 0;  // INDEX_HASH: the table (in offs) has 2^hash_bits slots
   bool valid = false;
   DevBuf offs;
 };
@@ -198,6 +199,7 @@ struct lob_engine {
   int opt_loop_cap_floor = 1 << 16;  // smallest buffer capacity (rows) the device loop plans with
   int opt_packed_backward = 1;    // diff-add-mult backward replays packed arms on the packed kernels
   int opt_cross_join = 1;         // unit semiring: fused cross-product step for two probes keyed by the delta row
+  int opt_proof_cap = 300;        // top-1-proofs: longest proof (input facts) a union may produce
   std::map<std::string, u64> loop_caps;  // buffer capacities the device loop needed, kept across runs
   u64 host_syncs = 0;             // host waits for the GPU (statistics)
   cudaStream_t capture_stream = nullptr;  // private stream the device loop's graph is captured on (created on first use)
@@ -215,6 +217,10 @@ struct lob_engine {
   DevBuf bfact[2][2 * kMaxArity];  // backward: per carried body fact, its row and tag
   std::vector<std::vector<std::pair<u64, u64>>> iter_counts;  // per iteration: (|F|, |recent|) per relation
   u64* pinned = nullptr;           // host readback slots
+  // top-1-proofs: the proof arena (u32 words), its tail and error word
+  // (top1_state[0], [1]) and the probability of every input-fact id
+  DevBuf arena, top1_state, top1_prob;
+  u64 arena_tail = 0, arena_cap = 0;  // host copies, current after every join step
   u64 launches = 0;
   u64 cand_emitted = 0;  // candidates emitted by the joins of the current run
 
@@ -242,8 +248,13 @@ inline void note_loop_cap(lob_engine& e, const std::string& key, u64 v) {
 }
 
 // tag widths and update policy per semiring
+inline bool sem_top1(int sem) { return sem == SR_TOP1 || sem == SR_DIFF_TOP1; }
 inline int cand_bytes(int sem) { return sem == SR_UNIT ? 0 : (sem == SR_MAX_MIN ? 4 : 8); }
-inline int stored_bytes(int sem) { return sem == SR_UNIT ? 0 : (sem == SR_DIFF_MAX_MIN ? 8 : 4); }
-inline bool sem_idempotent(int sem) { return sem == SR_UNIT || sem == SR_MAX_MIN || sem == SR_DIFF_MAX_MIN; }
+inline int stored_bytes(int sem) { return sem == SR_UNIT ? 0 : (sem == SR_DIFF_MAX_MIN || sem_top1(sem) ? 8 : 4); }
+inline bool sem_idempotent(int sem) {
+  return sem == SR_UNIT || sem == SR_MAX_MIN || sem == SR_DIFF_MAX_MIN || sem_top1(sem);
+}
 inline bool sem_stamps(int sem) { return sem == SR_ADD_MULT || sem == SR_DIFF_ADD_MULT; }
-inline int sem_kernel(int sem) { return sem == SR_DIFF_ADD_MULT ? SR_ADD_MULT : sem; }
+inline int sem_kernel(int sem) {
+  return sem == SR_DIFF_ADD_MULT ? SR_ADD_MULT : (sem == SR_DIFF_TOP1 ? SR_TOP1 : sem);
+}

@@ -92,7 +92,11 @@ __global__ void __launch_bounds__(256) k_join_emit(const __grid_constant__ StepP
       if (c >= P.prefix_len && ok) ok = apply_act(P.v_act[c], (u32)field_of(vk, P.v_lay.shift[c], P.v_lay.width[c]), val);
     }
     for (int f = 0; f < P.n_filters && ok; f++) ok = eval_filter(P.filters[f], val);
-    if constexpr (Sem::kTags) tag = Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v]));
+    if constexpr (std::is_same<Sem, SemTop1>::value) {
+      if (ok) tag = top1_union(P.top1, tag, reinterpret_cast<const S*>(P.v_tags)[v]);
+    } else if constexpr (Sem::kTags) {
+      tag = Sem::mul(tag, Sem::from_stored(reinterpret_cast<const S*>(P.v_tags)[v]));
+    }
     write_output<Sem>(P, P.out_base + (j - P.j_begin), ok, val, sample, tag);
   }
 }
@@ -241,7 +245,8 @@ __global__ void k_read_rows(Layout L, Perm perm, const void* __restrict__ keys, 
     if (samples) samples[i] = L.swidth ? (u32)field_of(k, L.sshift, L.swidth) : 0u;
     if (otags) {
       float t = 1.0f;
-      if constexpr (std::is_same<Sem, SemDiffMaxMin>::value) t = dmm_value(reinterpret_cast<const u64*>(tags)[i]);
+      if constexpr (std::is_same<Sem, SemDiffMaxMin>::value || std::is_same<Sem, SemTop1>::value)
+        t = dmm_value(reinterpret_cast<const u64*>(tags)[i]);
       else if constexpr (Sem::kTags) t = reinterpret_cast<const float*>(tags)[i];
       otags[i] = t;
     }
@@ -270,6 +275,7 @@ void by_sem(int sem, A&&... a) {
     case SR_UNIT: Launch<SemUnit>::go(a...); break;
     case SR_MAX_MIN: Launch<SemMaxMin>::go(a...); break;
     case SR_DIFF_MAX_MIN: Launch<SemDiffMaxMin>::go(a...); break;
+    case SR_TOP1: Launch<SemTop1>::go(a...); break;
     default: Launch<SemAddMult>::go(a...); break;
   }
 }
@@ -300,7 +306,7 @@ template <class Sem> struct ReadL {
 
 static double input_row_bytes(int sem, const StepParams& P) {
   const double tb = sem == SR_UNIT ? 0 : (sem == SR_MAX_MIN ? 4 : 8);
-  if (P.in_packed) return (P.in_lay.key64 ? 8 : 4) + (sem == SR_UNIT ? 0 : (sem == SR_DIFF_MAX_MIN ? 8 : 4));
+  if (P.in_packed) return (P.in_lay.key64 ? 8 : 4) + (sem == SR_UNIT ? 0 : (sem == SR_DIFF_MAX_MIN || sem == SR_TOP1 ? 8 : 4));
   return 4.0 * (P.n_in_cols + 1) + tb;
 }
 static double output_row_bytes(int sem, const StepParams& P) {
@@ -324,7 +330,7 @@ void lbs_partition(const u64* off, u64 n_in, u64 j_begin, u64 total, u64* part, 
 void join_emit(int sem, const StepParams& P, const u64* part, cudaStream_t st) {
   // read the input rows and their offsets once, each matched view row once,
   // write every output row once
-  const double vb = (P.v_lay.key64 ? 8 : 4) + (sem == SR_UNIT ? 0 : (sem == SR_DIFF_MAX_MIN ? 8 : 4));
+  const double vb = (P.v_lay.key64 ? 8 : 4) + (sem == SR_UNIT ? 0 : (sem == SR_DIFF_MAX_MIN || sem == SR_TOP1 ? 8 : 4));
   ProfScope ps("join_emit", P.n_in * (input_row_bytes(sem, P) + 16.0) + P.total * (vb + output_row_bytes(sem, P)), st);
   if (P.total) by_sem<EmitL>(sem, P, part, st);
 }
@@ -339,6 +345,34 @@ void build_dense_index(const Layout& L, int prefix_len, const void* keys, u64 n,
   ProfScope ps("index_build", (domain + 1) * 8.0 + n * (L.key64 ? 8.0 : 4.0), st);
   k_dense_index<<<grid_for(domain + 1), 256, 0, st>>>(keys, L.key64, n, rest_shift(L, prefix_len), offs, domain, n_dev,
                                                      changed_dev, keys_pp);
+}
+
+// Insert every distinct prefix of a sorted view, by the first row of its run.
+__global__ void k_hash_build(const void* __restrict__ keys, int key64, u64 n, int rs, HashSlot* __restrict__ tab, int bits) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  const u64 mask = (1ull << bits) - 1;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const u64 pv = shr64(load_key(keys, key64, i), rs);
+    if (i > 0 && shr64(load_key(keys, key64, i - 1), rs) == pv) continue;
+    const u64 klo = shl64(pv, rs), khi = klo + shl64(1ull, rs);
+    const u64 hi = (khi <= klo || rs >= 64) ? n : lower_bound_any(keys, key64, n, khi);
+    u64 sl = hash_home(pv, bits);
+    for (u64 t = 0; t <= mask; t++) {  // at most one pass over the table (load factor <= 1/2)
+      const unsigned long long old = atomicCAS(&tab[sl].key, 0ull, (unsigned long long)(pv + 1));
+      if (old == 0ull) {
+        tab[sl].lo = (u32)i;
+        tab[sl].cnt = (u32)(hi - i);
+        break;
+      }
+      sl = (sl + 1) & mask;
+    }
+  }
+}
+
+void build_hash_index(const Layout& L, int prefix_len, const void* keys, u64 n, void* table, int bits, cudaStream_t st) {
+  ProfScope ps("index_build", n * (L.key64 ? 8.0 : 4.0) + 16.0 * (double)(1ull << bits), st);
+  if (n) k_hash_build<<<grid_for(n), 256, 0, st>>>(keys, L.key64, n, rest_shift(L, prefix_len),
+                                                   reinterpret_cast<HashSlot*>(table), bits);
 }
 
 __global__ void k_copy_words(const u32* __restrict__ in, u32* __restrict__ out, u64 n_words, const u64* __restrict__ n_dev,

@@ -90,6 +90,8 @@ LOB_DEV bool probe_range(const StepParams& P, const u32* val, u32 sample, u64& l
   if (P.index_mode == INDEX_DENSE) {
     lo = P.dense_offs[pv];
     hi = P.dense_offs[pv + 1];
+  } else if (P.index_mode == INDEX_HASH) {
+    hash_find(reinterpret_cast<const HashSlot*>(P.dense_offs), P.hash_bits, pv, lo, hi);
   } else {
     const u64 klo = pv << rs;
     const u64 khi = klo + (1ull << rs);

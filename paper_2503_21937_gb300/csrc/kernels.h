@@ -106,7 +106,7 @@ struct FilterP {
   u32 a_const, b_const;
 };
 enum { STAMP_NONE = 0, STAMP_LT = 1, STAMP_EQ = 2 };
-enum { INDEX_DENSE = 1, INDEX_BSEARCH = 2 };
+enum { INDEX_DENSE = 1, INDEX_BSEARCH = 2, INDEX_HASH = 3 };
 
 // One step of a join pipeline: rows of an input table (a packed relation
 // segment or a materialised binding table) optionally joined with one
@@ -129,7 +129,8 @@ struct StepParams {
   int v_stamp_mode; u32 v_stamp_val;
   int prefix_len; int8_t prefix_slot[kMaxArity]; u32 prefix_const[kMaxArity];
   ColAct v_act[kMaxArity];
-  int index_mode; const u64* dense_offs; u64 dense_domain;
+  int index_mode; const u64* dense_offs; u64 dense_domain;  // INDEX_HASH: dense_offs holds the HashSlot table of 2^hash_bits slots
+  int hash_bits;
   int n_filters; FilterP filters[kMaxFilters];
   // output
   int out_packed;
@@ -144,6 +145,8 @@ struct StepParams {
   // fact of the head relation and every candidate emitted so far; only
   // candidates that set their bit are written, compacted at out_base + *out_count
   u32* bitmap; u64* out_count;
+  // top-1-proofs: the proof arena the tag product (a union of proofs) writes to
+  Top1Arena top1;
 };
 
 void join_count(int sem, const StepParams& P, cudaStream_t st);
@@ -183,6 +186,9 @@ void merge_nodup(int key64, const void* a, u64 na, const void* b, u64 nb, void* 
 // n_dev (optional): the key count in device memory, n its capacity;
 // changed_dev (optional): when it holds 0 the view is unchanged and the index is kept
 // keys_pp (optional): device slot holding the keys pointer (replaces keys)
+// hash index of the view's prefixes of prefix_len columns (and the sample id)
+// into a zeroed table of 2^bits HashSlot entries
+void build_hash_index(const Layout& L, int prefix_len, const void* keys, u64 n, void* table, int bits, cudaStream_t st);
 void build_dense_index(const Layout& L, int prefix_len, const void* keys, u64 n, u64* offs, u64 domain, cudaStream_t st,
                        const u64* n_dev = nullptr, const u64* changed_dev = nullptr, void* const* keys_pp = nullptr);
 // copy n elements of elem_bytes (a multiple of 4); n_dev as above; src_pp
@@ -199,3 +205,24 @@ void read_rows(int sem, const Layout& L, const int* perm, const void* keys, cons
                u64 stride, float* otags, u32* samples, cudaStream_t st);
 void reduce_max_u32(const u32* a, u64 n, u32* out_dev, cudaStream_t st);
 void gather_cand_tags(int sem, const void* stored, const u64* idx, u64 n, void* out, cudaStream_t st);
+
+// top-1-proofs (top1.cu).  The arena: word 0 the empty proof, words 1 + 2i and
+// 2 + 2i the singleton proof of input-fact id i (top1_init_arena writes both),
+// then the proofs joins append.
+void top1_init_arena(u32* words, u64 n_ids, cudaStream_t st);
+void fill_f32(float* a, u64 n, float v, cudaStream_t st);
+void set_u64_dev(unsigned long long* p, u64 v, cudaStream_t st);
+// per fact, the length of the proof its tag points to
+void top1_proof_lengths(const u64* tags, u64 n, const u32* words, u32* lens, cudaStream_t st);
+// per fact, its proof's ids copied to out + off[i]
+void top1_copy_proofs(const u64* tags, u64 n, const u32* words, const u64* off, u32* out, cudaStream_t st);
+// gradient of every output's proof probability, added to the input rows
+constexpr int kTop1GradRels = 64;
+struct Top1GradTable {
+  int n;
+  u32 base[kTop1GradRels];
+  u32 count[kTop1GradRels];
+  float* grad[kTop1GradRels];
+};
+void top1_grad_scatter(const u64* tags, const float* g, u64 n, const u32* words, const float* prob,
+                       const Top1GradTable& T, cudaStream_t st);

@@ -467,6 +467,8 @@ __global__ void __launch_bounds__(256) k_pcount_loc(const __grid_constant__ PSte
           if (P.index_mode == INDEX_DENSE) {
             l = P.dense_offs[pv];
             h = P.dense_offs[pv + 1];
+          } else if (P.index_mode == INDEX_HASH) {
+            hash_find(reinterpret_cast<const HashSlot*>(P.dense_offs), P.hash_bits, pv, l, h);
           } else {
             const u64 vn = dev_size(P.v_n, P.v_n_dev);
             if (P.whole_view) {
@@ -561,6 +563,8 @@ LOB_DEV u32 probe_row(const PStep& P, u64 r, u64& wi, u32& lo) {
   if (P.index_mode == INDEX_DENSE) {
     l = P.dense_offs[pv];
     h = P.dense_offs[pv + 1];
+  } else if (P.index_mode == INDEX_HASH) {
+    hash_find(reinterpret_cast<const HashSlot*>(P.dense_offs), P.hash_bits, pv, l, h);
   } else if (P.whole_view) {
     l = 0;
     h = P.v_n;
@@ -856,6 +860,8 @@ LOB_DEV u32 probe_b(const PStep& B, u64 wi, u32& lo) {
   if (B.index_mode == INDEX_DENSE) {
     l = B.dense_offs[pv];
     h = B.dense_offs[pv + 1];
+  } else if (B.index_mode == INDEX_HASH) {
+    hash_find(reinterpret_cast<const HashSlot*>(B.dense_offs), B.hash_bits, pv, l, h);
   } else if (B.whole_view) {
     l = 0;
     h = B.v_n;

@@ -34,7 +34,8 @@ struct PStep {
   const void* v_keys; int v_key64; const void* v_tags; const u32* v_stamp; u64 v_n;
   int v_stamp_mode; u32 v_stamp_val;
   int n_prefix; PField prefix[kMaxPFields];
-  int index_mode; const u64* dense_offs; int rest_shift; int whole_view;
+  int index_mode; const u64* dense_offs; int rest_shift; int whole_view;  // INDEX_HASH: dense_offs = HashSlot table
+  int hash_bits;
   int n_checks; PCheck checks[kMaxPChecks];
   // output word: a head key or a binding word
   void* out_words; int out_w64; void* out_tags; u64 out_base;

@@ -23,7 +23,8 @@ LOB_OK = 0
 ERRORS = {-1: "LOB_E_ARG", -2: "LOB_E_PARSE", -3: "LOB_E_UNKNOWN_REL", -4: "LOB_E_UNSAFE_RULE", -5: "LOB_E_OOM",
           -6: "LOB_E_MAXITER", -7: "LOB_E_TIMEOUT", -8: "LOB_E_CUDA", -9: "LOB_E_CAPACITY", -10: "LOB_E_STATE",
           -11: "LOB_E_KEY_WIDTH"}
-SEMIRINGS = {"unit": 0, "max_min": 1, "add_mult": 2, "diff_max_min": 3, "diff_add_mult": 4}
+SEMIRINGS = {"unit": 0, "max_min": 1, "add_mult": 2, "diff_max_min": 3, "diff_add_mult": 4,
+             "top1_proofs": 5, "diff_top1_proofs": 6}
 MEM_HOST, MEM_DEVICE = 0, 1
 
 # every symbol declared in include/lobster.h (checked by the tests)
@@ -31,7 +32,7 @@ EXPORTS = ["lob_create", "lob_destroy", "lob_last_error", "lob_declare_relation"
            "lob_load_relation", "lob_add_rule", "lob_run_to_fixpoint", "lob_relation_size", "lob_read_relation",
            "lob_backward", "lob_reset", "lob_set_option", "lob_profile_count", "lob_profile_entry",
            "lob_profile_reset", "lob_prim_sort", "lob_prim_exclusive_scan", "lob_prim_unique",
-           "lob_prim_diff_merge", "lob_unique_rows_noalloc", "lob_autotune"]
+           "lob_prim_diff_merge", "lob_unique_rows_noalloc", "lob_autotune", "lob_read_proofs"]
 NOALLOC_MAX_ROWS = 262144
 
 _lib = None
@@ -47,7 +48,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_uint32), ("semiring", ctypes.c_uint32), ("derived", ctypes.c_uint64),
                 ("candidates", ctypes.c_uint64), ("new_facts", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
                 ("ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64), ("host_syncs", ctypes.c_uint64),
-                ("device_iterations", ctypes.c_uint32), ("graph_launches", ctypes.c_uint32)]
+                ("device_iterations", ctypes.c_uint32), ("graph_launches", ctypes.c_uint32),
+                ("proof_words", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -64,7 +66,8 @@ class LobAlloc(ctypes.Structure):
 class TuneReport(ctypes.Structure):
     _fields_ = [("packed_join", ctypes.c_int32), ("warp_join", ctypes.c_int32), ("bitmap_delta", ctypes.c_int32),
                 ("join_index", ctypes.c_int32), ("radix_bits", ctypes.c_int32), ("emit_filter", ctypes.c_int32),
-                ("trials", ctypes.c_uint32), ("first_ms", ctypes.c_double), ("best_ms", ctypes.c_double)]
+                ("trials", ctypes.c_uint32), ("first_ms", ctypes.c_double), ("best_ms", ctypes.c_double),
+                ("acc_dense", ctypes.c_int32), ("cross_join", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -93,6 +96,7 @@ def load_library(path: str = LIB_PATH):
     lib.lob_relation_size.argtypes = [vp, u32, P(u64)]
     lib.lob_read_relation.argtypes = [vp, u32, vp, vp, vp, u64, P(u64), ctypes.c_int]
     lib.lob_backward.argtypes = [vp, u32, vp, vp, ctypes.c_int]
+    lib.lob_read_proofs.argtypes = [vp, u32, vp, vp, u64, P(u64), ctypes.c_int]
     lib.lob_reset.argtypes = [vp]
     lib.lob_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_int64]
     lib.lob_profile_count.argtypes = [vp, P(u32)]
@@ -294,6 +298,22 @@ class Engine:
                                              samples.ctypes.data if samples is not None else None, cap,
                                              ctypes.byref(got), MEM_HOST))
         return got.value
+
+    def proofs(self, name: str) -> list:
+        """top-1-proofs: per fact of ``read(name)`` (same order) its proof, an
+        ascending uint32 array of input-fact ids (row q of relation k has id q
+        plus the rows loaded into the relations declared before k)."""
+        n = self.size(name)
+        lens = np.zeros(max(n, 1), np.uint32)
+        total = ctypes.c_uint64()
+        self._chk(self.lib.lob_read_proofs(self.h, self.ids[name], lens.ctypes.data, None, 0, ctypes.byref(total),
+                                           MEM_HOST))
+        ids = np.zeros(max(total.value, 1), np.uint32)
+        self._chk(self.lib.lob_read_proofs(self.h, self.ids[name], None, ids.ctypes.data, total.value,
+                                           ctypes.byref(total), MEM_HOST))
+        if n == 0:
+            return []
+        return np.split(ids[:total.value], np.cumsum(lens[:n].astype(np.int64))[:-1])
 
     def backward(self, out_name: str, grad, grad_inputs: dict):
         """grad: gradient per fact of out_name (read order).  grad_inputs: name ->

@@ -75,6 +75,15 @@ def compare(program: str, inputs: dict, semiring: str = "unit", rels=None, rtol=
             assert np.array_equal(rel.tags, want.tags.astype(np.float32)), name
         elif semiring in ("add_mult", "diff_add_mult"):
             np.testing.assert_allclose(rel.tags, want.tags, rtol=rtol, atol=0, err_msg=name)
+        elif semiring in ("top1_proofs", "diff_top1_proofs"):
+            # with no equally likely proofs met, the kept proof of every key is
+            # unique: the same ids and the same f32 product on both sides
+            assert res.ties == 0, "instance has ties: proofs are not unique"
+            assert np.array_equal(rel.tags, want.tags.astype(np.float32)), name
+            got_p, want_p = e.proofs(name), res.proofs(name)
+            assert len(got_p) == len(want_p), name
+            for i, (a, b) in enumerate(zip(got_p, want_p)):
+                assert np.array_equal(a, b), (name, i, a, b)
         else:
             assert np.all(rel.tags == 1.0)
     e.close()

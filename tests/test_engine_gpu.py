@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from paper_2503_21937_gb300 import workloads as W
-from tests.common import compare, engine_run
+from tests.common import compare, engine_run, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -301,7 +301,9 @@ def test_autotune_then_run_matches_oracle():
     e.program(W.TC_PROGRAM)
     e.load("edge", (s, d))
     rep = e.autotune("unit", repeats=1)
-    assert rep["trials"] >= 1 + 1 + 2 + 1 + 2 + 2 + 2  # the first setting + every alternative of 6 knobs
+    # the first setting + every alternative of 7 knobs (join_index: offset table, 30-bit table, search, hash)
+    assert rep["trials"] >= 1 + 1 + 3 + 1 + 2 + 2 + 2 + 1
+    assert rep["join_index"] in (0, 1, 2, 3) and rep["cross_join"] in (0, 1)
     assert 0 < rep["best_ms"] <= rep["first_ms"]
     assert rep["warp_join"] in (0, 1, 2) and rep["bitmap_delta"] in (0, 1, 2) and rep["radix_bits"] in (6, 8)
     e.run("unit")
@@ -318,7 +320,8 @@ def test_autotune_then_run_matches_oracle():
     e.load("edge", (src, dst), np.asarray(p, np.float32))
     e.load("start", g["start"])
     rep = e.autotune("max_min", repeats=1)
-    assert rep["trials"] == 1 + 1 + 2 + 1  # semirings with tags tune packed_join, join_index, radix_bits
+    # semirings with tags tune packed_join, join_index, radix_bits and acc_dense
+    assert rep["trials"] == 1 + 1 + 3 + 1 + 1
     e.run("max_min")
     want = oracle_run(W.REACH_PROGRAM, inputs, "max_min").relation("reach")
     got = e.read("reach")
@@ -581,3 +584,37 @@ def test_cross_product_step(cross):
     samples = np.concatenate([np.zeros(len(parent), np.uint32), np.ones(len(p2), np.uint32)])
     compare(W.SG_PROGRAM, {"parent": ((np.concatenate([parent, p2]), np.concatenate([child, c2])), None, samples)},
             options=opts)
+
+
+# ---------------------------------------------------------------------------
+# hash index of join prefixes (join_index = 3)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("packed", [1, 0])
+def test_hash_index_join(packed):
+    """Join probes through the open-addressing hash index of each view's
+    distinct prefixes, on the packed and the general kernels: transitive
+    closure, same generation, Andersen (four rules, secondary views),
+    batched kinship in a tagged semiring, and the backward pass."""
+    opts = {"join_index": 3, "packed_join": packed}
+    a, b = W.erdos_renyi(400, 1400, seed_index=150)
+    compare(W.TC_PROGRAM, {"edge": ((a, b),)}, options=opts)
+    parent, child, _ = W.random_tree(3000, seed_index=151)
+    compare(W.SG_PROGRAM, {"parent": ((parent, child),)}, options=opts)
+    A = W.andersen_program(3000, 9000, seed_index=152)
+    compare(W.ANDERSEN_PROGRAM, {k: ((v[0], v[1]),) for k, v in A.items()}, rels=["pt"], options=opts)
+    B = W.batched_instance(5)
+    f, c = B["fact"], B["comp"]
+    inputs = {"fact": ((f[0], f[1], f[2]), f[3], f[4]), "comp": ((c[0], c[1], c[2]), None, c[4])}
+    compare(W.KIN_PROGRAM, inputs, "max_min", rels=["kin"], options=opts)
+    g = W.grid_reach_instance(12, sub=153)
+    src, dst, p = g["edge"]
+    p = (p * 0.5).astype(np.float32)
+    ins = {"edge": ((src, dst), p), "start": (g["start"],)}
+    res = oracle_run(W.REACH_PROGRAM, ins, "diff_add_mult")
+    gout = W.stream(154).normal(res.relation("reach").cols.shape[1])
+    e, st, got = engine_run(W.REACH_PROGRAM, ins, "diff_add_mult", options=opts, read=["reach"])
+    gin = {"edge": np.zeros(len(src), np.float32)}
+    e.backward("reach", gout.astype(np.float32), gin)
+    e.close()
+    np.testing.assert_allclose(gin["edge"], res.vjp({"reach": gout})["edge"], rtol=1e-4, atol=1e-4)
