@@ -19,6 +19,9 @@ Parity status per function (pins are in ``tests/test_oracle_pins.py``):
                                      paper's printed proof, union of shared
                                      facts, brute-force two-hop maxima, the cap,
                                      finite differences)
+  * computed heads and filters    -- pinned (bounded walk lengths by boolean
+                                     matrix powers; wrap-around, division,
+                                     reserved value by direct u32 arithmetic)
 """
 from __future__ import annotations
 

@@ -51,6 +51,10 @@
 // sorted id list is lexicographically smaller and counts the tie (orc_ties):
 // the engine may keep either, so parity is checked on instances without ties.
 //
+// Rules may compute (Sec. 5.2): head arguments are u32 expressions over the
+// body's variables (+, -, * modulo 2^32; unsigned /), and filters compare two
+// such expressions with ==, !=, <, <=, >, >= (unsigned); see Expr below.
+//
 // Batched inputs (Sec. 4.3): facts carry a sample id and samples never join; the
 // oracle states that directly by running the fixpoint once per sample.
 //
@@ -118,16 +122,65 @@ struct Atom {
   std::string rel;
   std::vector<Term> args;
 };
+// Arithmetic over u32 values in head arguments and filters (Sec. 5.2: a
+// projection or selection may compute): a leaf term, or a binary operation
+// '+', '-', '*' (all modulo 2^32) or '/' (unsigned; a zero divisor drops the
+// grounding).  A computed head value of 2^32 - 1 also drops the grounding (the
+// engine reserves that value).
+struct Expr {
+  char op = 0;  // 0: leaf
+  Term leaf;
+  std::vector<Expr> kid;  // op != 0: the two operands
+};
+enum Cmp { CMP_EQ, CMP_NE, CMP_LT, CMP_LE, CMP_GT, CMP_GE };
 struct Filter {
-  Term a, b;
-  bool equal = false;
+  Expr a, b;
+  int cmp = CMP_EQ;
 };
 struct Rule {
   Atom head;
+  std::vector<Expr> head_expr;  // per head argument (a leaf for a plain term)
   std::vector<Atom> body;
   std::vector<Filter> filters;
   int nvars = 0;
 };
+
+bool eval_expr(const Expr& e, const std::vector<uint32_t>& val, uint32_t& out) {
+  if (!e.op) {
+    out = e.leaf.is_var ? val[e.leaf.value] : e.leaf.value;
+    return true;
+  }
+  uint32_t x, y;
+  if (!eval_expr(e.kid[0], val, x) || !eval_expr(e.kid[1], val, y)) return false;
+  switch (e.op) {
+    case '+': out = x + y; break;
+#if ORACLE_MUTANT == 16  // mutant: subtraction with its operands swapped
+    case '-': out = y - x; break;
+#else
+    case '-': out = x - y; break;
+#endif
+    case '*': out = x * y; break;
+    default:
+      if (y == 0) return false;
+      out = x / y;
+  }
+  return true;
+}
+
+bool compare_u32(int cmp, uint32_t x, uint32_t y) {
+  switch (cmp) {
+    case CMP_EQ: return x == y;
+    case CMP_NE: return x != y;
+#if ORACLE_MUTANT == 15  // mutant: '<' admits equality
+    case CMP_LT: return x <= y;
+#else
+    case CMP_LT: return x < y;
+#endif
+    case CMP_LE: return x <= y;
+    case CMP_GT: return x > y;
+    default: return x >= y;
+  }
+}
 
 struct Parser {
   const char* s;
@@ -197,10 +250,58 @@ struct Parser {
     } while (eat(","));
     return eat(")") && a.args.size() <= (size_t)kMaxArity;
   }
+  // expr := product (('+' | '-') product)*; product := primary (('*' | '/') primary)*
+  bool primary(Expr& e) {
+    if (eat("(")) return expr(e) && eat(")");
+    e.op = 0;
+    return term(e.leaf);
+  }
+  bool product(Expr& e) {
+    if (!primary(e)) return false;
+    for (;;) {
+      skip();
+      const char c = s[i];
+      if (c != '*' && c != '/') return true;
+      i++;
+      Expr n;
+      n.op = c;
+      n.kid.resize(2);
+      n.kid[0] = e;
+      if (!primary(n.kid[1])) return false;
+      e = n;
+    }
+  }
+  bool expr(Expr& e) {
+    if (!product(e)) return false;
+    for (;;) {
+      skip();
+      const char c = s[i];
+      if (c != '+' && c != '-') return true;
+      i++;
+      Expr n;
+      n.op = c;
+      n.kid.resize(2);
+      n.kid[0] = e;
+      if (!product(n.kid[1])) return false;
+      e = n;
+    }
+  }
+  bool head(Rule& r) {
+    std::string name;
+    if (!ident(name)) return false;
+    r.head.rel = name;
+    if (!eat("(")) return false;
+    do {
+      Expr e;
+      if (!expr(e)) return false;
+      r.head.args.push_back(e.op ? Term{} : e.leaf);
+      r.head_expr.push_back(e);
+    } while (eat(","));
+    return eat(")") && r.head.args.size() <= (size_t)kMaxArity;
+  }
   bool rule(Rule& r) {
     vars.clear();
-    std::string name;
-    if (!ident(name) || !atom_after_name(name, r.head)) return false;
+    if (!head(r)) return false;
     if (!eat(":-")) return false;
     do {
       skip();
@@ -213,11 +314,15 @@ struct Parser {
       } else {
         i = save;
         Filter f;
-        if (!term(f.a)) return false;
-        if (eat("!=")) f.equal = false;
-        else if (eat("==")) f.equal = true;
+        if (!expr(f.a)) return false;
+        if (eat("!=")) f.cmp = CMP_NE;
+        else if (eat("==")) f.cmp = CMP_EQ;
+        else if (eat("<=")) f.cmp = CMP_LE;
+        else if (eat(">=")) f.cmp = CMP_GE;
+        else if (eat("<")) f.cmp = CMP_LT;
+        else if (eat(">")) f.cmp = CMP_GT;
         else return false;
-        if (!term(f.b)) return false;
+        if (!expr(f.b)) return false;
         r.filters.push_back(f);
       }
     } while (eat(","));
@@ -411,13 +516,15 @@ struct Engine {
 #else
         for (const Filter& f : r.filters) {
 #endif
-          uint32_t x = f.a.is_var ? val[f.a.value] : f.a.value;
-          uint32_t y = f.b.is_var ? val[f.b.value] : f.b.value;
-          if ((x == y) != f.equal) return;
+          uint32_t x, y;
+          if (!eval_expr(f.a, val, x) || !eval_expr(f.b, val, y)) return;
+          if (!compare_u32(f.cmp, x, y)) return;
         }
         Tuple h{};
-        for (size_t c = 0; c < r.head.args.size(); c++)
-          h[c] = r.head.args[c].is_var ? val[r.head.args[c].value] : r.head.args[c].value;
+        for (size_t c = 0; c < r.head.args.size(); c++) {
+          if (!eval_expr(r.head_expr[c], val, h[c])) return;
+          if (r.head_expr[c].op && h[c] == 0xFFFFFFFFu) return;
+        }
 #if ORACLE_MUTANT == 11  // mutant: the first two head columns are transposed
         if (r.head.args.size() >= 2) std::swap(h[0], h[1]);
 #endif

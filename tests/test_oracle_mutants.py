@@ -25,6 +25,8 @@ MUTANTS = {
     12: "diff-max-min (x) keeps the greater operand",
     13: "top-1-proofs union keeps a shared fact twice",
     14: "top-1-proofs (+) keeps the less likely proof",
+    15: "'<' admits equality",
+    16: "subtraction with its operands swapped",
 }
 
 

@@ -554,3 +554,47 @@ def test_top1_gradient_matches_finite_differences():
     # error small, and a product is linear in each factor, so the central
     # difference has no truncation error
     _fd_check(W.REACH_PROGRAM, inputs, "reach", "diff_top1_proofs", gout, range(len(src)), h=1e-3)
+
+
+# ----------------------------------------------------------------------------
+# computed projections and selections (Sec. 5.2): u32 arithmetic in head
+# arguments, comparisons in filters
+# ----------------------------------------------------------------------------
+
+def test_bounded_walk_lengths_match_boolean_matrix_powers():
+    """walk(y, d+1) :- walk(x, d), edge(x, y), d < L: walk(y, k) holds iff some
+    walk of exactly k <= L edges leads from node 0 to y (powers of the
+    adjacency matrix)."""
+    s = W.stream(4343)
+    n, m, L = 9, 20, 6
+    src, dst = s.below(m, n), s.below(m, n)
+    prog = ("walk(x, 0) :- start(x).\n"
+            "walk(y, d + 1) :- walk(x, d), edge(x, y), d < %d.\n" % L)
+    r = oracle.run(prog, {"edge": ((src, dst),), "start": ((np.array([0], np.uint32),),)})
+    A = np.zeros((n, n), bool)
+    A[src, dst] = True
+    want, v = set(), np.zeros(n, bool)
+    v[0] = True
+    for k in range(L + 1):
+        want |= {(int(y), k) for y in np.nonzero(v)[0]}
+        v = (v[:, None] & A).any(axis=0)
+    assert rel_set(r.relation("walk")) == want
+
+
+def test_arithmetic_wraps_and_drops():
+    x = np.array([0, 1, 5, 7, 4000000000, 3], np.uint32)
+    y = np.array([0, 3, 5, 2, 3000000000, 0], np.uint32)
+    prog = ("diff(x, y - x) :- p(x, y), x <= y.\n"
+            "quot(x, x / y) :- p(x, y).\n"
+            "prod(x, x * y + 1) :- p(x, y).\n"
+            "pred(x - 1) :- p(x, y).\n"
+            "big(x) :- p(x, y), x + y > y * 2, (x - y) / 2 >= 1.\n")
+    r = oracle.run(prog, {"p": ((x, y),)})
+    pairs = list(zip(x.tolist(), y.tolist()))
+    M = 1 << 32
+    assert rel_set(r.relation("diff")) == {(a, b - a) for a, b in pairs if a <= b}
+    assert rel_set(r.relation("quot")) == {(a, a // b) for a, b in pairs if b}  # a zero divisor drops the row
+    assert rel_set(r.relation("prod")) == {(a, (a * b + 1) % M) for a, b in pairs}
+    assert rel_set(r.relation("pred")) == {((a - 1) % M,) for a, b in pairs if a != 0}  # 2^32-1 is reserved
+    assert rel_set(r.relation("big")) == {(a,) for a, b in pairs
+                                          if (a + b) % M > (b * 2) % M and ((a - b) % M) // 2 >= 1}
