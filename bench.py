@@ -47,10 +47,22 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    h = hashlib.sha256()
+def kernel_source_hash(unit: str = "pjoin.cu"):
+    """Hash of the translation unit that holds the join emission kernels and
+    of every local header it includes (recursively): the sources the ncu
+    counters in profiles/ were taken on."""
+    import re
     d = os.path.join(ROOT, "paper_2503_21937_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    seen, todo = set(), [unit]
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(os.path.join(d, f)):
+            continue
+        seen.add(f)
+        with open(os.path.join(d, f)) as fh:
+            todo += re.findall(r'#include "([^"]+)"', fh.read())
+    h = hashlib.sha256()
+    for f in sorted(seen):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]

@@ -62,14 +62,16 @@ LOB_DEV double head_adjoint(const BwdParams& B, u64 key) {
   return B.h_adj[j];
 }
 
-LOB_DEV u64 head_key(const StepParams& P, const u32* val, u32 sample) {
+// the head key of a grounding; false when a computed head value drops it
+LOB_DEV bool head_key(const StepParams& P, const u32* val, u32 sample, u64& key) {
   const Layout& L = P.out_lay;
-  u64 key = L.swidth ? (u64)sample << L.sshift : 0ull;
+  key = L.swidth ? (u64)sample << L.sshift : 0ull;
   for (int j = 0; j < L.arity; j++) {
-    const u32 x = P.head_slot[j] >= 0 ? val[P.head_slot[j]] : P.head_const[j];
+    u32 x;
+    if (!head_value(P, j, val, x)) return false;
     key |= (u64)x << L.shift[j];
   }
-  return key;
+  return true;
 }
 
 __global__ void __launch_bounds__(256) k_bwd_emit(const __grid_constant__ StepParams P, const __grid_constant__ BwdParams B,
@@ -119,10 +121,11 @@ __global__ void __launch_bounds__(256) k_bwd_emit(const __grid_constant__ StepPa
     const u64 vk = load_key(P.v_keys, P.v_lay.key64, v);
     for (int c = 0; c < P.v_lay.arity; c++)
       if (c >= P.prefix_len && ok) ok = apply_act(P.v_act[c], (u32)field_of(vk, P.v_lay.shift[c], P.v_lay.width[c]), val);
-    for (int f = 0; f < P.n_filters && ok; f++) ok = eval_filter(P.filters[f], val);
+    for (int f = 0; f < P.n_filters && ok; f++) ok = eval_filter(P, P.filters[f], val);
     if (B.last) {
       if (!ok) continue;
-      const u64 hk = head_key(P, val, sample);
+      u64 hk;
+      if (!head_key(P, val, sample, hk)) continue;
       // most groundings re-derive a head that existed before iteration k: one
       // bit of the iteration's new-head bitmap rules them out
       if (B.h_new && !((B.h_new[hk >> 5] >> (hk & 31)) & 1u)) continue;
@@ -184,7 +187,8 @@ __global__ void k_bwd_project(const __grid_constant__ StepParams P, const __grid
     u32 sample;
     double tag;
     if (!read_input<SemAddMult>(P, r, val, sample, tag)) continue;
-    const u64 hk = head_key(P, val, sample);
+    u64 hk;
+    if (!head_key(P, val, sample, hk)) continue;
     if (B.h_new && !((B.h_new[hk >> 5] >> (hk & 31)) & 1u)) continue;
     const double a = head_adjoint(B, hk);
     if (a != 0.0 && B.fact_adj[0]) atomicAdd(B.fact_adj[0] + r, a);
@@ -294,6 +298,7 @@ void fill_filters_b(const RuleAst& R, const std::vector<int>& fs, FilterP* out, 
     p.b_slot = F.b.var ? (int8_t)F.b.v : (int8_t)-1;
     p.b_const = F.b.var ? 0 : F.b.v;
     p.eq = F.eq ? 1 : 0;
+    p.prog = (uint8_t)F.prog;
     out[n++] = p;
   }
 }
@@ -322,6 +327,7 @@ void replay_arm(lob_engine& e, BwdState& S, const RulePlan& rp, const ArmPlan& A
     if (R.head.args[c].var) P.head_slot[c] = (int8_t)R.head.args[c].v;
     else P.head_const[c] = R.head.args[c].v;
   }
+  set_rule_code(R, P);
   BwdParams B;
   std::memset(&B, 0, sizeof(B));
   B.packed_source = 1;

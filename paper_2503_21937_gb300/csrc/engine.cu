@@ -293,6 +293,7 @@ static ArmPlan plan_arm(lob_engine& e, const RuleAst& R, int delta, bool idempot
     const FilterAst& F = R.filters[f];
     for (size_t s = 0; s < A.steps.size(); s++) {
       bool ok = (!F.a.var || bound_after[s][F.a.v]) && (!F.b.var || bound_after[s][F.b.v]);
+      for (u32 v : F.vars) ok = ok && bound_after[s][v];
       if (ok) { A.steps[s].filters.push_back((int)f); break; }
     }
   }
@@ -305,10 +306,12 @@ static ArmPlan plan_arm(lob_engine& e, const RuleAst& R, int delta, bool idempot
       for (int f : A.steps[q].filters) {
         if (R.filters[f].a.var) need[R.filters[f].a.v] = 1;
         if (R.filters[f].b.var) need[R.filters[f].b.v] = 1;
+        for (u32 v : R.filters[f].vars) need[v] = 1;
       }
     }
     for (auto& t : R.head.args)
       if (t.var) need[t.v] = 1;
+    for (u32 v : R.head_vars) need[v] = 1;
     for (int v = 0; v < nv; v++)
       if (need[v] && bound_after[s][v]) A.steps[s].live.push_back(v);
   }
@@ -594,7 +597,8 @@ static void prepare(lob_engine& e, int sem) {
       for (size_t c = 0; c < R.head.args.size(); c++) {
         const Term& t = R.head.args[c];
         int need = 1;
-        if (!t.var) need = bitlen((u64)t.v + 1);
+        if (c < R.head_prog.size() && R.head_prog[c]) need = 32;  // computed: any u32 but 2^32 - 1
+        else if (!t.var) need = bitlen((u64)t.v + 1);
         else
           for (auto& a : R.body)
             for (size_t q = 0; q < a.args.size(); q++)
@@ -631,8 +635,9 @@ static void prepare(lob_engine& e, int sem) {
     }
   for (auto& p : e.plans)
     for (auto& A : p.arms) {
-      // top-1-proofs joins form unions of proofs: general steps only
-      A.packed = e.opt_packed_join && !sem_top1(sem) ? compile_packed(e, p.ast, A) : PackedArm{};
+      // top-1-proofs joins form unions of proofs, and computed head arguments
+      // and comparison filters run bytecode: general steps only
+      A.packed = e.opt_packed_join && !sem_top1(sem) && !p.ast.computes() ? compile_packed(e, p.ast, A) : PackedArm{};
       if (sem == SR_UNIT) compile_cross(e, p.ast, A, A.packed);
     }
 }
@@ -908,8 +913,20 @@ static void fill_filters(const RuleAst& R, const std::vector<int>& fs, FilterP* 
     p.b_slot = F.b.var ? (int8_t)F.b.v : (int8_t)-1;
     p.b_const = F.b.var ? 0 : F.b.v;
     p.eq = F.eq ? 1 : 0;
+    p.prog = (uint8_t)F.prog;
     out[n++] = p;
   }
+}
+
+// the rule's bytecode programs (computed head arguments, comparison filters)
+void set_rule_code(const RuleAst& R, StepParams& P) {
+  for (int j = 0; j < kMaxArity; j++) P.head_prog[j] = 0;
+  for (size_t c = 0; c < R.head_prog.size() && c < (size_t)kMaxArity; c++) P.head_prog[c] = (uint8_t)R.head_prog[c];
+  for (size_t k = 0; k < R.progs.size(); k++) {
+    P.prog_off[k] = (uint8_t)R.progs[k].first;
+    P.prog_len[k] = (uint8_t)R.progs[k].second;
+  }
+  std::copy(R.code.begin(), R.code.end(), P.code);
 }
 
 static void set_head_output(lob_engine& e, const RuleAst& R, StepParams& P, RelSt& H) {
@@ -1013,6 +1030,7 @@ static void run_arm(lob_engine& e, const RulePlan& rp, const ArmPlan& A, u32 k) 
   std::memset(&P, 0, sizeof(P));
   const bool top1 = sem_top1(e.semiring);
   if (top1) P.top1 = top1_desc(e);
+  set_rule_code(R, P);
   P.in_packed = 1;
   P.in_keys = D.rkeys.p;
   P.in_lay = D.views[0].lay;

@@ -30,13 +30,21 @@ struct AtomAst {
 struct FilterAst {
   Term a, b;
   bool eq = false;
+  int prog = 0;            // k > 0: a comparison compiled to bytecode program k - 1 (a, b unused)
+  std::vector<u32> vars;   // the variables a bytecode filter reads
 };
 struct RuleAst {
   std::string text;
-  AtomAst head;
+  AtomAst head;            // a computed head argument holds a placeholder constant here
   std::vector<AtomAst> body;
   std::vector<FilterAst> filters;
   std::vector<std::string> var_names;
+  // bytecode (Sec. 5.2): computed head arguments and comparison filters
+  std::vector<BcIns> code;
+  std::vector<std::pair<int, int>> progs;  // (first instruction, length)
+  std::vector<int> head_prog;              // per head argument: k > 0 = program k - 1
+  std::vector<u32> head_vars;              // variables read by computed head arguments
+  bool computes() const { return !progs.empty(); }
 };
 
 // ---------------------------------------------------------------------------
@@ -238,6 +246,8 @@ struct lob_engine {
 };
 
 void engine_ensure_index(lob_engine& e, ViewSt& v, int prefix);
+// copy a rule's bytecode programs into step parameters
+void set_rule_code(const RuleAst& R, StepParams& P);
 // device-driven iterations after iteration k (driver.cu)
 int run_device_loop(lob_engine& e, u32& k, u32 max_iters, lob_stats& s, bool* taken);
 // A size a host-driven iteration reached, kept (with a quarter of slack) so

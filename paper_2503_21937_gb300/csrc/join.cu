@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) k_join_emit(const __grid_constant__ StepP
       if (c >= P.v_lay.arity) break;
       if (c >= P.prefix_len && ok) ok = apply_act(P.v_act[c], (u32)field_of(vk, P.v_lay.shift[c], P.v_lay.width[c]), val);
     }
-    for (int f = 0; f < P.n_filters && ok; f++) ok = eval_filter(P.filters[f], val);
+    for (int f = 0; f < P.n_filters && ok; f++) ok = eval_filter(P, P.filters[f], val);
     if constexpr (std::is_same<Sem, SemTop1>::value) {
       if (ok) tag = top1_union(P.top1, tag, reinterpret_cast<const S*>(P.v_tags)[v]);
     } else if constexpr (Sem::kTags) {
@@ -155,13 +155,15 @@ __global__ void __launch_bounds__(256) k_join_emit_filtered(const __grid_constan
     const u64 vk = load_key(P.v_keys, P.v_lay.key64, v);
     for (int c = 0; c < P.v_lay.arity; c++)
       if (c >= P.prefix_len && ok) ok = apply_act(P.v_act[c], (u32)field_of(vk, P.v_lay.shift[c], P.v_lay.width[c]), val);
-    for (int f = 0; f < P.n_filters && ok; f++) ok = eval_filter(P.filters[f], val);
+    for (int f = 0; f < P.n_filters && ok; f++) ok = eval_filter(P, P.filters[f], val);
     if (!ok) continue;
     u64 key = L.swidth ? (u64)sample << L.sshift : 0ull;
-    for (int c = 0; c < L.arity; c++) {
-      const u32 x = P.head_slot[c] >= 0 ? val[P.head_slot[c]] : P.head_const[c];
+    for (int c = 0; c < L.arity && ok; c++) {
+      u32 x;
+      ok = head_value(P, c, val, x);
       key |= (u64)x << L.shift[c];
     }
+    if (!ok) continue;
     const u32 bit = 1u << (u32)(key & 31u);
     if (atomicOr(P.bitmap + (key >> 5), bit) & bit) continue;
     kept[nkeep++] = key;

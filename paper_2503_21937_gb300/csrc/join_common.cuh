@@ -13,10 +13,60 @@ LOB_DEV bool apply_act(const ColAct& a, u32 v, u32* val) {
   return v == a.cnst;
 }
 
-LOB_DEV bool eval_filter(const FilterP& f, const u32* val) {
+// Run bytecode program `prog` of P on the row's variables; false when a
+// division by zero drops the row.
+LOB_DEV bool bc_run(const StepParams& P, int prog, const u32* val, u32& out) {
+  u32 st[kBcStack];
+  int sp = 0;
+  const int b = P.prog_off[prog], n = P.prog_len[prog];
+  for (int i = 0; i < n; i++) {
+    const BcIns I = P.code[b + i];
+    if (I.op == BC_VAR) {
+      st[sp++] = val[I.slot];
+    } else if (I.op == BC_CONST) {
+      st[sp++] = I.imm;
+    } else {
+      const u32 y = st[--sp];
+      const u32 x = st[sp - 1];
+      u32 r;
+      switch (I.op) {
+        case BC_ADD: r = x + y; break;
+        case BC_SUB: r = x - y; break;
+        case BC_MUL: r = x * y; break;
+        case BC_DIV:
+          if (y == 0) return false;
+          r = x / y;
+          break;
+        case BC_EQ: r = x == y; break;
+        case BC_NE: r = x != y; break;
+        case BC_LT: r = x < y; break;
+        case BC_LE: r = x <= y; break;
+        case BC_GT: r = x > y; break;
+        default: r = x >= y; break;
+      }
+      st[sp - 1] = r;
+    }
+  }
+  out = st[0];
+  return true;
+}
+
+LOB_DEV bool eval_filter(const StepParams& P, const FilterP& f, const u32* val) {
+  if (f.prog) {
+    u32 r;
+    return bc_run(P, f.prog - 1, val, r) && r != 0u;
+  }
   u32 a = f.a_slot >= 0 ? val[f.a_slot] : f.a_const;
   u32 b = f.b_slot >= 0 ? val[f.b_slot] : f.b_const;
   return (a == b) == (f.eq != 0);
+}
+
+// Value of head column j; false drops the row (a division by zero, or a
+// computed value of 2^32 - 1, which the keys reserve).
+LOB_DEV bool head_value(const StepParams& P, int j, const u32* val, u32& x) {
+  if (P.head_prog[j]) return bc_run(P, P.head_prog[j] - 1, val, x) && x != 0xFFFFFFFFu;
+  x = P.head_slot[j] >= 0 ? val[P.head_slot[j]] : P.head_const[j];
+  return true;
 }
 
 LOB_DEV bool stamp_ok(u32 s, int mode, u32 v) {
@@ -38,7 +88,7 @@ LOB_DEV bool read_input(const StepParams& P, u64 r, u32* val, u32& sample, typen
       if (!apply_act(P.in_act[j], (u32)field_of(key, P.in_lay.shift[j], P.in_lay.width[j]), val)) return false;
     }
     for (int f = 0; f < P.n_in_filters; f++)
-      if (!eval_filter(P.in_filters[f], val)) return false;
+      if (!eval_filter(P, P.in_filters[f], val)) return false;
     if constexpr (Sem::kTags) tag = Sem::from_stored(reinterpret_cast<const S*>(P.in_tags)[r]);
     else tag = Sem::one();
   } else {
@@ -106,18 +156,15 @@ LOB_DEV void write_output(const StepParams& P, u64 o, bool ok, const u32* val, u
   typedef typename Sem::Cand C;
   if (P.out_packed) {
     const Layout& L = P.out_lay;
-    u64 key;
-    if (!ok) {
-      key = invalid_of(L.key64);
-    } else {
-      key = L.swidth ? (u64)sample << L.sshift : 0ull;
+    u64 key = L.swidth ? (u64)sample << L.sshift : 0ull;
 #pragma unroll
-      for (int j = 0; j < kMaxArity; j++) {
-        if (j >= L.arity) break;
-        const u32 x = P.head_slot[j] >= 0 ? val[P.head_slot[j]] : P.head_const[j];
-        key |= (u64)x << L.shift[j];
-      }
+    for (int j = 0; j < kMaxArity; j++) {
+      if (j >= L.arity || !ok) break;
+      u32 x;
+      ok = head_value(P, j, val, x);
+      key |= (u64)x << L.shift[j];
     }
+    if (!ok) key = invalid_of(L.key64);
     store_key(P.out_keys, L.key64, o, key);
   } else {
     P.out_sample[o] = ok ? sample : 0xFFFFFFFFu;

@@ -104,7 +104,24 @@ struct ColAct {
 struct FilterP {
   int8_t a_slot, b_slot, eq;  // slot -1: use the constant
   u32 a_const, b_const;
+  uint8_t prog;               // k > 0: the filter is bytecode program k - 1 (a comparison); 0: a ==/!= b
 };
+
+// Bytecode of computed head arguments and filters (Sec. 5.2: a stack machine,
+// one thread per row, a small fixed stack in thread-local memory).  Values are
+// u32; +, -, * wrap modulo 2^32, / is unsigned and a zero divisor drops the
+// row; comparisons push 1 or 0.  The host checks every program's stack depth.
+enum BcOp : uint8_t {
+  BC_VAR = 0, BC_CONST, BC_ADD, BC_SUB, BC_MUL, BC_DIV, BC_EQ, BC_NE, BC_LT, BC_LE, BC_GT, BC_GE
+};
+struct BcIns {
+  uint8_t op, slot;
+  uint16_t pad;
+  u32 imm;
+};
+constexpr int kMaxCode = 64;   // instructions of one rule
+constexpr int kMaxProgs = 16;  // programs of one rule (computed head arguments + comparison filters)
+constexpr int kBcStack = 8;
 enum { STAMP_NONE = 0, STAMP_LT = 1, STAMP_EQ = 2 };
 enum { INDEX_DENSE = 1, INDEX_BSEARCH = 2, INDEX_HASH = 3 };
 
@@ -147,6 +164,11 @@ struct StepParams {
   u32* bitmap; u64* out_count;
   // top-1-proofs: the proof arena the tag product (a union of proofs) writes to
   Top1Arena top1;
+  // bytecode of the rule: head column j is program head_prog[j] - 1 when
+  // head_prog[j] > 0; program k is code[prog_off[k] .. + prog_len[k])
+  uint8_t head_prog[kMaxArity];
+  uint8_t prog_off[kMaxProgs], prog_len[kMaxProgs];
+  BcIns code[kMaxCode];
 };
 
 void join_count(int sem, const StepParams& P, cudaStream_t st);

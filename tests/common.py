@@ -60,6 +60,20 @@ def _oracle_run(program: str, inputs: dict, semiring: str = "unit"):
                                 for k, v in inputs.items()}, semiring)
 
 
+def _fact_names(ids, order, rows):
+    """Input-fact ids -> sorted (relation, row) pairs, ids counting rows over
+    the relations in `order` (relations without loaded rows count 0)."""
+    bases, b = [], 0
+    for k in order:
+        bases.append((b, k))
+        b += rows.get(k, 0)
+    out = []
+    for i in np.asarray(ids).tolist():
+        base, k = max((bb, kk) for bb, kk in bases if bb <= i and i < bb + rows.get(kk, 0))
+        out.append((k, i - base))
+    return sorted(out)
+
+
 def compare(program: str, inputs: dict, semiring: str = "unit", rels=None, rtol=1e-5, options=None, allocator=None):
     """Engine vs oracle: key sets bit-exact, tags per semiring tolerance.
     Returns (engine stats, oracle result)."""
@@ -80,10 +94,15 @@ def compare(program: str, inputs: dict, semiring: str = "unit", rels=None, rtol=
             # unique: the same ids and the same f32 product on both sides
             assert res.ties == 0, "instance has ties: proofs are not unique"
             assert np.array_equal(rel.tags, want.tags.astype(np.float32)), name
-            got_p, want_p = e.proofs(name), res.proofs(name)
+            # both number input facts by row over the relations, but in
+            # different relation orders: compare (relation, row) pairs
+            rows = {k: len(np.asarray(v[0][0])) for k, v in inputs.items()}
+            eng_order = sorted(e.ids, key=lambda k: e.ids[k])
+            got_p = [_fact_names(p, eng_order, rows) for p in e.proofs(name)]
+            want_p = [_fact_names(p, list(inputs), rows) for p in res.proofs(name)]
             assert len(got_p) == len(want_p), name
             for i, (a, b) in enumerate(zip(got_p, want_p)):
-                assert np.array_equal(a, b), (name, i, a, b)
+                assert a == b, (name, i, a, b)
         else:
             assert np.all(rel.tags == 1.0)
     e.close()

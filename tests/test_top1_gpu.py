@@ -73,8 +73,12 @@ def test_grid_grows_the_proof_arena():
 def test_paper_example_proof():
     from tests.golden.load import pathfinder_example
     program, inputs = pathfinder_example()
+    from tests.common import _fact_names
     e, st, got = engine_run(program, inputs, "top1_proofs")
-    assert [p.tolist() for p in e.proofs("connected")] == [[1, 2, 3, 4]]  # edge(1,2) .. edge(4,5)
+    rows = {k: len(v[0][0]) for k, v in inputs.items()}
+    order = sorted(e.ids, key=lambda k: e.ids[k])
+    # edge(1,2) .. edge(4,5): rows 1..4 of the fixture's edge facts
+    assert [_fact_names(p, order, rows) for p in e.proofs("connected")] == [[("edge", q) for q in range(1, 5)]]
     assert got["connected"].tags.tolist() == [np.float32(0.9 * 0.8 * 0.95 * 0.85)]
     e.close()
     compare(program, inputs, "top1_proofs")
