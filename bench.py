@@ -660,9 +660,10 @@ def main():
     pathfinder = None
     if not args.no_pathfinder:
         from paper_2503_21937_gb300 import pathfinder as PF
-        pathfinder = {"metric": "training-step samples/s (CNN edge predictor -> batched diff-max-min fixpoint -> "
+        pathfinder = {"metric": "training-step samples/s (CNN edge predictor -> batched differentiable fixpoint -> "
                                 "BCE -> backward -> Adam), synthetic Pathfinder-like grids",
-                      "by_side": PF.sweep()}
+                      "by_side": PF.sweep(semiring="diff_max_min"),
+                      "by_side_diff_top1_proofs": PF.sweep(semiring="diff_top1_proofs")}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample()
