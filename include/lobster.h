@@ -273,6 +273,9 @@ int lob_reset(lob_engine* e);
  *   "proof_cap"    top-1-proofs: the most input facts a proof may hold; a
  *                  union beyond it ends the run with LOB_E_CAPACITY
  *                  (1 .. 2^20)                                       (default 300)
+ *   "proof_arena_words" top-1-proofs: free u32 words of the proof arena
+ *                  when a run starts; it doubles whenever a join step runs
+ *                  out (that step runs again)        (16 .. 2^31, default 2^22)
  *   "cross_join"   1: under LOB_UNIT, an arm with two probes keyed by the
  *                  delta row alone (same generation: children(a) x
  *                  children(b)) whose new facts only set bitmap bits runs

@@ -696,7 +696,7 @@ constexpr u64 kArenaMaxWords = 0xFFFFFFFFull;  // tags address words with 32 bit
 static void top1_setup(lob_engine& e, u64 n_ids) {
   const u64 base_words = 1 + 2 * n_ids;
   if (base_words > kArenaMaxWords) throw LobError(LOB_E_ARG, "top-1-proofs: more than 2^31 - 1 loaded rows");
-  const u64 words = std::min(kArenaMaxWords, std::max<u64>(2 * base_words, base_words + (1ull << 22)));
+  const u64 words = std::min(kArenaMaxWords, base_words + e.opt_arena_words);
   e.ensure(e.arena, words * 4);
   e.arena_cap = std::min<u64>(kArenaMaxWords, e.arena.cap / 4);
   top1_init_arena(e.arena.as<u32>(), n_ids, e.stream);
@@ -2495,6 +2495,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "packed_backward" && (value == 0 || value == 1)) e->opt_packed_backward = (int)value;
     else if (k == "cross_join" && (value == 0 || value == 1)) e->opt_cross_join = (int)value;
     else if (k == "proof_cap" && value >= 1 && value <= (1 << 20)) e->opt_proof_cap = (int)value;
+    else if (k == "proof_arena_words" && value >= 16 && value <= (1ll << 31)) e->opt_arena_words = (u64)value;
     else throw LobError(LOB_E_ARG, "unknown option or value out of range: " + k);
     return LOB_OK;
   });

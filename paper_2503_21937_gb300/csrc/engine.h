@@ -208,6 +208,7 @@ struct lob_engine {
   int opt_packed_backward = 1;    // diff-add-mult backward replays packed arms on the packed kernels
   int opt_cross_join = 1;         // unit semiring: fused cross-product step for two probes keyed by the delta row
   int opt_proof_cap = 300;        // top-1-proofs: longest proof (input facts) a union may produce
+  u64 opt_arena_words = 1ull << 22;  // top-1-proofs: free words of a fresh proof arena (it grows on demand)
   std::map<std::string, u64> loop_caps;  // buffer capacities the device loop needed, kept across runs
   u64 host_syncs = 0;             // host waits for the GPU (statistics)
   cudaStream_t capture_stream = nullptr;  // private stream the device loop's graph is captured on (created on first use)

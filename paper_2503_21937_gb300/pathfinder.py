@@ -203,7 +203,7 @@ def train(side: int = 6, batch: int = 32, steps: int = 60, lr: float = 3e-3, sem
         torch.cuda.synchronize()
         t_total += time.perf_counter() - t0
         acc = float(((pred > 0.5).float() == lab).float().mean())
-        hist.append((float(loss), acc))
+        hist.append((float(loss.detach()), acc))
     return {"history": hist, "s_per_step": t_total / steps}
 
 

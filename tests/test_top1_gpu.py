@@ -61,13 +61,14 @@ def test_batched_kinship():
 
 
 def test_grid_grows_the_proof_arena():
-    """A 48 x 48 grid: paths of up to ~100 edges, improved many times, need
-    several arena growths (each re-running the step that overflowed)."""
+    """A 48 x 48 grid (paths of up to ~100 edges, improved many times) with an
+    arena of 1,024 free words: it has to grow many times, each growth running
+    the overflowing step again, and the results stay exact."""
     g = W.grid_reach_instance(48)
     src, dst, p = g["edge"]
     inputs = {"edge": ((src, dst), p), "start": (g["start"],)}
-    st, _ = compare(W.REACH_PROGRAM, inputs, "top1_proofs")
-    assert st["proof_words"] > (1 << 22) + 2 * len(src) + 1
+    st, _ = compare(W.REACH_PROGRAM, inputs, "top1_proofs", options={"proof_arena_words": 1024})
+    assert st["proof_words"] > 2 * len(src) + 1 + (1 << 20)
 
 
 def test_paper_example_proof():
