@@ -913,6 +913,45 @@ __global__ void __launch_bounds__(256) k_pwarp_cross(const __grid_constant__ PSt
     const u64 tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
     if (!tot) continue;
     mine += tot;
+    if (tot <= 0xFFFFFFFFull) {
+      // the warp's products fit 32 bits: 32-bit scan values, and the division
+      // u / |B| by a per-row reciprocal m = ceil(2^32 / |B|): umulhi(u, m) is
+      // floor(u / |B|) or one more, fixed by one multiply-compare
+      const u32 ex32 = (u32)ex, tot32 = (u32)tot;
+      const u32 rcp = cb > 1 ? 0xFFFFFFFFu / cb + 1u : 0u;
+      for (u32 t0 = 0; t0 < tot32; t0 += 32) {
+        const u32 t = t0 + (u32)lane;
+        int src = 0;
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+          const u32 e = __shfl_sync(0xFFFFFFFFu, ex32, src + step);
+          if (e <= t) src += step;
+        }
+        const u64 wr = __shfl_sync(0xFFFFFFFFu, wi, src);
+        const u32 la = __shfl_sync(0xFFFFFFFFu, loa, src);
+        const u32 lb = __shfl_sync(0xFFFFFFFFu, lob, src);
+        const u32 nb = __shfl_sync(0xFFFFFFFFu, cb, src);
+        const u32 er = __shfl_sync(0xFFFFFFFFu, ex32, src);
+        const u32 m = __shfl_sync(0xFFFFFFFFu, rcp, src);
+        if (t >= tot32) continue;
+        const u32 u = t - er;
+        u32 i = nb == 1 ? u : __umulhi(u, m);
+        if ((u64)i * nb > u) i--;
+        const u32 j = u - i * nb;
+        const u64 wa = load_word(A.v_keys, A.v_key64, (u64)la + i);
+        const u64 wb = load_word(B.v_keys, B.v_key64, (u64)lb + j);
+        bool ok = true;
+#pragma unroll
+        for (int q = 0; q < NCHKA; q++) ok = ok && ((reg_pick3(aa[q], wr, wa, 0) == reg_pick3(ab[q], wr, wa, 0)) == aeq[q]);
+#pragma unroll
+        for (int q = 0; q < NCHKB; q++) ok = ok && ((reg_pick3(ba[q], wr, wa, wb) == reg_pick3(bb[q], wr, wa, wb)) == beq[q]);
+        u64 w = 0;
+#pragma unroll
+        for (int q = 0; q < NOUT; q++) w |= reg_pick3(out_op[q], wr, wa, wb) << out_sh[q];
+        if (ok) atomicOr(B.bitmap + (w >> 5), 1u << (u32)(w & 31u));
+      }
+      continue;
+    }
     for (u64 t0 = 0; t0 < tot; t0 += 32) {
       const u64 t = t0 + lane;
       int src = 0;
