@@ -616,9 +616,12 @@ def main():
         per_launch_s = v["ms"] / v["launches"] / 1e3
         ach = per_launch_bytes / per_launch_s / 1e9
         outs = sum(cands.values()) / max(v["launches"], 1) if name == "join_emit" else 0
+        traffic = ncu_traffic(name, outs)
         roofline = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(ach / peak, 4), "peak_source": peak_kind,
-                    "algorithmic_bytes_per_launch": per_launch_bytes, "traffic": ncu_traffic(name, outs)}
+                    "algorithmic_bytes_per_launch": per_launch_bytes, "traffic": traffic,
+                    # the same launch time against the DRAM bytes ncu measured (scaled from the small cases)
+                    "traffic_frac": round(traffic / per_launch_s / 1e9 / peak, 4) if traffic else None}
 
     # end to end through the C ABI with host buffers
     e2e = None
