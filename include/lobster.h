@@ -183,7 +183,11 @@ int lob_relation_size(lob_engine* e, uint32_t rel, uint64_t* n);
  *   tags       capacity floats or NULL (all 1 under LOB_UNIT)
  *   sample_ids capacity u32 or NULL
  * If the relation has more than `capacity` facts nothing is written,
- * *n_out receives the size and LOB_E_CAPACITY is returned. */
+ * *n_out receives the size and LOB_E_CAPACITY is returned.  With mem =
+ * LOB_MEM_HOST, buffers that are page-locked and mapped into the device's
+ * address space (cudaHostAlloc, cudaHostRegister; checked at both ends of each
+ * range) are written directly by the read-out kernel over the host link; other
+ * host memory is filled through a device staging buffer and cudaMemcpyAsync. */
 int lob_read_relation(lob_engine* e, uint32_t rel, uint32_t* cols, float* tags, uint32_t* sample_ids,
                       uint64_t capacity, uint64_t* n_out, int mem);
 

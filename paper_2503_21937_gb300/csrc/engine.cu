@@ -2236,6 +2236,27 @@ int lob_relation_size(lob_engine* e, uint32_t rel, uint64_t* n) {
   });
 }
 
+// The device address of host range [p, p + bytes) when the whole range is
+// page-locked memory mapped into the device's address space (checked at both
+// ends, so that it lies in one mapping); nullptr otherwise.
+static void* mapped_range(void* p, u64 bytes) {
+  if (!p || !bytes) return nullptr;
+  cudaPointerAttributes a{}, b{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  char* last = static_cast<char*>(p) + (bytes - 1);
+  if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+    return nullptr;
+  if (static_cast<char*>(b.devicePointer) - static_cast<char*>(a.devicePointer) != (ptrdiff_t)(bytes - 1)) return nullptr;
+  return a.devicePointer;
+}
+
 int lob_read_relation(lob_engine* e, uint32_t rel, uint32_t* cols, float* tags, uint32_t* sample_ids, uint64_t capacity,
                       uint64_t* n_out, int mem) {
   return guarded(e, [&] {
@@ -2253,6 +2274,18 @@ int lob_read_relation(lob_engine* e, uint32_t rel, uint32_t* cols, float* tags, 
     if (mem == LOB_MEM_DEVICE) {
       read_rows(ks, V.lay, V.perm, V.keys.p, V.tags.p, n, cols, capacity, tags, sample_ids, e->stream);
       e->after_launch("read");
+      e->sync();
+      return LOB_OK;
+    }
+    // page-locked, mapped host buffers (cudaHostAlloc, cudaHostRegister): the
+    // read-out kernel writes them directly over the host link, with no device
+    // staging copy
+    u32* dc = static_cast<u32*>(mapped_range(cols, (u64)r.arity * capacity * 4));
+    float* dt = tags ? static_cast<float*>(mapped_range(tags, n * 4)) : nullptr;
+    u32* ds = sample_ids ? static_cast<u32*>(mapped_range(sample_ids, n * 4)) : nullptr;
+    if (dc && (!tags || dt) && (!sample_ids || ds)) {
+      read_rows(ks, V.lay, V.perm, V.keys.p, V.tags.p, n, dc, capacity, dt, ds, e->stream);
+      e->after_launch("read (mapped host)");
       e->sync();
       return LOB_OK;
     }

@@ -618,3 +618,29 @@ def test_hash_index_join(packed):
     e.backward("reach", gout.astype(np.float32), gin)
     e.close()
     np.testing.assert_allclose(gin["edge"], res.vjp({"reach": gout})["edge"], rtol=1e-4, atol=1e-4)
+
+
+def test_read_into_pinned_host_buffers_matches_pageable():
+    """lob_read_relation writes page-locked, mapped host buffers directly from
+    the read-out kernel; the rows equal those read through the staging copy,
+    and a pageable or partly too small buffer still takes the staging path."""
+    import torch
+    from tests.common import engine_run
+    s = W.stream(4711)
+    src, dst, p = s.below(3000, 400), s.below(3000, 400), s.prob(3000)
+    e, st, got = engine_run(W.TC_PROGRAM, {"edge": ((src, dst), p)}, "max_min", read=["path"])
+    n = e.size("path")
+    cols = torch.zeros((2, n + 5), dtype=torch.int32).pin_memory().numpy()
+    tags = torch.zeros(n + 5, dtype=torch.float32).pin_memory().numpy()
+    smp = torch.zeros(n + 5, dtype=torch.int32).pin_memory().numpy()
+    assert e.read_into("path", cols, tags, smp) == n
+    ref = got["path"]
+    assert np.array_equal(cols[:, :n].view(np.uint32), ref.cols)
+    assert np.array_equal(tags[:n], ref.tags)
+    assert np.array_equal(smp[:n].view(np.uint32), ref.samples)
+    # pinned columns with pageable tags: the staging path, same rows
+    tags2 = np.zeros(n + 5, np.float32)
+    cols[:] = 0
+    assert e.read_into("path", cols, tags2, None) == n
+    assert np.array_equal(cols[:, :n].view(np.uint32), ref.cols) and np.array_equal(tags2[:n], ref.tags)
+    e.close()
