@@ -29,6 +29,8 @@
 #include "pjoin.h"
 #include "scan.cuh"
 
+#include <functional>
+
 namespace {
 
 constexpr int kGMaxRels = 16, kGMaxArms = 32, kGMaxSteps = 8, kGMaxViews = 4, kGMaxBefore = 8;
@@ -38,17 +40,18 @@ constexpr int kArmSlots = 1 + kGMaxSteps;
 enum : int { S_K = 0, S_STOP, S_UNUSED, S_OVERFLOW, S_EMITTED, S_NEW, S_ERR, S_ITERS, S_HDR = 8 };
 enum : u64 { STOP_NONE = 0, STOP_FIXPOINT = 1, STOP_MAXITER = 2, STOP_OVERFLOW = 3, STOP_RECORD = 4 };
 // relation slots: |F|, |recent|, unique candidates, then the merge's counts
-// (duplicates, new or improved, error word); view j >= 1 at 8 + 4 (j - 1):
+// (duplicates, new or improved, error word), whether an arm with this head
+// runs in the iteration; view j >= 1 at 8 + 4 (j - 1):
 // rows, duplicates, new, error word
-enum : int { R_FULL = 0, R_RECENT, R_NU, R_DUPS, R_NR, R_MERR };
+enum : int { R_FULL = 0, R_RECENT, R_NU, R_DUPS, R_NR, R_MERR, R_ACTIVE };
 
-constexpr int kGMaxGroups = kGMaxRels * (2 + kGMaxViews);
+
 struct GDesc {
   int nrel, narm;
   u32 max_iters, rec_cap;
   int rel_dense[kGMaxRels];
   int rel_nviews[kGMaxRels];
-  int arm_delta[kGMaxArms], arm_last[kGMaxArms], arm_nbefore[kGMaxArms];
+  int arm_delta[kGMaxArms], arm_last[kGMaxArms], arm_nbefore[kGMaxArms], arm_head[kGMaxArms];
   int arm_before[kGMaxArms][kGMaxBefore];
   // double-buffered groups: per dense relation its primary view, its
   // maintained views (in view-slot order) and its recent set
@@ -90,7 +93,21 @@ __global__ void k_iter_begin(const __grid_constant__ GDesc d, u64* s, u64* rec, 
       const u64* B = s + rel_base(d.arm_before[a][b]);
       if (B[R_FULL] == B[R_RECENT]) active = false;
     }
-    s[arm_base(d.nrel, a)] = active ? D[R_RECENT] : 0;
+    u64* A = s + arm_base(d.nrel, a);
+    A[0] = active ? D[R_RECENT] : 0;
+    // an inactive arm may be skipped by its guard: its step totals read 0
+    if (!active)
+      for (int st = 1; st <= d.arm_last[a]; st++) A[1 + st] = 0;
+  }
+  // a relation whose head arms all stay idle gets no candidates (its section
+  // may be skipped by its guard, leaving R_NU at 0)
+  for (int r = 0; r < d.nrel; r++) {
+    if (!d.rel_dense[r]) continue;
+    u64 any = 0;
+    for (int a = 0; a < d.narm; a++)
+      if (d.arm_head[a] == r && s[arm_base(d.nrel, a)]) any = 1;
+    s[rel_base(r) + R_ACTIVE] = any;
+    s[rel_base(r) + R_NU] = 0;
   }
   if (k <= d.rec_cap)
     for (int r = 0; r < d.nrel; r++) {
@@ -177,6 +194,10 @@ __global__ void k_phase_mark(u64* t, int i) {
 
 __global__ void k_set_cond(const u64* s, cudaGraphConditionalHandle h) {
   if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, s[S_STOP] == STOP_NONE ? 1u : 0u);
+}
+// IF guard of a section of the iteration: run it when state slot i is nonzero
+__global__ void k_set_cond_slot(const u64* s, int i, cudaGraphConditionalHandle h) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, s[i] != 0 ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -272,6 +293,7 @@ void plan_loop(lob_engine& e, GLoop& G, u32 max_iters) {
       G.d.arm_delta[a] = (int)p.ast.body[A.delta].rel;
       G.d.arm_last[a] = (int)A.steps.size() - 1;
       G.d.arm_nbefore[a] = (int)A.before_rels.size();
+      G.d.arm_head[a] = (int)p.ast.head.rel;
       for (size_t b = 0; b < A.before_rels.size(); b++) G.d.arm_before[a][b] = (int)A.before_rels[b];
     }
   G.d.narm = (int)G.arms.size();
@@ -441,8 +463,14 @@ void allocate(lob_engine& e, GLoop& G) {
 }
 
 // One iteration, captured into the stream.  Buffers of derived relations are
-// reached through the pointer table the begin kernel resolves.
-void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaStream_t st) {
+// reached through the pointer table the begin kernel resolves.  With guards
+// (option "loop_guards"), every join arm and every relation's difference+merge
+// section sits in a conditional IF node that runs it only when the arm is
+// active / an arm with that head ran, so an iteration in which most rules
+// have nothing to do launches few kernels; the IF bodies are captured on the
+// second stream `st2`, and their graphs are appended to `bodies`.
+void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaStream_t st0, cudaStream_t st2,
+                       std::vector<cudaGraph_t>& bodies) {
   const int sem = e.semiring, ks = sem_kernel(sem);
   const int sb = stored_bytes(sem), cb = cand_bytes(sem);
   const bool stamps = sem_stamps(sem);
@@ -458,11 +486,53 @@ void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaS
   auto grecent = [&](int r) { return G.d.rel_group[r] + 1 + (int)G.views[r].size(); };
   auto cur = [&](int g) { return res + ptr_slot(g, 0); };
   auto nxt = [&](int g) { return res + ptr_slot(g, 1); };
-  auto mark = [&](const char* name) {  // closes the phase that just ran
+  auto mark_on = [&](const char* name, cudaStream_t s) {  // closes the phase that just ran
     if (!G.timing) return;
-    k_phase_mark<<<1, 32, 0, st>>>(G.times.as<u64>(), name ? phase_id(G, name) : -1);
+    k_phase_mark<<<1, 32, 0, s>>>(G.times.as<u64>(), name ? phase_id(G, name) : -1);
     e.check(cudaGetLastError(), "phase mark");
   };
+  // run body(stream) under an IF node on state slot `cond`, or inline
+  auto guarded = [&](int cond, const std::function<void(cudaStream_t)>& body) {
+    if (!e.opt_loop_guards) {
+      body(st0);
+      return;
+    }
+    cudaStreamCaptureStatus cstat;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t ndeps = 0;
+    e.check(cudaStreamGetCaptureInfo(st0, &cstat, nullptr, &graph, &deps, &edata, &ndeps), "capture info");
+    cudaGraphConditionalHandle h;
+    e.check(cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault), "guard handle");
+    k_set_cond_slot<<<1, 32, 0, st0>>>(st_dev, cond, h);
+    e.check(cudaGetLastError(), "guard condition");
+    e.check(cudaStreamGetCaptureInfo(st0, &cstat, nullptr, &graph, &deps, &edata, &ndeps), "capture info");
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    e.check(cudaGraphAddNode(&node, graph, deps, edata, ndeps, &p), "guard node");
+    e.check(cudaStreamUpdateCaptureDependencies(st0, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+            "capture dependencies");
+    cudaGraph_t ifbody = p.conditional.phGraph_out[0];
+    e.check(cudaStreamBeginCaptureToGraph(st2, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "capture");
+    try {
+      body(st2);
+    } catch (...) {
+      cudaGraph_t dummy;
+      cudaStreamEndCapture(st2, &dummy);
+      cudaGetLastError();
+      throw;
+    }
+    cudaGraph_t done = nullptr;
+    e.check(cudaStreamEndCapture(st2, &done), "end capture");
+    bodies.push_back(ifbody);
+  };
+  cudaStream_t st = st0;
+  auto mark = [&](const char* name) { mark_on(name, st); };
   mark(nullptr);
   k_iter_begin<<<1, 32, 0, st>>>(G.d, st_dev, rec_dev, G.tab.as<void*>(), res);
   e.check(cudaGetLastError(), "iteration begin");
@@ -481,7 +551,8 @@ void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaS
   }
   mark("loop_begin_index");
   // the join arms: every output (+)-added into its head's dense accumulator
-  for (size_t a = 0; a < G.arms.size(); a++) {
+  for (size_t a = 0; a < G.arms.size(); a++) guarded(arm_base(G.d.nrel, (int)a), [&](cudaStream_t st) {
+    auto mark = [&](const char* name) { mark_on(name, st); };
     const RuleAst& R = G.arms[a].rp->ast;
     const ArmPlan& A = *G.arms[a].A;
     const int drel = (int)R.body[A.delta].rel;
@@ -493,7 +564,7 @@ void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaS
     void* const* in_pp = cur(grecent(drel));
     u64 n_cap = G.cap_r[drel];
     const u64* n_dev = slot(ab);
-    int in_packed = 1, side = 0;
+    int side = 0;
     for (size_t s = 1; s < A.steps.size(); s++) {
       const StepPlan& S = A.steps[s];
       const bool last = s + 1 == A.steps.size();
@@ -506,7 +577,6 @@ void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaS
       P.in_pp = in_pp;
       P.n_in = n_cap;
       P.n_in_dev = n_dev;
-      (void)in_packed;
       const bool derived = VR.idb;
       P.v_keys = W.keys.p;
       P.v_key64 = W.lay.key64;
@@ -578,13 +648,14 @@ void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaS
       in_pp = nullptr;
       n_cap = G.cap_bind;
       n_dev = slot(tslot);
-      in_packed = 0;
     }
-  }
+  });
   // per derived relation: unique candidates out of the accumulator, then the
   // difference+merge into F and the secondary views
   for (int r = 0; r < G.d.nrel; r++) {
     if (!G.d.rel_dense[r]) continue;
+    guarded(rel_base(r) + R_ACTIVE, [&](cudaStream_t st) {
+    auto mark = [&](const char* name) { mark_on(name, st); };
     RelSt& H = e.rels[r];
     ViewSt& V = H.views[0];
     const Layout& L = V.lay;
@@ -664,6 +735,7 @@ void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaS
       e.check(cudaGetLastError(), "view merge");
       mark((rtag + "_view_merge").c_str());
     }
+    });
   }
   (void)cb;
   k_iter_end<<<1, 32, 0, st>>>(G.d, st_dev);
@@ -730,6 +802,8 @@ int run_device_loop(lob_engine& e, u32& k, u32 max_iters, lob_stats& s, bool* ta
   // legacy default stream, which cannot be captured) and launched on the engine's
   if (!e.capture_stream) e.check(cudaStreamCreateWithFlags(&e.capture_stream, cudaStreamNonBlocking), "capture stream");
   cudaStream_t cap = e.capture_stream;
+  if (!e.capture_stream2) e.check(cudaStreamCreateWithFlags(&e.capture_stream2, cudaStreamNonBlocking), "capture stream");
+  cudaStream_t cap2 = e.capture_stream2;
   for (int round = 0;; round++) {
     if (round > 64) throw LobError(LOB_E_CUDA, "internal error: device loop capacities did not settle");
     G.d.rec_cap = rec_cap;
@@ -809,9 +883,10 @@ int run_device_loop(lob_engine& e, u32& k, u32 max_iters, lob_stats& s, bool* ta
       e.check(cudaStreamEndCapture(cap, &top), "end capture");
     }
     cudaGraph_t body = wp.conditional.phGraph_out[0];
+    std::vector<cudaGraph_t> if_bodies;
     e.check(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "capture");
     try {
-      capture_iteration(e, G, st_dev, rec_dev, cap);
+      capture_iteration(e, G, st_dev, rec_dev, cap, cap2, if_bodies);
       k_set_cond<<<1, 32, 0, cap>>>(st_dev, hw);
       e.check(cudaGetLastError(), "condition");
     } catch (...) {
@@ -822,7 +897,8 @@ int run_device_loop(lob_engine& e, u32& k, u32 max_iters, lob_stats& s, bool* ta
     }
     cudaGraph_t captured = nullptr;
     e.check(cudaStreamEndCapture(cap, &captured), "end capture");
-    const u64 per_iter = count_kernels(body);
+    u64 per_iter = count_kernels(body);  // guarded sections counted as if they all ran
+    for (cudaGraph_t b : if_bodies) per_iter += count_kernels(b);
     e.check(cudaGraphInstantiate(&gh.x, gh.g, 0), "instantiate");
     e.check(cudaGraphLaunch(gh.x, e.stream), "graph launch");
     std::vector<u64> out(G.n_slots);

@@ -2012,6 +2012,7 @@ void lob_destroy(lob_engine* e) {
   }
   if (e->pool) cudaMemPoolDestroy(e->pool);
   if (e->capture_stream) cudaStreamDestroy(e->capture_stream);
+  if (e->capture_stream2) cudaStreamDestroy(e->capture_stream2);
   cudaFreeHost(e->pinned);
   delete e;
 }
@@ -2524,6 +2525,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     else if (k == "acc_dense" && (value == 0 || value == 1)) e->opt_acc_dense = (int)value;
     else if (k == "acc_bits" && value >= 1 && value <= 30) e->opt_acc_bits = (int)value;
     else if (k == "driver" && value >= 0 && value <= 2) e->opt_driver = (int)value;
+    else if (k == "loop_guards" && (value == 0 || value == 1)) e->opt_loop_guards = (int)value;
     else if (k == "loop_cap_floor" && value >= 256 && value <= (1 << 24)) e->opt_loop_cap_floor = (int)value;
     else if (k == "packed_backward" && (value == 0 || value == 1)) e->opt_packed_backward = (int)value;
     else if (k == "cross_join" && (value == 0 || value == 1)) e->opt_cross_join = (int)value;

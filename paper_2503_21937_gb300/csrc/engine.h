@@ -212,6 +212,8 @@ struct lob_engine {
   std::map<std::string, u64> loop_caps;  // buffer capacities the device loop needed, kept across runs
   u64 host_syncs = 0;             // host waits for the GPU (statistics)
   cudaStream_t capture_stream = nullptr;  // private stream the device loop's graph is captured on (created on first use)
+  cudaStream_t capture_stream2 = nullptr; // second private stream: the bodies of the loop's IF guards
+  int opt_loop_guards = 1;        // device loop: IF nodes skip idle arms and relations
   EngineProfiler prof;
   // run state
   int state = 0;  // 0 loading, 1 ran
