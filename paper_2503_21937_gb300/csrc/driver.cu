@@ -76,7 +76,15 @@ LOB_HD int arm_base(int nrel, int a) { return S_HDR + nrel * kRelSlots + a * kAr
 // Which arms run in the coming iteration (a recent delta relation, and old
 // facts in every derived atom before the delta atom), and the iteration's
 // record of (|F|, |recent|) per relation for the backward pass.
-__global__ void k_iter_begin(const __grid_constant__ GDesc d, u64* s, u64* rec, void* const* tab, void** res) {
+// handles of the IF guards of the iteration's arms and relation sections
+// (on = 0: no guards), set by the begin kernel
+struct GGuards {
+  int on;
+  cudaGraphConditionalHandle arm[kGMaxArms], rel[kGMaxRels];
+};
+
+__global__ void k_iter_begin(const __grid_constant__ GDesc d, u64* s, u64* rec, void* const* tab, void** res,
+                             const __grid_constant__ GGuards gg) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int g = 0; g < d.ngroups; g++) {  // this iteration's current and next buffers of every group
     const int p = (int)(s[d.par_base + g] & 1);
@@ -108,6 +116,11 @@ __global__ void k_iter_begin(const __grid_constant__ GDesc d, u64* s, u64* rec, 
       if (d.arm_head[a] == r && s[arm_base(d.nrel, a)]) any = 1;
     s[rel_base(r) + R_ACTIVE] = any;
     s[rel_base(r) + R_NU] = 0;
+  }
+  if (gg.on) {
+    for (int a = 0; a < d.narm; a++) cudaGraphSetConditional(gg.arm[a], s[arm_base(d.nrel, a)] != 0 ? 1u : 0u);
+    for (int r = 0; r < d.nrel; r++)
+      if (d.rel_dense[r]) cudaGraphSetConditional(gg.rel[r], s[rel_base(r) + R_ACTIVE] != 0 ? 1u : 0u);
   }
   if (k <= d.rec_cap)
     for (int r = 0; r < d.nrel; r++) {
@@ -195,10 +208,7 @@ __global__ void k_phase_mark(u64* t, int i) {
 __global__ void k_set_cond(const u64* s, cudaGraphConditionalHandle h) {
   if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, s[S_STOP] == STOP_NONE ? 1u : 0u);
 }
-// IF guard of a section of the iteration: run it when state slot i is nonzero
-__global__ void k_set_cond_slot(const u64* s, int i, cudaGraphConditionalHandle h) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, s[i] != 0 ? 1u : 0u);
-}
+
 
 // ---------------------------------------------------------------------------
 // host side
@@ -491,9 +501,23 @@ void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaS
     k_phase_mark<<<1, 32, 0, s>>>(G.times.as<u64>(), name ? phase_id(G, name) : -1);
     e.check(cudaGetLastError(), "phase mark");
   };
-  // run body(stream) under an IF node on state slot `cond`, or inline
-  auto guarded = [&](int cond, const std::function<void(cudaStream_t)>& body) {
-    if (!e.opt_loop_guards) {
+  // the guards' handles, created on the graph being captured before the begin
+  // kernel that sets them
+  GGuards gg{};
+  gg.on = e.opt_loop_guards;
+  if (gg.on) {
+    cudaStreamCaptureStatus cstat;
+    cudaGraph_t graph = nullptr;
+    e.check(cudaStreamGetCaptureInfo(st0, &cstat, nullptr, &graph, nullptr, nullptr, nullptr), "capture info");
+    for (int a = 0; a < G.d.narm; a++)
+      e.check(cudaGraphConditionalHandleCreate(&gg.arm[a], graph, 0, cudaGraphCondAssignDefault), "guard handle");
+    for (int r = 0; r < G.d.nrel; r++)
+      if (G.d.rel_dense[r])
+        e.check(cudaGraphConditionalHandleCreate(&gg.rel[r], graph, 0, cudaGraphCondAssignDefault), "guard handle");
+  }
+  // run body(stream) under the IF node of handle h, or inline
+  auto guarded = [&](cudaGraphConditionalHandle h, const std::function<void(cudaStream_t)>& body) {
+    if (!gg.on) {
       body(st0);
       return;
     }
@@ -502,11 +526,6 @@ void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaS
     const cudaGraphNode_t* deps = nullptr;
     const cudaGraphEdgeData* edata = nullptr;
     size_t ndeps = 0;
-    e.check(cudaStreamGetCaptureInfo(st0, &cstat, nullptr, &graph, &deps, &edata, &ndeps), "capture info");
-    cudaGraphConditionalHandle h;
-    e.check(cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault), "guard handle");
-    k_set_cond_slot<<<1, 32, 0, st0>>>(st_dev, cond, h);
-    e.check(cudaGetLastError(), "guard condition");
     e.check(cudaStreamGetCaptureInfo(st0, &cstat, nullptr, &graph, &deps, &edata, &ndeps), "capture info");
     cudaGraphNodeParams p = {};
     p.type = cudaGraphNodeTypeConditional;
@@ -534,7 +553,7 @@ void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaS
   cudaStream_t st = st0;
   auto mark = [&](const char* name) { mark_on(name, st); };
   mark(nullptr);
-  k_iter_begin<<<1, 32, 0, st>>>(G.d, st_dev, rec_dev, G.tab.as<void*>(), res);
+  k_iter_begin<<<1, 32, 0, st>>>(G.d, st_dev, rec_dev, G.tab.as<void*>(), res, gg);
   e.check(cudaGetLastError(), "iteration begin");
   for (auto& gi : G.indexes) {
     RelSt& R = e.rels[gi.rel];
@@ -551,7 +570,7 @@ void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaS
   }
   mark("loop_begin_index");
   // the join arms: every output (+)-added into its head's dense accumulator
-  for (size_t a = 0; a < G.arms.size(); a++) guarded(arm_base(G.d.nrel, (int)a), [&](cudaStream_t st) {
+  for (size_t a = 0; a < G.arms.size(); a++) guarded(gg.arm[a], [&](cudaStream_t st) {
     auto mark = [&](const char* name) { mark_on(name, st); };
     const RuleAst& R = G.arms[a].rp->ast;
     const ArmPlan& A = *G.arms[a].A;
@@ -654,7 +673,7 @@ void capture_iteration(lob_engine& e, GLoop& G, u64* st_dev, u64* rec_dev, cudaS
   // difference+merge into F and the secondary views
   for (int r = 0; r < G.d.nrel; r++) {
     if (!G.d.rel_dense[r]) continue;
-    guarded(rel_base(r) + R_ACTIVE, [&](cudaStream_t st) {
+    guarded(gg.rel[r], [&](cudaStream_t st) {
     auto mark = [&](const char* name) { mark_on(name, st); };
     RelSt& H = e.rels[r];
     ViewSt& V = H.views[0];
