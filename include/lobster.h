@@ -271,6 +271,12 @@ int lob_reset(lob_engine* e);
  *                  2: as 1 without waiting for recorded sizes (the buffers
  *                  start from estimates and grow); 0: the host drives
  *                  every iteration                                   (default 1)
+ *   "loop_guards"  1: inside the device-driven loop, every join arm and
+ *                  every relation's difference+merge section sits under a
+ *                  conditional IF node set by the iteration's first kernel,
+ *                  so arms without a recent delta and relations without
+ *                  candidates launch nothing; 0: every section launches
+ *                  each iteration and exits early on empty input  (default 1)
  *   "loop_cap_floor" smallest row capacity the device-driven loop plans its
  *                  buffers with before they grow (256..2^24, default 65536;
  *                  small values exercise the regrowth path)
