@@ -116,6 +116,9 @@ __global__ void k_iter_begin(const __grid_constant__ GDesc d, u64* s, u64* rec, 
       if (d.arm_head[a] == r && s[arm_base(d.nrel, a)]) any = 1;
     s[rel_base(r) + R_ACTIVE] = any;
     s[rel_base(r) + R_NU] = 0;
+    // the counts an empty difference+merge would report, so that the end
+    // kernel's capacity checks do not read the last active iteration's
+    if (!any) s[rel_base(r) + R_DUPS] = s[rel_base(r) + R_NR] = 0;
   }
   if (gg.on) {
     for (int a = 0; a < d.narm; a++) cudaGraphSetConditional(gg.arm[a], s[arm_base(d.nrel, a)] != 0 ? 1u : 0u);
