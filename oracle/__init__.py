@@ -22,6 +22,11 @@ Parity status per function (pins are in ``tests/test_oracle_pins.py``):
   * computed heads and filters    -- pinned (bounded walk lengths by boolean
                                      matrix powers; wrap-around, division,
                                      reserved value by direct u32 arithmetic)
+  * strata run one after another  -- pinned (sums over every path of a chain's
+                                     closure, mutually recursive odd/even
+                                     lengths, widest paths by Floyd-Warshall,
+                                     rules written in reverse order, finite
+                                     differences)
 """
 from __future__ import annotations
 

@@ -13,6 +13,10 @@
 //                      evaluated over F_k, of (x) of the tags of g's body facts
 //   stop when an iteration changes nothing.
 //
+// The rules are split into strata (see stratify below), and the strata run one
+// after another, each iterated to its fixpoint over the database the earlier
+// strata left (Algorithm 1's loop over the strata of a RAM program).
+//
 // This is naive (not semi-naive) evaluation: every grounding over the whole
 // database is enumerated in every iteration, which is the textbook definition
 // of the least fixpoint.  How T(h) enters F_{k+1} depends on the semiring:
@@ -466,6 +470,92 @@ bool tag_equal(int sr, const Tag& a, const Tag& b) {
 }
 
 // ---------------------------------------------------------------------------
+// strata (Sec. 3.1: a RAM program is a sequence of strata, run one after
+// another, each to its own fixpoint; Algorithm 1's outer loop)
+// ---------------------------------------------------------------------------
+// The paper's front-end hands the engine its strata without saying how they
+// are formed.  Reading: the textbook stratification of a positive program.  A
+// relation that heads some rule is derived; a derived relation h depends on
+// every derived relation in the body of a rule with head h.  The strata are the
+// strongly connected components of that graph -- relations that depend on each
+// other, directly or through others, share one -- ordered so that a component
+// comes after every component it depends on; each rule goes to its head's.
+// Among components that are ready at the same point, the one whose first rule
+// comes first in the program goes first.
+std::vector<std::vector<size_t>> stratify(const std::vector<Rule>& rules) {
+  std::vector<std::string> derived;  // in order of first appearance as a head
+  for (const Rule& r : rules)
+    if (std::find(derived.begin(), derived.end(), r.head.rel) == derived.end()) derived.push_back(r.head.rel);
+  const size_t n = derived.size();
+  auto id = [&](const std::string& name) -> int {
+    for (size_t i = 0; i < n; i++)
+      if (derived[i] == name) return (int)i;
+    return -1;
+  };
+  // reach[a][b]: a depends on b through one or more rules
+  std::vector<std::vector<char>> reach(n, std::vector<char>(n, 0));
+  for (const Rule& r : rules)
+    for (const Atom& a : r.body) {
+      const int b = id(a.rel);
+      if (b >= 0) reach[id(r.head.rel)][b] = 1;
+    }
+  for (size_t m = 0; m < n; m++)  // transitive closure (Warshall)
+    for (size_t a = 0; a < n; a++)
+      if (reach[a][m])
+        for (size_t b = 0; b < n; b++)
+          if (reach[m][b]) reach[a][b] = 1;
+  // component of a relation: itself and every relation it is mutually reachable with
+  std::vector<int> comp(n, -1);
+  int ncomp = 0;
+  for (size_t a = 0; a < n; a++) {
+    if (comp[a] >= 0) continue;
+    comp[a] = ncomp;
+    for (size_t b = a + 1; b < n; b++)
+#if ORACLE_MUTANT == 18  // mutant: mutually recursive relations get separate strata
+      if (false && reach[a][b] && reach[b][a]) comp[b] = ncomp;
+#else
+      if (reach[a][b] && reach[b][a]) comp[b] = ncomp;
+#endif
+    ncomp++;
+  }
+  // order: a component is placed once every component it depends on is placed
+  std::vector<int> order;
+  std::vector<char> placed(ncomp, 0);
+  while ((int)order.size() < ncomp) {
+    const size_t before = order.size();
+    for (int c = 0; c < ncomp; c++) {
+      if (placed[c]) continue;
+      bool ready = true;
+      for (size_t a = 0; a < n && ready; a++)
+        if (comp[a] == c)
+          for (size_t b = 0; b < n; b++)
+            if (reach[a][b] && comp[b] != c && !placed[comp[b]]) ready = false;
+      if (!ready) continue;
+      placed[c] = 1;
+      order.push_back(c);
+      break;  // rescan from the first component, so ties go to program order
+    }
+    if (order.size() == before)  // no component ready: a dependency cycle across components
+      for (int c = 0; c < ncomp; c++)  // (impossible unless mutant 18 split a component)
+        if (!placed[c]) {
+          placed[c] = 1;
+          order.push_back(c);
+          break;
+        }
+  }
+#if ORACLE_MUTANT == 17  // mutant: strata run in reverse dependency order
+  std::reverse(order.begin(), order.end());
+#endif
+  std::vector<std::vector<size_t>> strata;
+  for (int c : order) {
+    strata.emplace_back();
+    for (size_t i = 0; i < rules.size(); i++)
+      if (comp[id(rules[i].head.rel)] == c) strata.back().push_back(i);
+  }
+  return strata;
+}
+
+// ---------------------------------------------------------------------------
 // naive fixpoint for one database (one sample)
 // ---------------------------------------------------------------------------
 using Relation = std::map<Tuple, Tag>;
@@ -562,16 +652,37 @@ struct Engine {
     rec(0);
   }
 
-  // returns 0 on fixpoint, -2 when max_iters iterations did not reach it
+  // Runs the strata in order, each to its fixpoint (Algorithm 1); max_iters
+  // bounds the iterations of all strata together.  Returns 0 on fixpoint, -2
+  // when max_iters iterations did not reach it.
   int run(uint32_t max_iters) {
+#if ORACLE_MUTANT == 19  // mutant: one loop over every rule, strata ignored
+    std::vector<std::vector<size_t>> strata(1);
+    for (size_t i = 0; i < rules.size(); i++) strata[0].push_back(i);
+#else
+    const std::vector<std::vector<size_t>> strata = stratify(rules);
+#endif
+    uint32_t used = 0;
+    for (const auto& stratum : strata) {
+      const int rc = run_stratum(stratum, max_iters, used);
+      if (rc) return rc;
+    }
+    return 0;
+  }
+
+  // One stratum: iterate its rules over the whole database until an iteration
+  // changes nothing.  `used` counts the iterations run so far.
+  int run_stratum(const std::vector<size_t>& stratum, uint32_t max_iters, uint32_t& used) {
 #if ORACLE_MUTANT == 9  // mutant: max-min keeps the first tag of a key (key policy)
     const bool key_policy = (sr == ADD_MULT || sr == DIFF_ADD_MULT || sr == MAX_MIN);
 #else
     const bool key_policy = (sr == ADD_MULT || sr == DIFF_ADD_MULT);
 #endif
-    for (uint32_t it = 0; it < max_iters; it++) {
+    for (uint32_t it = 0; used < max_iters; it++) {
+      used++;
       std::map<std::string, std::map<Tuple, Acc>> derived;
-      for (const Rule& r : rules) {
+      for (size_t ri : stratum) {
+        const Rule& r = rules[ri];
         auto& out = derived[r.head.rel];
         const Relation* existing = nullptr;
         auto e = db.find(r.head.rel);
@@ -607,7 +718,7 @@ struct Engine {
           }
         }
       }
-      iterations = (int)it + 1;
+      iterations = (int)used;
 #if ORACLE_MUTANT == 8  // mutant: stops after the second iteration
       if (it == 1) return 0;
 #endif

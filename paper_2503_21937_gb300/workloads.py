@@ -316,4 +316,17 @@ ANDERSEN_PROGRAM = ("pt(p,a) :- addr(p,a).\n"
                     "pt(p,o) :- load(p,q), pt(q,r), pt(r,o).\n"
                     "pt(r,o) :- store(p,q), pt(p,r), pt(q,o).\n")
 
+# Programs of several strata (Sec. 3.1: a RAM program is a sequence of strata).
+# LAYERED: the closure, then the nodes with a successor, then pairs two or more
+# hops apart from such a node -- three strata, the last reading both below it.
+LAYERED_PROGRAM = (TC_PROGRAM +
+                   "src(x) :- path(x,y).\n"
+                   "far(x,z) :- src(x), path(x,y), path(y,z), x != z.\n")
+# ODD_EVEN: odd and even path lengths are mutually recursive (one stratum of two
+# relations), and cnt reads even from the stratum above.
+ODD_EVEN_PROGRAM = ("odd(x,y) :- edge(x,y).\n"
+                    "odd(x,z) :- even(x,y), edge(y,z).\n"
+                    "even(x,z) :- odd(x,y), edge(y,z).\n"
+                    "cnt(x) :- even(x,y).\n")
+
 SEMIRINGS = {"unit": 0, "max_min": 1, "add_mult": 2, "diff_max_min": 3, "diff_add_mult": 4}

@@ -27,6 +27,9 @@ MUTANTS = {
     14: "top-1-proofs (+) keeps the less likely proof",
     15: "'<' admits equality",
     16: "subtraction with its operands swapped",
+    17: "strata run in reverse dependency order",
+    18: "mutually recursive relations split into separate strata",
+    19: "one loop over every rule, strata ignored",
 }
 
 

@@ -598,3 +598,118 @@ def test_arithmetic_wraps_and_drops():
     assert rel_set(r.relation("pred")) == {((a - 1) % M,) for a, b in pairs if a != 0}  # 2^32-1 is reserved
     assert rel_set(r.relation("big")) == {(a,) for a, b in pairs
                                           if (a + b) % M > (b * 2) % M and ((a - b) % M) // 2 >= 1}
+
+
+# ----------------------------------------------------------------------------
+# strata (Sec. 3.1; Algorithm 1's loop over the strata of a program): each
+# stratum runs to its fixpoint before the next one reads its relations
+# ----------------------------------------------------------------------------
+
+def _chain(n, seed):
+    """Chain 0 -> 1 -> ... -> n-1 with probabilities below 1/2, so that sums of
+    path products stay below 1 (no clamp), and its path products P[x][y]."""
+    a = np.arange(n - 1, dtype=np.uint32)
+    p = W.stream(seed).prob(n - 1).astype(np.float64) * 0.5
+    P = {}
+    for x in range(n):
+        v = 1.0
+        for y in range(x + 1, n):
+            v *= p[y - 1]
+            P[x, y] = v
+    return (a, a + 1), p, P
+
+
+@pytest.mark.parametrize("reverse", [False, True])
+def test_strata_projection_sums_every_path_of_the_closure(reverse):
+    """out(x) :- path(x,y) in the stratum above the closure: on a chain every
+    path fact has one derivation (the product of its edges), and out(x) sums
+    all of them -- min(1, sum_{y > x} P[x][y]) -- because the closure is complete
+    before out is derived.  Rules written above the rules they read must give
+    the same result."""
+    n = 9
+    cols, p, P = _chain(n, 6100)
+    rules = [W.TC_PROGRAM, "out(x) :- path(x,y).\n"]
+    prog = "".join(reversed(rules) if reverse else rules)
+    r = oracle.run(prog, {"edge": (cols, p)}, "add_mult")
+    path = {tuple(c): t for c, t in zip(r.relation("path").cols.T.tolist(), r.relation("path").tags)}
+    assert set(path) == set(P)
+    for k in P:
+        assert path[k] == pytest.approx(P[k], rel=1e-12)
+    out = {int(c): t for c, t in zip(r.relation("out").cols[0], r.relation("out").tags)}
+    assert set(out) == set(range(n - 1))
+    for x in range(n - 1):
+        want = min(1.0, sum(P[x, y] for y in range(x + 1, n)))
+        assert out[x] == pytest.approx(want, rel=1e-12)
+
+
+def test_strata_mutually_recursive_relations_share_one_stratum():
+    """odd/even path lengths depend on each other, so they are evaluated
+    together; cnt(x) :- even(x,y) above them sums every even-length path of
+    the chain: min(1, sum over y - x even >= 2 of P[x][y])."""
+    n = 10
+    cols, p, P = _chain(n, 6200)
+    r = oracle.run(W.ODD_EVEN_PROGRAM, {"edge": (cols, p)}, "add_mult")
+    odd = {tuple(c): t for c, t in zip(r.relation("odd").cols.T.tolist(), r.relation("odd").tags)}
+    even = {tuple(c): t for c, t in zip(r.relation("even").cols.T.tolist(), r.relation("even").tags)}
+    assert set(odd) == {k for k in P if (k[1] - k[0]) % 2 == 1}
+    assert set(even) == {k for k in P if (k[1] - k[0]) % 2 == 0}
+    for k, t in list(odd.items()) + list(even.items()):
+        assert t == pytest.approx(P[k], rel=1e-12)
+    cnt = {int(c): t for c, t in zip(r.relation("cnt").cols[0], r.relation("cnt").tags)}
+    assert set(cnt) == set(range(n - 2))
+    for x in range(n - 2):
+        want = min(1.0, sum(P[x, y] for y in range(x + 2, n, 2)))
+        assert cnt[x] == pytest.approx(want, rel=1e-12)
+
+
+def test_strata_three_layers_sum_over_middle_vertices():
+    """LAYERED on a chain: src(x) = sum_y P[x][y]; far(x,z) sums, over the middle
+    vertices x < y < z, src(x) * P[x][y] * P[y][z] = src(x) * (z - x - 1) *
+    P[x][z], clamped to 1."""
+    n = 8
+    cols, p, P = _chain(n, 6300)
+    r = oracle.run(W.LAYERED_PROGRAM, {"edge": (cols, p)}, "add_mult")
+    src = {x: min(1.0, sum(P[x, y] for y in range(x + 1, n))) for x in range(n - 1)}
+    far = {tuple(c): t for c, t in zip(r.relation("far").cols.T.tolist(), r.relation("far").tags)}
+    want = {(x, z): min(1.0, src[x] * (z - x - 1) * P[x, z]) for x in range(n) for z in range(x + 2, n)}
+    assert set(far) == set(want)
+    for k in want:
+        assert far[k] == pytest.approx(want[k], rel=1e-12)
+
+
+def test_strata_maxmin_reads_the_widest_paths():
+    """max-min: q(x,z) :- path(x,y), hop(y,z) above the closure is
+    max_y min(W[x][y], hop(y,z)) with W the widest-path (max over paths of the
+    smallest edge) matrix from Floyd-Warshall."""
+    s = W.stream(6400)
+    n, m = 8, 18
+    a, b = W.erdos_renyi(n, m, seed_index=6401)
+    pe = s.prob(len(a)).astype(np.float32).astype(np.float64)
+    ha, hb = s.below(6, n), s.below(6, n)
+    keep = np.unique(np.stack([ha, hb]), axis=1)
+    ha, hb = keep[0].astype(np.uint32), keep[1].astype(np.uint32)
+    ph = s.prob(len(ha)).astype(np.float32).astype(np.float64)
+    Wm = np.zeros((n, n))
+    for x, y, t in zip(a, b, pe):
+        Wm[x, y] = max(Wm[x, y], t)
+    for k in range(n):
+        Wm = np.maximum(Wm, np.minimum(Wm[:, k:k + 1], Wm[k:k + 1, :]))
+    prog = W.TC_PROGRAM + "q(x,z) :- path(x,y), hop(y,z).\n"
+    r = oracle.run(prog, {"edge": ((a, b), pe), "hop": ((ha, hb), ph)}, "max_min")
+    want = {}
+    for x in range(n):
+        for y, z, t in zip(ha, hb, ph):
+            if Wm[x, y] > 0:
+                want[x, int(z)] = max(want.get((x, int(z)), 0.0), min(Wm[x, y], t))
+    got = {tuple(c): t for c, t in zip(r.relation("q").cols.T.tolist(), r.relation("q").tags)}
+    assert want and got == want
+
+
+def test_strata_gradient_matches_finite_differences():
+    a, b = W.erdos_renyi(12, 26, seed_index=6500)
+    p = W.stream(6501).prob(len(a)).astype(np.float64) * 0.3
+    inputs = {"edge": ((a, b), p)}
+    n_out = oracle.run(W.LAYERED_PROGRAM, inputs, "add_mult").relation("far").cols.shape[1]
+    assert n_out > 10
+    gout = W.stream(6502).normal(n_out)
+    _fd_check(W.LAYERED_PROGRAM, inputs, "far", "diff_add_mult", gout, range(len(a)))
