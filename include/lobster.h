@@ -85,6 +85,8 @@ typedef struct lob_stats {
   uint32_t device_iterations; /* iterations run by the device-driven loop (option "driver") */
   uint32_t graph_launches;  /* launches of that loop's graph (1 unless a buffer had to grow) */
   uint64_t proof_words;     /* top-1-proofs: u32 words of the proof arena in use at the end */
+  uint32_t strata;          /* strata run one after another (1: one loop over every rule) */
+  uint32_t reserved;
 } lob_stats;
 
 /* Create an engine on the current CUDA device.  `alloc` may be NULL (stream-
@@ -132,14 +134,21 @@ int lob_add_rule(lob_engine* e, const char* text);
  * with the semi-naive arms of the appendix's Join rule).  At most max_iters
  * iterations run; on LOB_E_MAXITER the partial state stays readable.  A second
  * call needs lob_reset first (LOB_E_STATE).  `stats` may be NULL.
- * With option "driver" = 1 (default), a tagged run whose derived relations all
- * use dense accumulation and whose recursive rules are packed join pipelines
- * runs its iterations after the first as one CUDA graph: a conditional WHILE
- * node around two iterations (buffer sets 0 -> 1, then 1 -> 0 under an IF
- * node), every size and the stop decision held in device memory, and no host
- * wait between iterations; buffers that turn out too small end the graph
- * early, grow, and the graph is launched again from the last committed
- * iteration. */
+ * Strata (Sec. 3.1; Algorithm 1's loop over the strata of a program): derived
+ * relations that depend on one another form a component, and a component runs
+ * after every component it reads.  Under the add-mult and top-1-proofs
+ * semirings the strata run one after another, each to its own fixpoint, and
+ * every fact of the database is recent when a stratum starts; under unit,
+ * max-min and diff-max-min, whose least fixpoint does not depend on that
+ * order, every rule runs in one loop.  stats->strata gives the count.
+ * With option "driver" = 1 (default), a tagged run of one stratum whose
+ * derived relations all use dense accumulation and whose recursive rules are
+ * packed join pipelines runs its iterations after the first as one CUDA
+ * graph: a conditional WHILE node around one iteration, per-relation double
+ * buffers chosen through a device pointer table, every size and the stop
+ * decision held in device memory, and no host wait between iterations;
+ * buffers that turn out too small end the graph early, grow, and the graph is
+ * launched again from the last committed iteration. */
 int lob_run_to_fixpoint(lob_engine* e, int semiring, uint32_t max_iters, lob_stats* stats);
 
 /* Options chosen by lob_autotune and the timings behind them. */

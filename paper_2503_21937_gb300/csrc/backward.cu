@@ -12,7 +12,8 @@
 //   reverse: all adjoints flowing into a fact of iteration k come from facts of
 //   later iterations, so they are complete when iteration k is replayed.  Each
 //   replay re-runs iteration k's semi-naive arms on the final relations with
-//   stamp filters (delta = stamp k-1, full = stamp < k, old = stamp < k-1),
+//   stamp filters (delta = stamp k-1, full = stamp < k, old = stamp < k-1;
+//   when k begins a stratum after the first, delta = stamp < k: every fact),
 //   recomputing the groundings instead of storing them, and pushes
 //   adjoint(h) * (product of the other tags) to every body fact with FP64
 //   atomics.  Loaded facts finally pass their adjoints to the caller's input
@@ -303,6 +304,19 @@ void fill_filters_b(const RuleAst& R, const std::vector<int>& fs, FilterP* out, 
   }
 }
 
+// The stamp filter that selects iteration k's recent set from a relation's
+// facts: those first derived in iteration k - 1, or, when k begins a stratum
+// after the first (every fact recent), all facts derived before k.
+void set_delta_stamps(const lob_engine& e, u32 k, int& mode, u32& val) {
+  if (begins_stratum(e.stratum_begin, k)) {
+    mode = STAMP_LT;
+    val = k;
+  } else {
+    mode = STAMP_EQ;
+    val = k - 1;
+  }
+}
+
 void replay_arm(lob_engine& e, BwdState& S, const RulePlan& rp, const ArmPlan& A, u32 k) {
   const RuleAst& R = rp.ast;
   RelSt& D = e.rels[R.body[A.delta].rel];
@@ -317,8 +331,7 @@ void replay_arm(lob_engine& e, BwdState& S, const RulePlan& rp, const ArmPlan& A
   std::copy(A.steps[0].act, A.steps[0].act + kMaxArity, P.in_act);
   P.in_tags = DV.tags.p;
   P.in_stamp = DV.stamps.as<u32>();
-  P.in_stamp_mode = STAMP_EQ;
-  P.in_stamp_val = k - 1;
+  set_delta_stamps(e, k, P.in_stamp_mode, P.in_stamp_val);
   P.n_in = DV.n;
   fill_filters_b(R, A.steps[0].filters, P.in_filters, P.n_in_filters);
   P.out_lay = HV.lay;
@@ -504,10 +517,9 @@ bool replay_arm_packed(lob_engine& e, BwdState& S, const RulePlan& rp, const Arm
     P.in_words = in_words;
     P.in_tags = nullptr;
     P.n_in = n_in;
-    if (s == 1) {  // the delta atom: facts first derived in iteration k - 1
+    if (s == 1) {  // the delta atom: the recent set of iteration k
       P.in_stamp = DV.stamps.as<u32>();
-      P.in_stamp_mode = STAMP_EQ;
-      P.in_stamp_val = k - 1;
+      set_delta_stamps(e, k, P.in_stamp_mode, P.in_stamp_val);
     } else {
       P.in_stamp_mode = STAMP_NONE;
     }
@@ -686,8 +698,10 @@ int backward_impl(lob_engine* e, u32 out_rel, const float* grad_tags, float* con
             for (auto& a : p.ast.body)
               if (!needed[a.rel]) needed[a.rel] = grew = true;
       }
-      // facts first derived in iteration k (the recent set at the start of k + 1)
+      // facts first derived in iteration k (the recent set at the start of k + 1,
+      // unless k + 1 began a stratum: then iteration k, its stratum's last, found none)
       auto new_in = [&](u32 k, u32 rel) -> u64 {
+        if (begins_stratum(e->stratum_begin, k + 1)) return 0;
         return k < e->iter_counts.size() ? e->iter_counts[k][rel].second : e->rels[rel].n_recent;
       };
       for (u32 k = e->last_iter; k >= 1; k--) {
@@ -700,8 +714,10 @@ int backward_impl(lob_engine* e, u32 out_rel, const float* grad_tags, float* con
                                                                       S.hnew[q].as<u32>());
           e->after_launch("new heads");
         }
+        const int stratum = stratum_of_iter(e->stratum_begin, k);
         for (auto& p : e->plans)
           for (auto& A : p.arms) {
+            if (p.stratum != stratum) continue;  // the rule did not run in iteration k
             if (!needed[p.ast.head.rel] || !new_in(k, p.ast.head.rel)) continue;  // no adjoint can flow here
             const auto& cnt = e->iter_counts[k - 1];  // (total, recent) per relation at the start of iteration k
             if (!cnt[p.ast.body[A.delta].rel].second) continue;

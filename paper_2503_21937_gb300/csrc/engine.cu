@@ -562,6 +562,50 @@ static void compile_cross(lob_engine& e, const RuleAst& R, const ArmPlan& A, Pac
   out.cross_ok = true;
 }
 
+// Strata (Sec. 3.1: a RAM program is a sequence of strata; Algorithm 1 runs
+// each to its fixpoint before the next).  Derived relations that depend on one
+// another, directly or through others, form a component; a component's level
+// is 0 when its rules read no derived relation outside it, else one more than
+// the highest level among the components they read.  Components of one level
+// never read each other, so they share a stratum (one semi-naive loop); the
+// levels run in increasing order.  Only semirings whose result depends on that
+// order (sem_strata) are split; the others keep every rule in one loop.
+static void assign_strata(lob_engine& e, int sem) {
+  e.n_strata = 1;
+  for (auto& p : e.plans) p.stratum = 0;
+  if (!sem_strata(sem)) return;
+  const size_t n = e.rels.size();
+  std::vector<std::vector<char>> dep(n, std::vector<char>(n, 0));  // dep[h][b]: h reads b
+  for (auto& p : e.plans)
+    for (auto& a : p.ast.body)
+      if (e.rels[a.rel].idb) dep[p.ast.head.rel][a.rel] = 1;
+  for (size_t m = 0; m < n; m++)
+    for (size_t h = 0; h < n; h++)
+      if (dep[h][m])
+        for (size_t b = 0; b < n; b++) dep[h][b] |= dep[m][b];
+  std::vector<int> level(n, 0);
+  for (size_t round = 0; round <= n; round++) {
+    bool changed = false;
+    for (size_t h = 0; h < n; h++) {
+      if (!e.rels[h].idb) continue;
+      int lv = 0;
+      for (size_t b = 0; b < n; b++)
+        if (dep[h][b] && !dep[b][h]) lv = std::max(lv, level[b] + 1);  // b lies in a lower component
+      for (size_t b = 0; b < n; b++)  // the component shares one level
+        if (dep[h][b] && dep[b][h]) lv = std::max(lv, level[b]);
+      if (lv != level[h]) {
+        level[h] = lv;
+        changed = true;
+      }
+    }
+    if (!changed) break;
+  }
+  for (auto& p : e.plans) {
+    p.stratum = level[p.ast.head.rel];
+    e.n_strata = std::max(e.n_strata, p.stratum + 1);
+  }
+}
+
 static void prepare(lob_engine& e, int sem) {
   release_derived(e);
   e.semiring = sem;
@@ -619,6 +663,7 @@ static void prepare(lob_engine& e, int sem) {
     for (size_t i = 0; i < R.body.size(); i++) p.arms.push_back(plan_arm(e, R, (int)i, idem));
     e.plans.push_back(std::move(p));
   }
+  assign_strata(e, sem);
   // A secondary view is merged every iteration only if an arm whose delta
   // relation can have recent facts after iteration 1 (a rule head) probes it;
   // arms whose delta is a plain input relation run in iteration 1 only.  The
@@ -1814,6 +1859,25 @@ static void enable_dense(lob_engine& e) {
   }
 }
 
+// Start of a stratum after the first: the recent set of every relation is the
+// whole relation (its primary view's keys and tags).
+static void all_recent(lob_engine& e) {
+  const int sb = stored_bytes(e.semiring);
+  for (auto& r : e.rels) {
+    ViewSt& V = r.views[0];
+    if (r.keys_stale) throw LobError(LOB_E_STATE, "internal error: stratum start without materialised keys");
+    r.n_recent = V.n;
+    if (!V.n) continue;
+    const int kb = V.lay.key64 ? 8 : 4;
+    e.ensure(r.rkeys, V.n * kb);
+    e.check(cudaMemcpyAsync(r.rkeys.p, V.keys.p, V.n * kb, cudaMemcpyDeviceToDevice, e.stream), "recent keys");
+    if (sb) {
+      e.ensure(r.rtags, V.n * sb);
+      e.check(cudaMemcpyAsync(r.rtags.p, V.tags.p, V.n * sb, cudaMemcpyDeviceToDevice, e.stream), "recent tags");
+    }
+  }
+}
+
 static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   if (e.state != 0) throw LobError(LOB_E_STATE, "run_to_fixpoint was already called; call lob_reset first");
   if (sem < 0 || sem > 6) throw LobError(LOB_E_ARG, "unknown semiring id");
@@ -1842,6 +1906,8 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   e.cand_emitted = 0;
   e.check(cudaMemsetAsync(sort_err(e), 0, sizeof(u32), e.stream), "sort error word");
   e.check(cudaMemsetAsync(e.counts.as<u64>() + 13, 0, sizeof(u64), e.stream), "emitted counter");
+  e.stratum_begin.clear();
+  int stratum = 0;  // the stratum being run (assign_strata)
   for (;;) {
     if (k >= max_iters) { rc = LOB_E_MAXITER; break; }
     k++;
@@ -1851,6 +1917,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
     for (auto& r : e.rels) choose_dedup_mode(e, r);
     for (auto& r : e.rels) r.n_cand = 0;
     for (auto& p : e.plans) {
+      if (p.stratum != stratum) continue;
       for (auto& A : p.arms) {
         if (!e.rels[p.ast.body[A.delta].rel].n_recent) continue;
         bool skip = false;  // an atom before the delta atom has no old facts
@@ -1875,8 +1942,16 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
       r.n_next = 0;
     }
     s.new_facts += total_new;
-    if (!total_new) break;
-    if (k == 1) {  // the rest of the run as a device-driven graph, when it qualifies
+    if (!total_new) {
+      if (stratum + 1 >= e.n_strata) break;
+      // the next stratum starts as Algorithm 1 starts one: every fact of the
+      // database is recent, so its first iteration joins over all of them
+      stratum++;
+      all_recent(e);
+      e.stratum_begin.push_back(k + 1);
+      continue;
+    }
+    if (k == 1 && e.n_strata == 1) {  // the rest of the run as a device-driven graph, when it qualifies
       bool taken = false;
       const int r2 = run_device_loop(e, k, max_iters, s, &taken);
       if (taken) {
@@ -1904,6 +1979,7 @@ static int run_fixpoint(lob_engine& e, int sem, u32 max_iters, lob_stats* st) {
   s.kernel_launches = e.launches;
   s.host_syncs = e.host_syncs - syncs0;
   s.proof_words = e.arena_tail;
+  s.strata = (u32)e.n_strata;
   e.stats = s;
   e.last_iter = k;
   e.state = 1;

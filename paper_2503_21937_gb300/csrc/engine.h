@@ -151,6 +151,7 @@ struct ArmPlan {
 struct RulePlan {
   RuleAst ast;
   std::vector<ArmPlan> arms;
+  int stratum = 0;  // the stratum its head belongs to (0 when the run uses one loop)
 };
 
 struct ProfAgg {
@@ -227,6 +228,10 @@ struct lob_engine {
   DevBuf bind[2][kMaxSlots + 2];  // binding tables (cols..., sample, tags) ping-pong
   DevBuf bfact[2][2 * kMaxArity];  // backward: per carried body fact, its row and tag
   std::vector<std::vector<std::pair<u64, u64>>> iter_counts;  // per iteration: (|F|, |recent|) per relation
+  // strata of the current run (1: one loop over every rule), and the
+  // iterations that begin a stratum after the first (every fact recent)
+  int n_strata = 1;
+  std::vector<u32> stratum_begin;
   u64* pinned = nullptr;           // host readback slots
   // top-1-proofs: the proof arena (u32 words), its tail and error word
   // (top1_state[0], [1]) and the probability of every input-fact id
@@ -268,6 +273,23 @@ inline bool sem_idempotent(int sem) {
   return sem == SR_UNIT || sem == SR_MAX_MIN || sem == SR_DIFF_MAX_MIN || sem_top1(sem);
 }
 inline bool sem_stamps(int sem) { return sem == SR_ADD_MULT || sem == SR_DIFF_ADD_MULT; }
+// Semirings whose result can depend on running the strata one after another:
+// add-mult's tags are fixed when a key first appears, and a top-1 proof kept
+// by the improvement policy can rest on a body fact's earlier, since replaced
+// proof.  Under unit, max-min and diff-max-min ((+) and (x) a distributive
+// lattice) one loop over every rule reaches the same least fixpoint.
+inline bool sem_strata(int sem) { return sem_stamps(sem) || sem_top1(sem); }
+// the stratum that iteration k belongs to
+inline int stratum_of_iter(const std::vector<u32>& begin, u32 k) {
+  int s = 0;
+  for (u32 b : begin) s += b <= k;
+  return s;
+}
+inline bool begins_stratum(const std::vector<u32>& begin, u32 k) {
+  for (u32 b : begin)
+    if (b == k) return true;
+  return false;
+}
 inline int sem_kernel(int sem) {
   return sem == SR_DIFF_ADD_MULT ? SR_ADD_MULT : (sem == SR_DIFF_TOP1 ? SR_TOP1 : sem);
 }

@@ -49,7 +49,7 @@ class Stats(ctypes.Structure):
                 ("candidates", ctypes.c_uint64), ("new_facts", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
                 ("ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64), ("host_syncs", ctypes.c_uint64),
                 ("device_iterations", ctypes.c_uint32), ("graph_launches", ctypes.c_uint32),
-                ("proof_words", ctypes.c_uint64)]
+                ("proof_words", ctypes.c_uint64), ("strata", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
