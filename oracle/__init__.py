@@ -56,7 +56,7 @@ def build(force: bool = False) -> str:
     """Compile oracle.cpp into liboracle.so (g++, no GPU code)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", f"-DORACLE_MUTANT={_MUTANT}", "-o", tmp, _SRC],
+        subprocess.run(["g++", "-O2", "-std=c++17", "-pthread", "-shared", "-fPIC", f"-DORACLE_MUTANT={_MUTANT}", "-o", tmp, _SRC],
                        check=True)
         os.replace(tmp, _LIB)
     return _LIB

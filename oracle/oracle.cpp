@@ -76,8 +76,10 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 #ifndef ORACLE_MUTANT
@@ -102,11 +104,13 @@ struct Tag {
 };
 
 std::string g_err;
-// top-1-proofs state of the current run
+// top-1-proofs state of the current run: the probabilities are set before any
+// sample runs and only read afterwards; the overflow flag and the tie count
+// belong to the thread running a sample
 std::vector<double> g_prob;  // input-fact id -> probability
 uint32_t g_proof_cap = 300;
-bool g_proof_overflow = false;
-uint64_t g_ties = 0;
+thread_local bool g_proof_overflow = false;
+thread_local uint64_t g_ties = 0;
 
 // probability of a proof: FP64 product in ascending id order, rounded to f32
 double proof_prob(const std::vector<uint32_t>& proof) {
@@ -816,28 +820,76 @@ int orc_run(const char* program, int semiring, int n_inputs, const char* const* 
     base += nrows[k];
   }
   if (loaded.empty()) loaded[0];
+  if (g_proof_overflow) {  // a loaded proof alone is longer than the cap
+    delete res;
+    g_err = "a proof is longer than the proof cap";
+    return -5;
+  }
+  // Samples never join, so each one is its own fixpoint; they run on separate
+  // threads (one sample at a time per thread), and the results are gathered
+  // in sample order, as a loop over the samples would produce them.
+  struct SampleRun {
+    uint32_t sample;
+    std::map<std::string, std::map<Tuple, Acc>>* facts;
+    Database db;
+    int rc = 0, iterations = 0;
+    bool overflow = false;
+    uint64_t ties = 0;
+  };
+  const uint64_t load_ties = g_ties;  // ties met while merging duplicate loaded rows
+  std::vector<SampleRun> runs;
+  for (auto& smp : loaded) runs.push_back({smp.first, &smp.second, {}, 0, 0, false, 0});
+  size_t next = 0;
+  std::mutex mu;
+  auto worker = [&]() {
+    for (;;) {
+      size_t i;
+      {
+        std::lock_guard<std::mutex> lock(mu);
+        if (next >= runs.size()) return;
+        i = next++;
+      }
+      SampleRun& sr = runs[i];
+      g_proof_overflow = false;
+      g_ties = 0;
+      Engine e(semiring, rules);
+      for (auto& rel : *sr.facts)
+        for (auto& kv : rel.second) e.db[rel.first][kv.first] = acc_value(semiring, kv.second);
+      sr.rc = e.run(max_iters);
+      sr.iterations = e.iterations;
+      sr.overflow = g_proof_overflow;
+      sr.ties = g_ties;
+      sr.db = std::move(e.db);
+    }
+  };
+  const size_t n_threads = std::min<size_t>(runs.size(), std::max(1u, std::thread::hardware_concurrency()));
+  if (n_threads <= 1) {
+    worker();
+  } else {
+    std::vector<std::thread> pool;
+    for (size_t t = 0; t < n_threads; t++) pool.emplace_back(worker);
+    for (auto& t : pool) t.join();
+  }
   int max_it = 0;
-  for (auto& smp : loaded) {
-    Engine e(semiring, rules);
-    for (auto& rel : smp.second)
-      for (auto& kv : rel.second) e.db[rel.first][kv.first] = acc_value(semiring, kv.second);
-    int rc = e.run(max_iters);
-    if (g_proof_overflow) {
+  uint64_t ties = load_ties;
+  for (auto& sr : runs) {
+    if (sr.overflow) {
       delete res;
       g_err = "a proof is longer than the proof cap";
       return -5;
     }
-    if (rc != 0) {
+    if (sr.rc != 0) {
       delete res;
       g_err = "max_iters reached";
-      return rc;
+      return sr.rc;
     }
-    max_it = std::max(max_it, e.iterations);
-    for (auto& rel : e.db) res->out[rel.first][smp.first] = std::move(rel.second);
+    max_it = std::max(max_it, sr.iterations);
+    ties += sr.ties;
+    for (auto& rel : sr.db) res->out[rel.first][sr.sample] = std::move(rel.second);
   }
   res->iterations = max_it;
   res->prob = g_prob;
-  res->ties = g_ties;
+  res->ties = ties;
   *result = res;
   return 0;
 }

@@ -51,6 +51,27 @@ def closure_count_scipy(src, dst, n_nodes):
     return total
 
 
+def closure_keys_scipy(src, dst, n_nodes):
+    """Transitive closure as sorted uint64 keys (x << 32 | y), one scipy BFS per
+    source; (s, s) belongs to it when a successor of s reaches back to s."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import breadth_first_order
+    g = sp.csr_matrix((np.ones(len(src)), (np.asarray(src, np.int64), np.asarray(dst, np.int64))),
+                      shape=(n_nodes, n_nodes))
+    gt = g.T.tocsr()
+    parts = []
+    for s in range(n_nodes):
+        if g.indptr[s + 1] == g.indptr[s]:
+            continue
+        order = breadth_first_order(g, s, directed=True, return_predecessors=False)
+        reach = order[1:].astype(np.uint64)
+        back = gt.indices[gt.indptr[s]:gt.indptr[s + 1]]
+        if np.isin(back, order).any():
+            reach = np.append(reach, np.uint64(s))
+        parts.append((np.uint64(s) << np.uint64(32)) | reach)
+    return np.sort(np.concatenate(parts)) if parts else np.zeros(0, np.uint64)
+
+
 def same_generation_closed_form(depth):
     """|sg| on a tree: ordered pairs of distinct nodes at equal depth >= 1."""
     nd = np.bincount(depth)

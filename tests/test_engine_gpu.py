@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 from paper_2503_21937_gb300 import workloads as W
+from tests import pins
 from tests.common import compare, engine_run, oracle_run
 
 pytestmark = pytest.mark.gpu
@@ -20,17 +21,41 @@ def _built():
 # unit semiring
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n", [2, 3, 65, 700])
+def _closure_against_bfs(a, b, n_nodes):
+    """Unit TC where the naive oracle would take minutes: the engine's path
+    relation, element by element, against the per-source BFS closure (the
+    textbook computation the oracle is pinned to)."""
+    e, st, got = engine_run(W.TC_PROGRAM, {"edge": ((a, b),)}, read=["path"])
+    e.close()
+    x, y = got["path"].cols.astype(np.uint64)
+    keys = (x << np.uint64(32)) | y
+    assert np.all(keys[1:] > keys[:-1])  # sorted distinct facts, read order
+    assert np.array_equal(keys, pins.closure_keys_scipy(a, b, n_nodes))
+    return st
+
+
+@pytest.mark.parametrize("n", [2, 3, 65])
 def test_tc_chain(n):
     a, b = W.ktree_chain(n)
     st, _ = compare(W.TC_PROGRAM, {"edge": ((a, b),)})
     assert st["derived"] == n * (n - 1) // 2
 
 
-@pytest.mark.parametrize("n,m,seed", [(40, 80, 1), (300, 900, 2), (2000, 5000, 3)])
+def test_tc_long_chain():
+    """700 iterations, one new fact per source and iteration."""
+    st = _closure_against_bfs(*W.ktree_chain(700), 700)
+    assert st["derived"] == 700 * 699 // 2
+
+
+@pytest.mark.parametrize("n,m,seed", [(40, 80, 1), (300, 900, 2)])
 def test_tc_random(n, m, seed):
     a, b = W.erdos_renyi(n, m, seed_index=100 + seed)
     compare(W.TC_PROGRAM, {"edge": ((a, b),)})
+
+
+def test_tc_random_2000_nodes():
+    a, b = W.erdos_renyi(2000, 5000, seed_index=103)
+    _closure_against_bfs(a, b, 2000)
 
 
 def test_tc_config1_full_size():
@@ -46,7 +71,7 @@ def test_sg_random_tree():
 
 def test_tc_power_law_small():
     s, d = W.chung_lu_power_law(1500, 6000, seed_index=23)
-    compare(W.TC_PROGRAM, {"edge": ((s, d),)})
+    _closure_against_bfs(s, d, 1500)
 
 
 def test_andersen_small():

@@ -52,6 +52,19 @@ def test_tc_matches_bfs_on_random_graphs():
         assert rel_set(r.relation("path")) == pins.bfs_closure(a, b)
 
 
+def test_scipy_closure_keys_equal_the_bfs_closure():
+    """The vectorised closure the large engine checks use is the same set as
+    the per-source BFS that pins the oracle."""
+    for n, m, seed in [(30, 60, 14), (300, 700, 15), (100, 900, 16)]:
+        a, b = W.erdos_renyi(n, m, seed_index=seed)
+        keys = pins.closure_keys_scipy(a, b, n)
+        assert np.all(keys[1:] > keys[:-1])
+        want = pins.bfs_closure(a, b)
+        assert {(int(k >> 32), int(k & 0xFFFFFFFF)) for k in keys} == want
+    keys = pins.closure_keys_scipy(*W.ktree_chain(50), 50)
+    assert len(keys) == 50 * 49 // 2
+
+
 def test_sg_tree_depth_closed_form():
     parent, child, depth = W.random_tree(600, seed_index=21)
     r = oracle.run(W.SG_PROGRAM, {"parent": ((parent, child),)})
