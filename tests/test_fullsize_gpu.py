@@ -144,27 +144,23 @@ def test_batched_512_samples_sampled_against_oracle(semiring):
     samples = _spread_samples(B["sides"])
     assert B["sides"][samples].min() == 8 and B["sides"][samples].max() == 48
     exact = semiring == "diff_max_min"
-    for smp in samples:
-        me, mf = e_[3] == smp, f[4] == smp
-        single = {"edge": ((e_[0][me], e_[1][me]), e_[2][me]), "start": ((np.array([0], np.uint32),),)}
-        res = oracle_run(W.REACH_PROGRAM, single, semiring)
-        want = res.relation("reach")
-        m = reach.samples == smp
-        assert np.array_equal(reach.cols[:, m], want.cols), smp
+    # the chosen samples in one oracle call: the oracle runs every sample as its
+    # own fixpoint (pinned by test_batched_equals_per_sample), and its results
+    # come sorted by sample, then tuple, as the engine reads them
+    me, mf, ms, mc = (np.isin(x, samples) for x in (e_[3], f[4], st[2], c[4]))
+    res = oracle_run(W.REACH_PROGRAM, {"edge": ((e_[0][me], e_[1][me]), e_[2][me], e_[3][me]),
+                                       "start": ((st[0][ms],), None, st[2][ms])}, semiring)
+    resk = oracle_run(W.KIN_PROGRAM, {"fact": ((f[0][mf], f[1][mf], f[2][mf]), f[3][mf], f[4][mf]),
+                                      "comp": ((c[0][mc], c[1][mc], c[2][mc]), None, c[4][mc])}, semiring)
+    for out, res_, rel, g_out, inp, m_in in (("reach", res, reach, g_reach, "edge", me), ("kin", resk, kin, g_kin, "fact", mf)):
+        want = res_.relation(out)
+        assert sorted(set(want.samples.tolist())) == samples, out
+        m = np.isin(rel.samples, samples)
+        assert np.array_equal(rel.samples[m], want.samples), out
+        assert np.array_equal(rel.cols[:, m], want.cols), out
         if exact:
-            assert np.array_equal(reach.tags[m], want.tags.astype(np.float32)), smp
+            assert np.array_equal(rel.tags[m], want.tags.astype(np.float32)), out
         else:
-            np.testing.assert_allclose(reach.tags[m], want.tags, rtol=1e-5, atol=0, err_msg=str(smp))
-        gw = res.vjp({"reach": g_reach[m].astype(np.float64)})["edge"]
-        np.testing.assert_allclose(gin["edge"][me], gw, rtol=1e-4, atol=1e-4, err_msg=str(smp))
-        singlek = {"fact": ((f[0][mf], f[1][mf], f[2][mf]), f[3][mf]), "comp": (W.composition_table(),)}
-        resk = oracle_run(W.KIN_PROGRAM, singlek, semiring)
-        wk = resk.relation("kin")
-        mk = kin.samples == smp
-        assert np.array_equal(kin.cols[:, mk], wk.cols), smp
-        if exact:
-            assert np.array_equal(kin.tags[mk], wk.tags.astype(np.float32)), smp
-        else:
-            np.testing.assert_allclose(kin.tags[mk], wk.tags, rtol=1e-5, atol=0, err_msg=str(smp))
-        gk = resk.vjp({"kin": g_kin[mk].astype(np.float64)})["fact"]
-        np.testing.assert_allclose(gin["fact"][mf], gk, rtol=1e-4, atol=1e-4, err_msg=str(smp))
+            np.testing.assert_allclose(rel.tags[m], want.tags, rtol=1e-5, atol=0, err_msg=out)
+        gw = res_.vjp({out: g_out[m].astype(np.float64)})[inp]
+        np.testing.assert_allclose(gin[inp][m_in], gw, rtol=1e-4, atol=1e-4, err_msg=out)
