@@ -247,7 +247,8 @@ def andersen_sparse(addr, assign, load, store, n_vars):
     Ad, As, Ld, St = mat(addr), mat(assign), mat(load), mat(store)
     P = boolify(Ad)
     while True:
-        nxt = boolify(Ad + As @ P + Ld @ (P @ P) + P.T @ (St @ P))
+        # products grouped so that the few-row statement matrices go first
+        nxt = boolify(Ad + As @ P + boolify(Ld @ P) @ P + P.T @ boolify(St @ P))
         if nxt.nnz == P.nnz:
             return nxt
         P = nxt

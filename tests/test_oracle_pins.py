@@ -65,6 +65,17 @@ def test_scipy_closure_keys_equal_the_bfs_closure():
     assert len(keys) == 50 * 49 // 2
 
 
+def test_sparse_matrix_andersen_matches_the_worklist_solver():
+    """The boolean sparse-matrix fixpoint that checks the full-size Andersen
+    run computes the same points-to set as the worklist solver pinned above."""
+    for nv, ns, seed in [(3000, 8000, 31), (20000, 100000, 34)]:
+        A = W.andersen_program(nv, ns, seed_index=seed)
+        P = pins.andersen_sparse(A["addr"], A["assign"], A["load"], A["store"], nv).tocoo()
+        got = set(zip(P.row.tolist(), P.col.tolist()))
+        assert len(got) > 1000
+        assert got == pins.andersen_worklist(A["addr"], A["assign"], A["load"], A["store"])
+
+
 def test_sg_tree_depth_closed_form():
     parent, child, depth = W.random_tree(600, seed_index=21)
     r = oracle.run(W.SG_PROGRAM, {"parent": ((parent, child),)})
