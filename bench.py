@@ -242,6 +242,19 @@ def cpu_checkers(andersen: bool = False) -> dict:
     return out
 
 
+def side_leg(name: str, fn):
+    """Run one of the secondary measurements (per-config lines, batched,
+    pathfinder, CPU checkers).  They are taken after the headline; if one of
+    them fails, the JSON line still carries the headline and reports the
+    failure in that leg's place instead of being lost."""
+    try:
+        return fn()
+    except Exception as exc:  # reported in the line, with the traceback on stderr
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{name}: {type(exc).__name__}: {exc}"}
+
+
 def max_over_ranks(ms: float, dist=None, device: str = "cuda") -> float:
     """The job's time: the slowest rank's (all_reduce MAX); `ms` itself when
     there is one process."""
@@ -656,21 +669,23 @@ def main():
 
     configs = None
     if not args.no_configs:
-        configs = config_legs()
+        configs = side_leg("configs", config_legs)
     batched = None
     if not args.no_batched:
-        batched = batched_fwd_bwd()
+        batched = side_leg("batched", batched_fwd_bwd)
     pathfinder = None
     if not args.no_pathfinder:
-        from paper_2503_21937_gb300 import pathfinder as PF
-        pathfinder = {"metric": "training-step samples/s (CNN edge predictor -> batched differentiable fixpoint -> "
-                                "BCE -> backward -> Adam), synthetic Pathfinder-like grids",
-                      "by_side": PF.sweep(semiring="diff_max_min"),
-                      "by_side_diff_top1_proofs": PF.sweep(semiring="diff_top1_proofs")}
+        def pathfinder_leg():
+            from paper_2503_21937_gb300 import pathfinder as PF
+            return {"metric": "training-step samples/s (CNN edge predictor -> batched differentiable fixpoint -> "
+                              "BCE -> backward -> Adam), synthetic Pathfinder-like grids",
+                    "by_side": PF.sweep(semiring="diff_max_min"),
+                    "by_side_diff_top1_proofs": PF.sweep(semiring="diff_top1_proofs")}
+        pathfinder = side_leg("pathfinder", pathfinder_leg)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample()
-        cpu["checkers"] = cpu_checkers(andersen=args.cpu_andersen)
+        cpu["checkers"] = side_leg("checkers", lambda: cpu_checkers(andersen=args.cpu_andersen))
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

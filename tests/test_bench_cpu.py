@@ -48,3 +48,14 @@ def test_single_process_value():
     import bench
     assert bench.max_over_ranks(12.5) == 12.5
     assert bench.job_throughput(10, 3, 1, 30.0) == pytest.approx(1000.0)
+
+
+def test_a_failing_side_leg_is_reported_in_its_place():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.side_leg("ok", lambda: {"v": 1}) == {"v": 1}
+
+    def boom():
+        raise RuntimeError("no such kernel")
+    got = bench.side_leg("batched", boom)
+    assert got == {"error": "batched: RuntimeError: no such kernel"}
