@@ -158,6 +158,7 @@ typedef struct lob_tune_report {
   double first_ms;  /* median run time with the options in force when called */
   double best_ms;   /* median run time with the chosen options */
   int32_t acc_dense, cross_join;
+  int32_t hash_slots;  /* hash index: slots per view row at least (option "hash_slots") */
 } lob_tune_report;
 
 /* Autotuner for the loaded program (not part of the paper's method).  It picks
@@ -167,6 +168,8 @@ typedef struct lob_tune_report {
  *   - packed_join: packed-word vs general join steps;
  *   - join_index: dense offset table vs binary search vs hash table (the join
  *     strategy: offset-table / hash probes vs sorted-merge search);
+ *   - hash_slots: the hash table's size per view row (2 or 4, the load
+ *     factor of Sec. 5.1's index), when the hash index was kept;
  *   - radix_bits: the sort's digit width;
  *   - for the tagged semirings acc_dense (dense (+)-accumulation vs sorted
  *     candidates);
@@ -232,8 +235,10 @@ int lob_reset(lob_engine* e);
  *                  search; 1 dense up to 30 bits; 2 binary search; 3 a hash
  *                  table of the view's distinct join prefixes (open
  *                  addressing, linear probing, each slot holding the
- *                  prefix's first row and row count; 2 slots per row at
- *                  most)                                             (default 0)
+ *                  prefix's first row and row count)               (default 0)
+ *   "hash_slots"   hash index size: the smallest power of two of at least
+ *                  this many slots per view row, 2, 4 or 8 (load factor at
+ *                  most 1/2, 1/4, 1/8; 16 bytes a slot)              (default 2)
  *   "dense_bits"   largest join-prefix width, in bits, indexed densely (default 24)
  *   "radix_bits"   bits per radix-sort pass: 4, 6 or 8 (other values
  *                  in 4..11 select 8)                                (default 8)

@@ -9,9 +9,11 @@
 //      their tag improves, for idempotent (+)), merges the rest into F and
 //      writes them as the next recent set; secondary sorted views of the
 //      relation receive the same new facts;
-//   3. stop when no relation has recent facts.
+//   3. stop when no relation has recent facts; a program of several strata
+//      runs them in order, each to this stop (assign_strata).
 #include <algorithm>
 #include <cstring>
+#include <functional>
 
 #include "engine.h"
 #include "scan.cuh"
@@ -900,9 +902,10 @@ static void ensure_index(lob_engine& e, ViewSt& v, int prefix) {
   if (e.opt_join_index == 1) dense = dbits <= 30;
   if (e.opt_join_index >= 2) dense = false;
   if (e.opt_join_index == 3 && v.n < (1ull << 31)) {
-    // hash index of the view's distinct prefixes (Sec. 5.1), load factor <= 1/2
+    // hash index of the view's distinct prefixes (Sec. 5.1): at least
+    // opt_hash_slots slots per row, so the load factor is at most 1 / opt_hash_slots
     int bits = 4;
-    while ((1ull << bits) < 2 * std::max<u64>(v.n, 1)) bits++;
+    while ((1ull << bits) < (u64)e.opt_hash_slots * std::max<u64>(v.n, 1)) bits++;
     I.mode = INDEX_HASH;
     I.hash_bits = bits;
     I.domain = 1ull << bits;
@@ -2216,6 +2219,7 @@ namespace {
 struct TuneKnob {
   int* field;
   std::vector<int> values;
+  std::function<bool()> active;  // null: always searched
 };
 }  // namespace
 
@@ -2223,8 +2227,12 @@ static int autotune(lob_engine& e, int sem, u32 max_iters, u32 repeats, lob_tune
   if (e.state != 0) throw LobError(LOB_E_STATE, "autotune a loaded engine before lob_run_to_fixpoint");
   if (sem < 0 || sem > 6) throw LobError(LOB_E_ARG, "unknown semiring id");
   if (!repeats) repeats = 1;
-  std::vector<TuneKnob> knobs = {{&e.opt_packed_join, {1, 0}}, {&e.opt_join_index, {0, 1, 2, 3}},
-                                 {&e.opt_radix_bits, {8, 6}}};
+  // the hash table's size (Sec. 5.1's load factor) is searched only when the
+  // hash index has been kept
+  std::vector<TuneKnob> knobs = {{&e.opt_packed_join, {1, 0}, nullptr},
+                                 {&e.opt_join_index, {0, 1, 2, 3}, nullptr},
+                                 {&e.opt_hash_slots, {2, 4}, [&e] { return e.opt_join_index == 3; }},
+                                 {&e.opt_radix_bits, {8, 6}, nullptr}};
   if (sem == SR_UNIT) {
     knobs.push_back({&e.opt_warp_join, {1, 2, 0}});
     knobs.push_back({&e.opt_bitmap_delta, {1, 2, 0}});
@@ -2266,6 +2274,7 @@ static int autotune(lob_engine& e, int sem, u32 max_iters, u32 repeats, lob_tune
     const double first = score();
     double best = first;
     for (auto& k : knobs) {
+      if (k.active && !k.active()) continue;
       const int cur = *k.field;
       int keep = cur;
       for (int v : k.values) {
@@ -2288,6 +2297,7 @@ static int autotune(lob_engine& e, int sem, u32 max_iters, u32 repeats, lob_tune
       rep->emit_filter = e.opt_emit_filter;
       rep->acc_dense = e.opt_acc_dense;
       rep->cross_join = e.opt_cross_join;
+      rep->hash_slots = e.opt_hash_slots;
       rep->trials = trials;
       rep->first_ms = first;
       rep->best_ms = best;
@@ -2588,6 +2598,7 @@ int lob_set_option(lob_engine* e, const char* key, int64_t value) {
     if (!key) throw LobError(LOB_E_ARG, "null key");
     std::string k = key;
     if (k == "join_index" && value >= 0 && value <= 3) e->opt_join_index = (int)value;
+    else if (k == "hash_slots" && (value == 2 || value == 4 || value == 8)) e->opt_hash_slots = (int)value;
     else if (k == "dense_bits" && value >= 1 && value <= 30) e->opt_dense_bits = (int)value;
     else if (k == "radix_bits" && value >= 4 && value <= 11) e->opt_radix_bits = sort_supported_radix_bits((int)value);
     else if (k == "sync_check" && (value == 0 || value == 1)) e->opt_sync_check = (int)value;

@@ -195,6 +195,7 @@ struct lob_engine {
   std::vector<RulePlan> plans;
   // options
   int opt_join_index = 0, opt_dense_bits = 24, opt_radix_bits = 8, opt_sync_check = 0, opt_profile = 0;
+  int opt_hash_slots = 2;         // hash index: slots per view row at least (load factor <= 1 / opt_hash_slots)
   u64 opt_max_cand = 1ull << 30;  // candidates sorted at once (bounds every sort below 2^32 keys)
   int opt_emit_filter = 1;        // unit semiring: membership bitmap at emission when duplicates dominate
   int opt_sort_algo = 0;          // 0: reduce-then-scan passes, 1: one kernel per pass with look-back

@@ -67,7 +67,7 @@ class TuneReport(ctypes.Structure):
     _fields_ = [("packed_join", ctypes.c_int32), ("warp_join", ctypes.c_int32), ("bitmap_delta", ctypes.c_int32),
                 ("join_index", ctypes.c_int32), ("radix_bits", ctypes.c_int32), ("emit_filter", ctypes.c_int32),
                 ("trials", ctypes.c_uint32), ("first_ms", ctypes.c_double), ("best_ms", ctypes.c_double),
-                ("acc_dense", ctypes.c_int32), ("cross_join", ctypes.c_int32)]
+                ("acc_dense", ctypes.c_int32), ("cross_join", ctypes.c_int32), ("hash_slots", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -326,8 +326,9 @@ def test_autotune_then_run_matches_oracle():
     e.program(W.TC_PROGRAM)
     e.load("edge", (s, d))
     rep = e.autotune("unit", repeats=1)
-    # the first setting + every alternative of 7 knobs (join_index: offset table, 30-bit table, search, hash)
-    assert rep["trials"] >= 1 + 1 + 3 + 1 + 2 + 2 + 2 + 1
+    # the first setting + every alternative of 7 knobs (join_index: offset table, 30-bit table, search, hash;
+    # the hash table's size only when the hash index was kept)
+    assert rep["trials"] >= 1 + 1 + 3 + 1 + 2 + 2 + 2 + 1 + (1 if rep["join_index"] == 3 else 0)
     assert rep["join_index"] in (0, 1, 2, 3) and rep["cross_join"] in (0, 1)
     assert 0 < rep["best_ms"] <= rep["first_ms"]
     assert rep["warp_join"] in (0, 1, 2) and rep["bitmap_delta"] in (0, 1, 2) and rep["radix_bits"] in (6, 8)
@@ -345,8 +346,10 @@ def test_autotune_then_run_matches_oracle():
     e.load("edge", (src, dst), np.asarray(p, np.float32))
     e.load("start", g["start"])
     rep = e.autotune("max_min", repeats=1)
-    # semirings with tags tune packed_join, join_index, radix_bits and acc_dense
-    assert rep["trials"] == 1 + 1 + 3 + 1 + 1
+    # semirings with tags tune packed_join, join_index, radix_bits and acc_dense,
+    # and the hash table's size when the hash index was kept
+    assert rep["trials"] == 1 + 1 + 3 + 1 + 1 + (1 if rep["join_index"] == 3 else 0)
+    assert rep["hash_slots"] in (2, 4)
     e.run("max_min")
     want = oracle_run(W.REACH_PROGRAM, inputs, "max_min").relation("reach")
     got = e.read("reach")
