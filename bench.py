@@ -204,8 +204,8 @@ def cpu_checkers(andersen: bool = False) -> dict:
     """Full-size textbook computations of the benchmark's relations on the host:
     the same-generation closed form (sum over tree levels of n_d (n_d - 1)), the
     transitive closure by one BFS per source on every host core, the oracle on
-    the 1,000-node / 3,000-edge Erdos-Renyi closure, and (optionally, about two
-    minutes) Andersen points-to as a boolean sparse-matrix fixpoint."""
+    the 1,000-node / 3,000-edge Erdos-Renyi closure, and (optionally, under a
+    minute) Andersen points-to as a boolean sparse-matrix fixpoint."""
     import multiprocessing as mp
     import numpy as np
     out = {}
