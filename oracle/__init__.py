@@ -26,7 +26,8 @@ Parity status per function (pins are in ``tests/test_oracle_pins.py``):
                                      closure, mutually recursive odd/even
                                      lengths, widest paths by Floyd-Warshall,
                                      rules written in reverse order, finite
-                                     differences)
+                                     differences, a top-1 proof that reads
+                                     the stratum below when it is finished)
 """
 from __future__ import annotations
 

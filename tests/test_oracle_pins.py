@@ -737,3 +737,23 @@ def test_strata_gradient_matches_finite_differences():
     assert n_out > 10
     gout = W.stream(6502).normal(n_out)
     _fd_check(W.LAYERED_PROGRAM, inputs, "far", "diff_add_mult", gout, range(len(a)))
+
+
+def test_top1_strata_read_the_finished_proofs_of_the_stratum_below():
+    """top-1-proofs under strata: h(y) :- r(y), s(y) sits above r and s, so it
+    reads their final proofs.  r(2) first gets the proof {e(0,2)} (0.5), then the
+    likelier {e(0,1), e(1,2)} (0.81); s(2) has {e(0,2)}.  Run after r and s are
+    complete, h(2) = their union {e(0,1), e(1,2), e(0,2)} = 0.9 * 0.9 * 0.5;
+    h(1) = {e(0,1)} = 0.9.  (One loop over every rule would have kept the union
+    with r(2)'s first proof, {e(0,2)} = 0.5.)"""
+    prog = ("r(x) :- start(x).\n"
+            "r(y) :- r(x), e(x,y).\n"
+            "s(y) :- e(0,y).\n"
+            "h(y) :- r(y), s(y).\n")
+    e = (np.array([0, 1, 0], np.uint32), np.array([1, 2, 2], np.uint32))
+    p = np.array([0.9, 0.9, 0.5])
+    r = oracle.run(prog, {"e": (e, p), "start": ((np.array([0], np.uint32),),)}, "top1_proofs")
+    assert r.ties == 0
+    rel = r.relation("h")
+    got = {int(c): (t, pr.tolist()) for c, t, pr in zip(rel.cols[0], rel.tags.tolist(), r.proofs("h"))}
+    assert got == {1: (_f32(0.9), [0]), 2: (_f32(0.9 * 0.9 * 0.5), [0, 1, 2])}
