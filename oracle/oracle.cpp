@@ -60,7 +60,8 @@
 // such expressions with ==, !=, <, <=, >, >= (unsigned); see Expr below.
 //
 // Batched inputs (Sec. 4.3): facts carry a sample id and samples never join; the
-// oracle states that directly by running the fixpoint once per sample.
+// oracle states that directly by running the fixpoint once per sample (the
+// samples on separate threads, their results gathered in sample order).
 //
 // ORACLE_MUTANT (default 0, the oracle itself): a positive value compiles one
 // deliberate, plausible mistake into a separate library, so that
