@@ -757,3 +757,27 @@ def test_top1_strata_read_the_finished_proofs_of_the_stratum_below():
     rel = r.relation("h")
     got = {int(c): (t, pr.tolist()) for c, t, pr in zip(rel.cols[0], rel.tags.tolist(), r.proofs("h"))}
     assert got == {1: (_f32(0.9), [0]), 2: (_f32(0.9 * 0.9 * 0.5), [0, 1, 2])}
+
+
+def test_strata_keep_loaded_facts_of_a_derived_relation():
+    """add-mult, out(x) :- path(x,y) above the closure of a chain, with out(0)
+    also loaded (tag 0.25): a loaded key keeps its tag (first appearance), the
+    other keys sum every path of the closure, and a sample of its own runs its
+    own strata (the same program on a second, shorter chain)."""
+    n = 7
+    cols, p, P = _chain(n, 6600)
+    prog = W.TC_PROGRAM + "out(x) :- path(x,y).\n"
+    a, b = cols
+    m = 4  # sample 1: the chain's first m nodes
+    edge = ((np.concatenate([a, a[:m - 1]]), np.concatenate([b, b[:m - 1]])),
+            np.concatenate([p, p[:m - 1]]), np.concatenate([np.zeros(n - 1, np.uint32), np.ones(m - 1, np.uint32)]))
+    out_in = ((np.array([0], np.uint32),), np.array([0.25]), np.array([0], np.uint32))
+    r = oracle.run(prog, {"edge": edge, "out": out_in}, "add_mult")
+    rel = r.relation("out")
+    got = {(int(s), int(c)): t for s, c, t in zip(rel.samples, rel.cols[0], rel.tags)}
+    want = {(0, 0): 0.25}
+    want.update({(0, x): min(1.0, sum(P[x, y] for y in range(x + 1, n))) for x in range(1, n - 1)})
+    want.update({(1, x): min(1.0, sum(P[x, y] for y in range(x + 1, m))) for x in range(m - 1)})
+    assert set(got) == set(want)
+    for k in want:
+        assert got[k] == pytest.approx(want[k], rel=1e-12), k
