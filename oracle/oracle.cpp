@@ -80,6 +80,7 @@
 #include <mutex>
 #include <set>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -864,13 +865,16 @@ int orc_run(const char* program, int semiring, int n_inputs, const char* const* 
     }
   };
   const size_t n_threads = std::min<size_t>(runs.size(), std::max(1u, std::thread::hardware_concurrency()));
-  if (n_threads <= 1) {
-    worker();
-  } else {
-    std::vector<std::thread> pool;
-    for (size_t t = 0; t < n_threads; t++) pool.emplace_back(worker);
-    for (auto& t : pool) t.join();
+  std::vector<std::thread> pool;
+  for (size_t t = 1; t < n_threads; t++) {
+    try {
+      pool.emplace_back(worker);
+    } catch (const std::system_error&) {
+      break;  // no more threads: the ones started and this one share the samples
+    }
   }
+  worker();
+  for (auto& t : pool) t.join();
   int max_it = 0;
   uint64_t ties = load_ties;
   for (auto& sr : runs) {
