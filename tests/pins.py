@@ -79,6 +79,23 @@ def same_generation_closed_form(depth):
     return int((nd * (nd - 1)).sum())
 
 
+def same_generation_keys(depth):
+    """The same-generation relation of a tree as sorted uint64 keys (x << 32 | y):
+    every ordered pair of distinct nodes at equal depth >= 1 (siblings, or nodes
+    whose parents are of the same generation, down from the root's children)."""
+    depth = np.asarray(depth)
+    parts = []
+    for d in range(1, int(depth.max()) + 1 if len(depth) else 1):
+        v = np.flatnonzero(depth == d).astype(np.uint64)
+        if len(v) < 2:
+            continue
+        x = np.repeat(v, len(v))
+        y = np.tile(v, len(v))
+        keep = x != y
+        parts.append((x[keep] << np.uint64(32)) | y[keep])
+    return np.sort(np.concatenate(parts)) if parts else np.zeros(0, np.uint64)
+
+
 def andersen_worklist(addr, assign, load, store):
     """Andersen's inclusion-based points-to analysis by a textbook worklist
     over points-to sets (no Datalog):

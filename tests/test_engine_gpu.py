@@ -601,17 +601,27 @@ def test_cross_product_step(cross):
     """Same generation, whose recursive rule probes parent twice with keys from
     the delta row alone: the fused cross-product step (children(a) x
     children(b) straight into the membership bitmap) and the two-step
-    pipeline, against the oracle and the depth closed form; also on a
-    batched (sample-id) instance."""
-    from tests import pins
+    pipeline, against the same-generation pairs by depth; also on a batched
+    (sample-id) instance."""
     parent, child, depth = W.random_tree(5000, seed_index=31)
     opts = {"cross_join": cross, "bitmap_delta": 2}
-    st, _ = compare(W.SG_PROGRAM, {"parent": ((parent, child),)}, options=opts)
+    # element by element against the same-generation pairs by depth (which pin
+    # the oracle; its naive run on these trees takes most of a minute)
+    e, st, got = engine_run(W.SG_PROGRAM, {"parent": ((parent, child),)}, read=["sg"], options=opts)
+    e.close()
+    x, y = got["sg"].cols.astype(np.uint64)
+    assert np.array_equal((x << np.uint64(32)) | y, pins.same_generation_keys(depth))
     assert st["derived"] == pins.same_generation_closed_form(depth)
-    p2, c2, _ = W.random_tree(800, seed_index=32)
+    p2, c2, depth2 = W.random_tree(800, seed_index=32)
     samples = np.concatenate([np.zeros(len(parent), np.uint32), np.ones(len(p2), np.uint32)])
-    compare(W.SG_PROGRAM, {"parent": ((np.concatenate([parent, p2]), np.concatenate([child, c2])), None, samples)},
-            options=opts)
+    e, st, got = engine_run(W.SG_PROGRAM, {"parent": ((np.concatenate([parent, p2]), np.concatenate([child, c2])),
+                                                     None, samples)}, read=["sg"], options=opts)
+    e.close()
+    rel = got["sg"]
+    for smp, d in ((0, depth), (1, depth2)):
+        m = rel.samples == smp
+        x, y = rel.cols[:, m].astype(np.uint64)
+        assert np.array_equal((x << np.uint64(32)) | y, pins.same_generation_keys(d)), smp
 
 
 # ---------------------------------------------------------------------------

@@ -83,6 +83,8 @@ def test_sg_tree_depth_closed_form():
     assert sg.cols.shape[1] == pins.same_generation_closed_form(depth)
     x, y = sg.cols
     assert np.all(depth[x] == depth[y]) and np.all(x != y) and np.all(depth[x] >= 1)
+    keys = (x.astype(np.uint64) << np.uint64(32)) | y.astype(np.uint64)
+    assert np.array_equal(keys, pins.same_generation_keys(depth))
 
 
 @pytest.mark.parametrize("k,levels", [(2, 4), (3, 3)])
