@@ -783,3 +783,22 @@ def test_strata_keep_loaded_facts_of_a_derived_relation():
     assert set(got) == set(want)
     for k in want:
         assert got[k] == pytest.approx(want[k], rel=1e-12), k
+
+
+def test_strata_diamond_written_bottom_up():
+    """A diamond of strata, rules written with the top first: path (the chain's
+    closure), then b(x) = sum over successors and c(y) = sum over predecessors,
+    then d(x) :- b(x), c(x) with one grounding per x: d(x) = b(x) * c(x)."""
+    n = 8
+    cols, p, P = _chain(n, 6700)
+    prog = ("d(x) :- b(x), c(x).\n"
+            "c(y) :- path(x,y).\n"
+            "b(x) :- path(x,y).\n" + W.TC_PROGRAM)
+    r = oracle.run(prog, {"edge": (cols, p)}, "add_mult")
+    b = {x: min(1.0, sum(P[x, y] for y in range(x + 1, n))) for x in range(n - 1)}
+    c = {y: min(1.0, sum(P[x, y] for x in range(y))) for y in range(1, n)}
+    rel = r.relation("d")
+    got = {int(x): t for x, t in zip(rel.cols[0], rel.tags)}
+    assert set(got) == set(range(1, n - 1))
+    for x in got:
+        assert got[x] == pytest.approx(min(1.0, b[x] * c[x]), rel=1e-12), x
